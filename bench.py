@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark: energy + exact gradient throughput (G elements/s) on one GB300 per rank.
+
+Workload (default): 3D compressible Neo-Hookean on the unit cube, 128^3 hexahedra x 6
+tetrahedra (12,582,912 P1 tets, 2,146,689 nodes), face x=0 clamped, smooth displacement
+0.05 sin(pi x) per component + U[-1e-4, 1e-4] noise (seed 2).  One step = one call of
+fe_energy_gradient (node preparation, fused element kernel, patch gather).  The element
+data of one step (1.5 GB) is larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f64|f32]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Prints one JSON line on rank 0.  For N > 1 (torchrun) every rank evaluates its own replica
+of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic bytes of one launch of the element kernel, per element and per node (each
+# input read once in the paper's mesh layout: dim+1 shape gradients of dim entries, the
+# volume, dim+1 node ids, and the nodal values gathered once).
+ELEM_BYTES = {  # (dim, precision) -> (bytes per element, bytes per node)
+    (3, "f64"): (12 * 8 + 8 + 4 * 4, 24),
+    (2, "f64"): (6 * 8 + 8 + 3 * 4, 16),
+    (3, "f32"): (12 * 4 + 4 + 4 * 4, 12),
+    (2, "f32"): (6 * 4 + 4 + 3 * 4, 8),
+}
+# Whole-step algorithmic bytes add the patch CSR entries (4 B per element-node pair), the
+# row pointers (4 B per node) and the gradient written in FP64.
+STEP_EXTRA = {3: (4 * 4, 4 + 24), 2: (3 * 4, 4 + 16)}
+# FP64 operations of the 3D Neo-Hookean energy + exact gradient per element, counted on the
+# algorithm (F: 36 fma, cofactors/det: 27 + 5, I1: 9 fma, W ~ 6, dW/dF ~ 40, forces 36 fma;
+# an fma counts 2; log and one division counted as one operation each).
+F64_FLOPS_PER_TET = 250.0
+# FP64 peak of GB300: 152 SMs x 2 FP64 FMA lanes per SM per clock x 2 flops x 2.07 GHz.
+F64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def load_peaks():
+    try:
+        with open(MEASURED_PEAKS) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "100"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------------------
+
+def dist_setup(ngpus):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------------------
+
+def oracle_sample(w, fraction):
+    """A bounded sample of the workload: its first `fraction` of elements (whole layers of
+    the structured mesh) on the full node set."""
+    import numpy as np
+    from paper_2109_01158_gb300 import meshgen as mg
+    m = max(1, int(w.ne * fraction))
+    return mg.Workload(w.name + f"_first{m}", w.dim, w.d, w.coords, np.ascontiguousarray(w.elems[:m]),
+                       w.dirichlet, w.model, p=w.p, C1=w.C1, D1=w.D1, f=w.f, v=w.v, eps=w.eps)
+
+
+def time_oracle(ws, reps):
+    import oracle
+    om = oracle.OracleMesh(ws)
+    om.energy(ws.v)            # page in the working set once
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        om.energy(ws.v)
+        om.gradient_exact(ws.v)
+        ts.append(time.perf_counter() - t0)
+    return ts
+
+
+def run_reference(args, rank, world):
+    from paper_2109_01158_gb300 import meshgen as mg
+    if rank != 0:
+        return None
+    w = mg.config_workload(args.workload)
+    ws = oracle_sample(w, args.sample_fraction)
+    ts = time_oracle(ws, args.warmup + args.steps)[args.warmup:]
+    total = sum(ts)
+    value = ws.ne * len(ts) / total / 1e9
+    sample = (f"first {ws.ne} of {w.ne} elements of {w.name} ({args.sample_fraction:g} of the mesh, "
+              f"whole element layers), energy + exact gradient per step, single thread")
+    line = {
+        "impl": "reference", "metric": "energy+grad throughput", "value": value, "unit": "Gelem/s",
+        "n_gpus": 0, "steps": len(ts), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(w, "f64"),
+        "cpu_baseline": {"value": value, "unit": "Gelem/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    return line
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+
+def workload_config(w, precision):
+    return {
+        "workload": (f"{w.name}: {'3D' if w.dim == 3 else '2D'} "
+                     f"{'compressible Neo-Hookean' if w.model == 1 else f'p-Laplacian p={w.p:g}'}, "
+                     f"{w.ne} P1 elements, {w.nn} nodes, {w.ndof} dofs; energy + exact gradient"),
+        "elements": w.ne, "nodes": w.nn, "dofs": w.ndof, "precision": precision,
+        "l2": "inputs larger than L2 (element data of one step > 129 MB), no flush",
+        "parallelism": "replicas",
+    }
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_2109_01158_gb300 import fem
+    from paper_2109_01158_gb300 import meshgen as mg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = mg.config_workload(args.workload)
+    precs = (fem.FE_F64, fem.FE_F32_COMP) if args.precision == "f64" else (fem.FE_F32_COMP, fem.FE_F64)
+    gm = fem.FEMesh.from_workload(w, device=local, order=args.order, precisions=precs)
+    v = torch.from_numpy(w.v).to(dev)
+    J = torch.empty((), dtype=torch.float64, device=dev)
+    g = torch.empty(w.ndof, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def steps(n):
+        for _ in range(n):
+            gm.energy_gradient(v, J, g)
+
+    def timed(n, profile=False):
+        if profile:
+            gm.profile(True)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        l0 = gm.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        steps(n)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        ms = e0.elapsed_time(e1)
+        prof = gm.profile_read() if profile else None
+        if profile:
+            gm.profile(False)
+        return ms, gm.launch_count() - l0, prof
+
+    steps(args.warmup)
+    assert gm.sync_status() == fem.FE_OK, "domain error in the benchmark workload"
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    ms, launches, prof = timed(args.steps, profile=True)
+    clocks = sampler.stop()
+    ms = max_over_ranks(ms, world, dev)
+    ms_step = ms / args.steps
+    value = w.ne * args.steps * world / (ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel (the element kernel), timed by events on its stream
+    hbm_peak, peak_kind = load_peaks()
+    prec = args.precision
+    elem_ms = prof["element"][0] / max(prof["element"][1], 1)
+    bpe, bpn = ELEM_BYTES[(w.dim, prec)]
+    elem_bytes = w.ne * bpe + w.nn * bpn
+    xe, xn = STEP_EXTRA[w.dim]
+    step_bytes = elem_bytes + w.ne * xe + w.nn * xn
+    hbm_achieved = elem_bytes / (elem_ms / 1e3) / 1e9
+    if prec == "f64" and w.dim == 3 and w.model == mg.MODEL_NEOHOOKE:
+        achieved = F64_FLOPS_PER_TET * w.ne / (elem_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": F64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / F64_PEAK_TFLOPS, "traffic": None,
+                "peak_kind": "derived FP64 (152 SMs x 2 FMA/clk x 2.07 GHz)",
+                "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": hbm_achieved / hbm_peak, "peak_kind": peak_kind}}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind}
+    roof["kernel"] = "k_elem_%s (energy+gradient)" % prec
+    roof["kernel_ms"] = elem_ms
+    roof["algorithmic_bytes_per_launch"] = elem_bytes
+    stages = {k: {"ms_per_launch": t / n if n else 0.0, "launches": n} for k, (t, n) in prof.items() if n}
+
+    # end to end through the public API with host buffers (pinned), copies inside the region
+    vh = torch.from_numpy(w.v).pin_memory()
+    gh = torch.empty(w.ndof, dtype=torch.float64).pin_memory()
+    vh_np, gh_np = vh.numpy(), gh.numpy()
+    for _ in range(2):
+        gm.energy_gradient_host(vh_np, gh_np)
+    e2e_steps = max(3, args.steps // 2)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        gm.energy_gradient_host(vh_np, gh_np)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = {"value": w.ne * e2e_steps * world / e2e_s / 1e9, "unit": "Gelem/s",
+           "h2d_bytes_per_step": w.ndof * 8, "d2h_bytes_per_step": w.ndof * 8 + 8,
+           "api": "fe_energy_gradient_host"}
+
+    # other precision (same mesh), for context
+    other = "f32" if prec == "f64" else "f64"
+    gm.set_precision(fem.FE_F32_COMP if other == "f32" else fem.FE_F64)
+    steps(3)
+    oms, _, oprof = timed(max(5, args.steps // 4), profile=True)
+    o_elem = oprof["element"][0] / max(oprof["element"][1], 1)
+    ob, on = ELEM_BYTES[(w.dim, other)]
+    variants = {other: {"value": w.ne * max(5, args.steps // 4) / (oms / 1e3) / 1e9, "unit": "Gelem/s",
+                        "element_kernel_ms": o_elem,
+                        "element_hbm_frac": (w.ne * ob + w.nn * on) / (o_elem / 1e3) / 1e9 / hbm_peak}}
+    gm.set_precision(fem.FE_F64 if prec == "f64" else fem.FE_F32_COMP)
+
+    line = {
+        "metric": "energy+grad throughput", "value": value, "unit": "Gelem/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": workload_config(w, prec),
+        "roofline": roof,
+        "step_hbm": {"algorithmic_bytes": step_bytes,
+                     "achieved_gbs": step_bytes / (ms_step / 1e3) / 1e9,
+                     "frac": step_bytes / (ms_step / 1e3) / 1e9 / hbm_peak},
+        "stages": stages, "variants": variants,
+        "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ws = oracle_sample(w, args.sample_fraction)
+        ts = time_oracle(ws, 2)
+        best = min(ts)
+        line["cpu_baseline"] = {
+            "value": ws.ne / best / 1e9, "unit": "Gelem/s", "cores": 1, "kind": "oracle",
+            "sample": (f"first {ws.ne} of {w.ne} elements (whole element layers), energy + exact "
+                       f"gradient, best of 2, single thread")}
+    gm.close()
+    return line if rank == 0 else None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="C3")
+    ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--order", type=int, default=0, help="0 generator order, 1 Morton")
+    ap.add_argument("--sample-fraction", type=float, default=0.125)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * femenergy.h -- C ABI of libfemenergy.so: evaluation of the discrete nonlinear energy
+ * J(v) and its gradient over P1 triangles (dim = 2) and tetrahedra (dim = 3) on one
+ * NVIDIA GB300 GPU (sm_103a).
+ *
+ * The method is that of Moskovka & Valdman, "Fast MATLAB evaluation of nonlinear
+ * energies using FEM in 2D and 3D: Nodal elements" (arXiv 2109.01158):
+ *   J(v) = J_grad(v) - b.v,   J_grad(v) = sum_k |T_k| W(grad v |T_k)        (eq. Denergy)
+ *   b^(j) = M f^(j)  (P1 mass matrix M, nodal load f)                      (eqs. mass2D, linearTerm2)
+ * with the compressible Neo-Hookean density (eq. neoHook) for the vector deformation v
+ * (d = dim) or the p-Laplacian density (1/p)|grad v|^p (eq. pLaplacian, d = 1).
+ *
+ * Conventions shared by every entry point:
+ *   - Indices are 0-based.  Node i has coordinates coords[i*dim + m] (the paper's
+ *     nodes2coord); element e has nodes elems[e*(dim+1) + l] (elems2nodes, the map I_LG).
+ *   - Degrees of freedom are interleaved as in Section 5 (eq. bvvectors): dof n = d*i + j is
+ *     component j of node i.  v, g, f and the Dirichlet mask use this order, always in the
+ *     caller's node numbering, whatever internal reordering the library applies.
+ *   - Pointers named *_host are host memory; all other array pointers of the evaluation
+ *     calls are DEVICE memory owned by the caller (e.g. torch tensors) on the context's
+ *     device.  Host arrays passed to set-up calls are copied; the caller keeps ownership.
+ *   - Evaluation calls are asynchronous on the context's stream.  Their return value
+ *     reports argument and launch errors only; errors found on the device (an element with
+ *     det F <= 0) are reported by fe_sync_status() or by the *_host calls.
+ *   - No call throws; every call returns an fe_status.  fe_last_error() gives a message
+ *     for the last failing call of the calling thread.
+ *   - Results are deterministic: the same inputs give bitwise identical outputs run to
+ *     run (no floating-point atomics; fixed reduction trees and patch-sum orders).
+ */
+#ifndef FEMENERGY_H
+#define FEMENERGY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fe_ctx fe_ctx; /* opaque; the library owns every mesh buffer on the device */
+
+typedef enum {
+    FE_OK = 0,
+    FE_EINVAL = 1,   /* bad argument, malformed mesh, or call out of order              */
+    FE_ENOMEM = 2,   /* device or host allocation failed                               */
+    FE_ECUDA = 3,    /* CUDA runtime error (message in fe_last_error)                  */
+    FE_EDOMAIN = 4,  /* Neo-Hookean: some element has det F <= 0; J = +Inf              */
+    FE_ETIMEOUT = 5, /* a bounded device wait gave up                                  */
+    FE_EBUSY = 6     /* resource in use                                                */
+} fe_status;
+
+typedef enum { FE_PLAPLACE = 0, FE_NEOHOOKE = 1 } fe_model;
+
+/* Arithmetic of the element kernels.  FE_F64: IEEE double throughout.  FE_F32_COMP:
+ * per-element float arithmetic in displacement form with double-precision patch sums and
+ * compensated double-precision energy reductions (not in the paper; its error against the
+ * FP64 result is reported per result by the caller's tests). */
+typedef enum { FE_F64 = 0, FE_F32_COMP = 1 } fe_precision;
+
+/* Internal node/element numbering used for the device layout (invisible to callers). */
+typedef enum { FE_ORDER_NONE = 0, FE_ORDER_MORTON = 1 } fe_order;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int fe_version(void);
+
+/* Message describing the last failing call on this thread (owned by the library). */
+const char* fe_last_error(void);
+
+/* Create a context on CUDA device `device` that enqueues all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the context. */
+fe_status fe_create(fe_ctx** out, int device, void* cuda_stream);
+
+/* Release every device and host buffer of the context (synchronises its stream). */
+fe_status fe_destroy(fe_ctx* ctx);
+
+/* Change the stream later calls enqueue on. */
+fe_status fe_set_stream(fe_ctx* ctx, void* cuda_stream);
+
+/* Upload a mesh (the paper's `mesh` structure, Sec. 4.1).
+ *   dim        2 (triangles) or 3 (tetrahedra)
+ *   d          components per node: 1 (scalar, p-Laplacian) or dim (Neo-Hookean)
+ *   n_nodes    |N|;  coords_host: n_nodes*dim doubles, row-major (nodes2coord)
+ *   n_elems    |T|;  elems_host:  n_elems*(dim+1) int32 node ids in [0, n_nodes)
+ *   dirichlet_host: n_nodes*d bytes, 1 = fixed dof (dofsDirichlet), 0 = free (dofsMinim);
+ *                   NULL = every dof free
+ *   order      FE_ORDER_NONE keeps the caller's numbering; FE_ORDER_MORTON renumbers nodes
+ *              along a Morton curve and sorts elements by their first renumbered node so
+ *              that the gathers of v hit L2
+ * Validates ids and sizes (n_elems*(dim+1) < 2^31).  Replaces any previous mesh and
+ * invalidates the precompute.  FE_EINVAL on a malformed mesh. */
+fe_status fe_mesh_upload(fe_ctx* ctx, int dim, int d, int64_t n_nodes,
+                         const double* coords_host, int64_t n_elems,
+                         const int32_t* elems_host, const uint8_t* dirichlet_host,
+                         int order);
+
+/* Select the density: FE_PLAPLACE with exponent p > 1 (eq. pLaplacian; requires d = 1),
+ * or FE_NEOHOOKE with constants C1, D1 (eq. neoHook; requires d = dim).  For material
+ * data, C1 = mu/2 and D1 = K/2 with mu = E/(2(1+nu)), K = E/(3(1-2nu)) (Benchmark 2). */
+fe_status fe_set_model(fe_ctx* ctx, int model, double p, double C1, double D1);
+
+/* Nodal load f in V_h (n_nodes*d doubles, host, dof order; NULL = 0).  The library forms
+ * b = M f with the P1 mass matrix on the device at fe_precompute (eq. linearTerm2). */
+fe_status fe_set_load(fe_ctx* ctx, const double* f_host);
+
+/* Per-mesh precompute on the device (Sec. 4.1-4.2, done once per mesh): element volumes
+ * |T| and shape-function gradients dphi, the nodal-patch CSR (node -> (element, local
+ * index)) in increasing element order, b = M f, and the device buffers of the requested
+ * precisions.  precisions: bit mask, 1 << FE_F64 and/or 1 << FE_F32_COMP.  The first
+ * requested precision becomes the active one.  FE_EINVAL if an element is degenerate. */
+fe_status fe_precompute(fe_ctx* ctx, unsigned precisions);
+
+/* Choose the arithmetic of later evaluation calls (must have been precomputed). */
+fe_status fe_set_precision(fe_ctx* ctx, int precision);
+
+/* Device bytes held by the context (mesh, precompute and work buffers). */
+fe_status fe_footprint(const fe_ctx* ctx, size_t* bytes);
+
+/* Energy (Sec. 5): *J_dev = sum_k |T_k| W(F_k) - b.v  (one double, device).
+ *   v_dev    n_nodes*d doubles (device), full vector including Dirichlet values
+ *   dens_dev NULL, or n_elems doubles (device) receiving W(F_k) per element (the paper's
+ *            densities output), in the caller's element order
+ * Neo-Hookean with some det F <= 0: *J_dev = +Inf and fe_sync_status returns FE_EDOMAIN. */
+fe_status fe_energy(fe_ctx* ctx, const double* v_dev, double* J_dev, double* dens_dev);
+
+/* Exact gradient (Sec. 6.2, eqs. dJdvn, dWFv): g_dev[n] = dJ/dv_n for every free dof n
+ * (patch sum of |T| dW/dF : dF/dv_n, minus b_n) and 0 on Dirichlet dofs (Remark 1: the
+ * gradient restricted to free dofs is g[free]).  g_dev: n_nodes*d doubles (device). */
+fe_status fe_gradient_exact(fe_ctx* ctx, const double* v_dev, double* g_dev);
+
+/* Energy and exact gradient in one pass over the elements (J_dev as in fe_energy). */
+fe_status fe_energy_gradient(fe_ctx* ctx, const double* v_dev, double* J_dev, double* g_dev);
+
+/* Central-difference gradient over nodal patches (Sec. 6.1, eqs. CD, CDS, jgradpm,
+ * sumpatch): for dof n of node i, component j,
+ *   g_n = ( sum_{T in T^i} |T| W(F_T^+) - sum_{T in T^i} |T| W(F_T^-) ) / (2 eps) - b_n,
+ * where F_T^{+-} is F_T with row j recomputed from nodal values whose (i, j) entry is
+ * shifted by +-eps (the paper's GG layers).  Dirichlet dofs give 0.
+ *   dofs_dev NULL: every dof, g_dev has n_nodes*d entries.
+ *   dofs_dev non-NULL: n_dofs int64 dof ids (device); g_dev[q] is the value for dofs_dev[q].
+ * Always evaluated in FP64.  eps > 0. */
+fe_status fe_gradient_fd(fe_ctx* ctx, const double* v_dev, double eps, double* g_dev,
+                         const int64_t* dofs_dev, int64_t n_dofs);
+
+/* End-to-end call with HOST buffers: copies v_host to the device, evaluates the energy
+ * and the exact gradient, copies J and g back and synchronises.  J_host: one double;
+ * g_host: n_nodes*d doubles.  Returns FE_EDOMAIN if some det F <= 0. */
+fe_status fe_energy_gradient_host(fe_ctx* ctx, const double* v_host, double* J_host,
+                                  double* g_host);
+
+/* Synchronise the stream and return (and clear) the device-side status of the calls
+ * since the last fe_sync_status: FE_EDOMAIN if an element had det F <= 0, else FE_OK. */
+fe_status fe_sync_status(fe_ctx* ctx);
+
+/* Read back the precompute for inspection (synchronous, host outputs, caller's element
+ * order): dphi_host[(e*(dim+1)+l)*dim + m] = d(phi_{e,l})/d(x_m), vol_host[e] = |T_e|. */
+fe_status fe_get_shape_gradients(fe_ctx* ctx, double* dphi_host, double* vol_host);
+
+/* Read back the nodal patches in the caller's numbering (synchronous): row_ptr_host has
+ * n_nodes+1 entries, ent_host n_elems*(dim+1) entries e*(dim+1)+l, rows in increasing
+ * element order (the offsets p_i of eq. pind1 and the patch rows of Sec. 4.2). */
+fe_status fe_get_patches(fe_ctx* ctx, int64_t* row_ptr_host, int64_t* ent_host);
+
+/* Read back b = M f in dof order (synchronous, host output of n_nodes*d doubles). */
+fe_status fe_get_load_vector(fe_ctx* ctx, double* b_host);
+
+/* Number of kernels this context has launched since creation (instrumentation). */
+fe_status fe_launch_count(const fe_ctx* ctx, int64_t* count);
+
+/* Kernel timing (instrumentation).  While enabled, every kernel launch of the evaluation
+ * calls is bracketed by a pair of CUDA events on the context stream, grouped by stage:
+ *   0 node preparation, 1 element kernel, 2 patch gather, 3 central-difference element
+ *   kernel, 4 central-difference gather / subset kernel.
+ * fe_profile_read synchronises the stream, writes the summed milliseconds and the launch
+ * count of each of the first n_stages stages (n_stages <= FE_PROFILE_STAGES) to host
+ * arrays, and resets the sums. */
+#define FE_PROFILE_STAGES 5
+fe_status fe_profile_enable(fe_ctx* ctx, int enable);
+fe_status fe_profile_read(fe_ctx* ctx, double* ms_host, int64_t* launches_host, int n_stages);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEMENERGY_H */

@@ -1,0 +1,599 @@
+// fe_api.cu -- host side of the C ABI declared in include/femenergy.h: argument checks,
+// mesh upload and internal renumbering, device buffer management, dispatch of the
+// precompute and evaluation kernels, and read-back helpers.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "fe_internal.cuh"
+
+namespace fe {
+
+static thread_local std::string g_err;
+
+fe_status set_error(fe_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+fe_status cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FE_OK;
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA;
+}
+
+void prof_begin(fe_ctx* c, int stage) {
+  if (!c->prof) return;
+  auto& ev = c->prof_ev[stage];
+  const size_t need = 2 * (size_t)c->prof_n[stage] + 2;
+  while (ev.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    ev.push_back(e);
+  }
+  cudaEventRecord(ev[2 * c->prof_n[stage]], c->stream);
+}
+
+void prof_end(fe_ctx* c, int stage) {
+  if (!c->prof) return;
+  auto& ev = c->prof_ev[stage];
+  if (ev.size() < 2 * (size_t)c->prof_n[stage] + 2) return;
+  cudaEventRecord(ev[2 * c->prof_n[stage] + 1], c->stream);
+  c->prof_n[stage]++;
+}
+
+namespace {
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+fe_status dev_alloc(fe_ctx* c, T** p, size_t count) {
+  size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_check(e, "cudaMalloc");
+  }
+  c->bytes += bytes;
+  return FE_OK;
+}
+
+template <typename T>
+void dev_free(fe_ctx* c, T** p, size_t count) {
+  if (*p) {
+    cudaFree(*p);
+    size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+    c->bytes = c->bytes >= bytes ? c->bytes - bytes : 0;
+  }
+  *p = nullptr;
+}
+
+void free_precompute(fe_ctx* c) {
+  const size_t ne = (size_t)c->ne, nn = (size_t)c->nn, k = (size_t)c->dim + 1;
+  dev_free(c, &c->dphi, ne * c->dim * c->dim);
+  dev_free(c, &c->vol, ne);
+  dev_free(c, &c->row_ptr, nn + 1);
+  dev_free(c, &c->ent, ne * k);
+  dev_free(c, &c->slot, ne * k);
+  dev_free(c, &c->b, nn * c->d);
+  dev_free(c, &c->dphi32, ne * c->dim * c->dim);
+  dev_free(c, &c->vol32, ne);
+  dev_free(c, &c->u, nn * padded_d(c->d));
+  dev_free(c, &c->u32, nn * padded_d(c->d));
+  dev_free(c, &c->r, ne * k * c->d);
+  dev_free(c, &c->r32, ne * k * c->d);
+  dev_free(c, &c->stage_v, nn * c->d);
+  dev_free(c, &c->stage_g, nn * c->d);
+  c->have_pre = false;
+  c->pre_mask = 0;
+}
+
+void free_mesh(fe_ctx* c) {
+  free_precompute(c);
+  const size_t ne = (size_t)c->ne, nn = (size_t)c->nn, k = (size_t)c->dim + 1;
+  dev_free(c, &c->X, nn * c->dim);
+  dev_free(c, &c->elems, ne * k);
+  dev_free(c, &c->dir, nn * c->d);
+  dev_free(c, &c->perm, nn);
+  dev_free(c, &c->eperm, ne);
+  c->perm_h.clear();
+  c->eperm_h.clear();
+  c->have_mesh = false;
+}
+
+// Spread the low `bits` bits of x so that consecutive bits land `stride` apart.
+uint64_t spread_bits(uint64_t x, int bits, int stride) {
+  uint64_t r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((x >> b) & 1ull) << (b * stride);
+  return r;
+}
+
+// Morton (Z-order) renumbering of the nodes; perm[new] = old.
+std::vector<int32_t> morton_order(int dim, int64_t nn, const double* X) {
+  std::vector<double> lo(dim, 0.0), hi(dim, 0.0);
+  for (int m = 0; m < dim; ++m) {
+    lo[m] = hi[m] = nn > 0 ? X[m] : 0.0;
+  }
+  for (int64_t i = 0; i < nn; ++i)
+    for (int m = 0; m < dim; ++m) {
+      lo[m] = std::min(lo[m], X[i * dim + m]);
+      hi[m] = std::max(hi[m], X[i * dim + m]);
+    }
+  const int bits = dim == 3 ? 21 : 31;
+  const double scale = (double)((1ull << bits) - 1);
+  std::vector<uint64_t> key(nn);
+  for (int64_t i = 0; i < nn; ++i) {
+    uint64_t k = 0;
+    for (int m = 0; m < dim; ++m) {
+      double ext = hi[m] - lo[m];
+      double t = ext > 0 ? (X[i * dim + m] - lo[m]) / ext : 0.0;
+      uint64_t q = (uint64_t)(t * scale);
+      k |= spread_bits(q, bits, dim) << m;
+    }
+    key[i] = k;
+  }
+  std::vector<int32_t> perm(nn);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  return perm;
+}
+
+fe_status check_ready(fe_ctx* c, bool need_model = true) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  if (!c->have_mesh) return set_error(FE_EINVAL, "no mesh uploaded");
+  if (!c->have_pre) return set_error(FE_EINVAL, "fe_precompute has not been called");
+  if (need_model && !c->model_set) return set_error(FE_EINVAL, "fe_set_model has not been called");
+  return FE_OK;
+}
+
+fe_status eval(fe_ctx* c, const double* v, double* J, double* dens, double* g, bool want_energy,
+               bool want_grad) {
+  if (c->precision == FE_F32_COMP) return launch_eval_f32(c, v, J, dens, g, want_energy, want_grad);
+  return launch_eval_f64(c, v, J, dens, g, want_energy, want_grad);
+}
+
+}  // namespace
+}  // namespace fe
+
+using namespace fe;
+
+extern "C" {
+
+int fe_version(void) { return 10000; }
+
+const char* fe_last_error(void) { return g_err.c_str(); }
+
+fe_status fe_create(fe_ctx** out, int device, void* cuda_stream) {
+  if (!out) return set_error(FE_EINVAL, "out is null");
+  *out = nullptr;
+  int ndev = 0;
+  fe_status st = cuda_check(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+  if (st) return st;
+  if (device < 0 || device >= ndev) return set_error(FE_EINVAL, "bad device index");
+  fe_ctx* c = new (std::nothrow) fe_ctx();
+  if (!c) return set_error(FE_ENOMEM, "host allocation");
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  DeviceGuard g(device);
+  if (!g.ok) {
+    delete c;
+    return set_error(FE_ECUDA, "cudaSetDevice failed");
+  }
+  if ((st = dev_alloc(c, &c->partials, kMaxElemBlocks + kMaxNodeBlocks)) ||
+      (st = dev_alloc(c, &c->counter, 1)) || (st = dev_alloc(c, &c->status, 1)) ||
+      (st = dev_alloc(c, &c->stage_J, 1))) {
+    fe_destroy(c);
+    return st;
+  }
+  cudaMemset(c->counter, 0, sizeof(unsigned));
+  cudaMemset(c->status, 0, sizeof(int));
+  if ((st = cuda_check(cudaDeviceSynchronize(), "fe_create"))) {
+    fe_destroy(c);
+    return st;
+  }
+  *out = c;
+  return FE_OK;
+}
+
+fe_status fe_destroy(fe_ctx* c) {
+  if (!c) return FE_OK;
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& pool : c->prof_ev)
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  free_mesh(c);
+  dev_free(c, &c->partials, kMaxElemBlocks + kMaxNodeBlocks);
+  dev_free(c, &c->counter, 1);
+  dev_free(c, &c->status, 1);
+  dev_free(c, &c->stage_J, 1);
+  delete c;
+  return FE_OK;
+}
+
+fe_status fe_set_stream(fe_ctx* c, void* cuda_stream) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  c->stream = (cudaStream_t)cuda_stream;
+  return FE_OK;
+}
+
+fe_status fe_mesh_upload(fe_ctx* c, int dim, int d, int64_t nn, const double* coords, int64_t ne,
+                         const int32_t* elems, const uint8_t* dirichlet, int order) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  if (dim != 2 && dim != 3) return set_error(FE_EINVAL, "dim must be 2 or 3");
+  if (d != 1 && d != dim) return set_error(FE_EINVAL, "d must be 1 or dim");
+  if (nn < 0 || ne < 0) return set_error(FE_EINVAL, "negative size");
+  if (nn >= (int64_t)1 << 31 || ne * (dim + 1) >= (int64_t)1 << 31)
+    return set_error(FE_EINVAL, "mesh too large: n_nodes and n_elems*(dim+1) must be < 2^31");
+  if ((nn > 0 && !coords) || (ne > 0 && !elems)) return set_error(FE_EINVAL, "null mesh array");
+  if (order != FE_ORDER_NONE && order != FE_ORDER_MORTON) return set_error(FE_EINVAL, "bad order");
+  const int k = dim + 1;
+  for (int64_t e = 0; e < ne; ++e)
+    for (int l = 0; l < k; ++l) {
+      int32_t i = elems[e * k + l];
+      if (i < 0 || i >= nn) return set_error(FE_EINVAL, "element node id out of range");
+      for (int l2 = 0; l2 < l; ++l2)
+        if (elems[e * k + l2] == i) return set_error(FE_EINVAL, "repeated node in an element");
+    }
+  DeviceGuard g(c->device);
+  if (!g.ok) return set_error(FE_ECUDA, "cudaSetDevice failed");
+  cudaStreamSynchronize(c->stream);
+  free_mesh(c);
+  c->dim = dim;
+  c->d = d;
+  c->nn = nn;
+  c->ne = ne;
+  c->order = order;
+
+  // internal numbering
+  std::vector<int32_t> iperm;  // caller node -> device node
+  if (order == FE_ORDER_MORTON && nn > 0) {
+    c->perm_h = morton_order(dim, nn, coords);
+    iperm.resize(nn);
+    for (int64_t i = 0; i < nn; ++i) iperm[c->perm_h[i]] = (int32_t)i;
+    std::vector<int32_t> minnode(ne);
+    for (int64_t e = 0; e < ne; ++e) {
+      int32_t m = iperm[elems[e * k]];
+      for (int l = 1; l < k; ++l) m = std::min(m, iperm[elems[e * k + l]]);
+      minnode[e] = m;
+    }
+    c->eperm_h.resize(ne);
+    std::iota(c->eperm_h.begin(), c->eperm_h.end(), 0);
+    std::stable_sort(c->eperm_h.begin(), c->eperm_h.end(),
+                     [&](int32_t a, int32_t b) { return minnode[a] < minnode[b]; });
+  }
+  const bool ident = c->perm_h.empty();
+  std::vector<double> Xd(nn * dim);
+  std::vector<uint8_t> dd(nn * d, 0);
+  for (int64_t i = 0; i < nn; ++i) {
+    const int64_t src = ident ? i : c->perm_h[i];
+    for (int m = 0; m < dim; ++m) Xd[i * dim + m] = coords[src * dim + m];
+    if (dirichlet)
+      for (int j = 0; j < d; ++j) dd[i * d + j] = dirichlet[src * d + j] ? 1 : 0;
+  }
+  std::vector<int32_t> Ed(ne * k);
+  for (int64_t e = 0; e < ne; ++e) {
+    const int64_t src = ident ? e : c->eperm_h[e];
+    for (int l = 0; l < k; ++l) {
+      int32_t n = elems[src * k + l];
+      Ed[(int64_t)l * ne + e] = ident ? n : iperm[n];
+    }
+  }
+  fe_status st;
+  if ((st = dev_alloc(c, &c->X, nn * dim)) || (st = dev_alloc(c, &c->elems, ne * k)) ||
+      (st = dev_alloc(c, &c->dir, nn * d))) {
+    free_mesh(c);
+    return st;
+  }
+  cudaMemcpy(c->X, Xd.data(), sizeof(double) * nn * dim, cudaMemcpyHostToDevice);
+  cudaMemcpy(c->elems, Ed.data(), sizeof(int32_t) * ne * k, cudaMemcpyHostToDevice);
+  cudaMemcpy(c->dir, dd.data(), nn * d, cudaMemcpyHostToDevice);
+  if (!ident) {
+    if ((st = dev_alloc(c, &c->perm, nn)) || (st = dev_alloc(c, &c->eperm, ne))) {
+      free_mesh(c);
+      return st;
+    }
+    cudaMemcpy(c->perm, c->perm_h.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice);
+    cudaMemcpy(c->eperm, c->eperm_h.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice);
+  }
+  if ((st = cuda_check(cudaDeviceSynchronize(), "mesh upload"))) {
+    free_mesh(c);
+    return st;
+  }
+  c->have_mesh = true;
+  if (!c->f_host.empty() && (int64_t)c->f_host.size() != nn * d) c->f_host.clear();
+  if (c->model_set && ((c->model == FE_NEOHOOKE && d != dim) || (c->model == FE_PLAPLACE && d != 1)))
+    c->model_set = false;
+  return FE_OK;
+}
+
+fe_status fe_set_model(fe_ctx* c, int model, double p, double C1, double D1) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  if (!c->have_mesh) return set_error(FE_EINVAL, "upload the mesh before the model");
+  if (model == FE_PLAPLACE) {
+    if (c->d != 1) return set_error(FE_EINVAL, "the p-Laplacian needs d = 1");
+    if (!(p > 1.0) || !std::isfinite(p)) return set_error(FE_EINVAL, "p must be > 1");
+  } else if (model == FE_NEOHOOKE) {
+    if (c->d != c->dim) return set_error(FE_EINVAL, "Neo-Hookean needs d = dim");
+    if (!std::isfinite(C1) || !std::isfinite(D1)) return set_error(FE_EINVAL, "bad C1/D1");
+  } else {
+    return set_error(FE_EINVAL, "unknown model");
+  }
+  c->model = model;
+  c->p = p;
+  c->C1 = C1;
+  c->D1 = D1;
+  c->model_set = true;
+  return FE_OK;
+}
+
+fe_status fe_set_load(fe_ctx* c, const double* f_host) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  if (!c->have_mesh) return set_error(FE_EINVAL, "upload the mesh before the load");
+  if (!f_host) {
+    c->f_host.clear();
+  } else {
+    c->f_host.assign(f_host, f_host + c->nn * c->d);
+  }
+  if (c->have_pre) {
+    DeviceGuard g(c->device);
+    fe_status st = launch_load_vector(c);
+    if (st) return st;
+    return cuda_check(cudaStreamSynchronize(c->stream), "load vector");
+  }
+  return FE_OK;
+}
+
+fe_status fe_precompute(fe_ctx* c, unsigned precisions) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  if (!c->have_mesh) return set_error(FE_EINVAL, "no mesh uploaded");
+  if (precisions == 0 || (precisions & ~3u)) return set_error(FE_EINVAL, "bad precision mask");
+  DeviceGuard g(c->device);
+  if (!g.ok) return set_error(FE_ECUDA, "cudaSetDevice failed");
+  cudaStreamSynchronize(c->stream);
+  free_precompute(c);
+  const size_t ne = (size_t)c->ne, nn = (size_t)c->nn, k = (size_t)c->dim + 1;
+  const int dp = padded_d(c->d);
+  fe_status st;
+  if ((st = dev_alloc(c, &c->dphi, ne * c->dim * c->dim)) || (st = dev_alloc(c, &c->vol, ne)) ||
+      (st = dev_alloc(c, &c->row_ptr, nn + 1)) || (st = dev_alloc(c, &c->ent, ne * k)) ||
+      (st = dev_alloc(c, &c->slot, ne * k)) || (st = dev_alloc(c, &c->b, nn * c->d))) {
+    free_precompute(c);
+    return st;
+  }
+  if (precisions & (1u << FE_F64)) {
+    if ((st = dev_alloc(c, &c->u, nn * dp)) || (st = dev_alloc(c, &c->r, ne * k * c->d))) {
+      free_precompute(c);
+      return st;
+    }
+  }
+  if (precisions & (1u << FE_F32_COMP)) {
+    if ((st = dev_alloc(c, &c->dphi32, ne * c->dim * c->dim)) || (st = dev_alloc(c, &c->vol32, ne)) ||
+        (st = dev_alloc(c, &c->u32, nn * dp)) || (st = dev_alloc(c, &c->r32, ne * k * c->d))) {
+      free_precompute(c);
+      return st;
+    }
+  }
+  c->pre_mask = precisions;
+  cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+  if ((st = launch_precompute(c)) || (st = launch_load_vector(c))) {
+    free_precompute(c);
+    return st;
+  }
+  int hs = 0;
+  cudaMemcpyAsync(&hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if ((st = cuda_check(cudaStreamSynchronize(c->stream), "precompute"))) {
+    free_precompute(c);
+    return st;
+  }
+  cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+  if (hs & kStatusDegenerate) {
+    free_precompute(c);
+    return set_error(FE_EINVAL, "degenerate element (zero volume)");
+  }
+  c->have_pre = true;
+  c->precision = (precisions & 1u) ? FE_F64 : FE_F32_COMP;
+  return FE_OK;
+}
+
+fe_status fe_set_precision(fe_ctx* c, int precision) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  if (precision != FE_F64 && precision != FE_F32_COMP) return set_error(FE_EINVAL, "bad precision");
+  if (!c->have_pre || !(c->pre_mask & (1u << precision)))
+    return set_error(FE_EINVAL, "precision was not precomputed");
+  c->precision = precision;
+  return FE_OK;
+}
+
+fe_status fe_footprint(const fe_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return set_error(FE_EINVAL, "null argument");
+  *bytes = c->bytes;
+  return FE_OK;
+}
+
+fe_status fe_energy(fe_ctx* c, const double* v, double* J, double* dens) {
+  fe_status st = check_ready(c);
+  if (st) return st;
+  if (!v || !J) return set_error(FE_EINVAL, "null v or J");
+  DeviceGuard g(c->device);
+  return eval(c, v, J, dens, nullptr, true, false);
+}
+
+fe_status fe_gradient_exact(fe_ctx* c, const double* v, double* gout) {
+  fe_status st = check_ready(c);
+  if (st) return st;
+  if (!v || !gout) return set_error(FE_EINVAL, "null v or g");
+  DeviceGuard g(c->device);
+  return eval(c, v, nullptr, nullptr, gout, false, true);
+}
+
+fe_status fe_energy_gradient(fe_ctx* c, const double* v, double* J, double* gout) {
+  fe_status st = check_ready(c);
+  if (st) return st;
+  if (!v || !J || !gout) return set_error(FE_EINVAL, "null v, J or g");
+  DeviceGuard g(c->device);
+  return eval(c, v, J, nullptr, gout, true, true);
+}
+
+fe_status fe_gradient_fd(fe_ctx* c, const double* v, double eps, double* gout, const int64_t* dofs,
+                         int64_t ndofs) {
+  fe_status st = check_ready(c);
+  if (st) return st;
+  if (!v || !gout) return set_error(FE_EINVAL, "null v or g");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return set_error(FE_EINVAL, "eps must be > 0");
+  if (dofs && ndofs < 0) return set_error(FE_EINVAL, "negative n_dofs");
+  if (!(c->pre_mask & (1u << FE_F64)))
+    return set_error(FE_EINVAL, "the central-difference gradient needs the FP64 precompute");
+  DeviceGuard g(c->device);
+  return launch_fd_f64(c, v, eps, gout, dofs, ndofs);
+}
+
+fe_status fe_energy_gradient_host(fe_ctx* c, const double* v_host, double* J_host, double* g_host) {
+  fe_status st = check_ready(c);
+  if (st) return st;
+  if (!v_host || !J_host || !g_host) return set_error(FE_EINVAL, "null argument");
+  DeviceGuard g(c->device);
+  const size_t n = (size_t)c->nn * c->d;
+  if (!c->stage_v && ((st = dev_alloc(c, &c->stage_v, n)) || (st = dev_alloc(c, &c->stage_g, n))))
+    return st;
+  cudaMemcpyAsync(c->stage_v, v_host, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+  if ((st = eval(c, c->stage_v, c->stage_J, nullptr, c->stage_g, true, true))) return st;
+  cudaMemcpyAsync(J_host, c->stage_J, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(g_host, c->stage_g, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+  return fe_sync_status(c);
+}
+
+fe_status fe_sync_status(fe_ctx* c) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  DeviceGuard g(c->device);
+  int hs = 0;
+  cudaMemcpyAsync(&hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  fe_status st = cuda_check(cudaStreamSynchronize(c->stream), "stream");
+  if (st) return st;
+  if (hs) {
+    cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    cudaStreamSynchronize(c->stream);
+  }
+  if (hs & kStatusDomain) return set_error(FE_EDOMAIN, "an element has det F <= 0");
+  return FE_OK;
+}
+
+fe_status fe_get_shape_gradients(fe_ctx* c, double* dphi_host, double* vol_host) {
+  fe_status st = check_ready(c, false);
+  if (st) return st;
+  if (!dphi_host || !vol_host) return set_error(FE_EINVAL, "null argument");
+  DeviceGuard g(c->device);
+  const size_t nd = (size_t)c->ne * (c->dim + 1) * c->dim;
+  double *dd = nullptr, *vv = nullptr;
+  if ((st = cuda_check(cudaMalloc((void**)&dd, sizeof(double) * (nd ? nd : 1)), "alloc"))) return st;
+  if ((st = cuda_check(cudaMalloc((void**)&vv, sizeof(double) * (c->ne ? c->ne : 1)), "alloc"))) {
+    cudaFree(dd);
+    return st;
+  }
+  st = launch_expand_dphi(c, dd, vv);
+  if (!st) {
+    cudaMemcpyAsync(dphi_host, dd, sizeof(double) * nd, cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(vol_host, vv, sizeof(double) * c->ne, cudaMemcpyDeviceToHost, c->stream);
+    st = cuda_check(cudaStreamSynchronize(c->stream), "read back");
+  }
+  cudaFree(dd);
+  cudaFree(vv);
+  return st;
+}
+
+fe_status fe_get_patches(fe_ctx* c, int64_t* row_ptr_host, int64_t* ent_host) {
+  fe_status st = check_ready(c, false);
+  if (st) return st;
+  if (!row_ptr_host || !ent_host) return set_error(FE_EINVAL, "null argument");
+  DeviceGuard g(c->device);
+  const int64_t nn = c->nn, ne = c->ne, k = c->dim + 1;
+  std::vector<int32_t> rp(nn + 1), en(ne * k);
+  cudaMemcpyAsync(rp.data(), c->row_ptr, sizeof(int32_t) * (nn + 1), cudaMemcpyDeviceToHost, c->stream);
+  if (ne > 0)
+    cudaMemcpyAsync(en.data(), c->ent, sizeof(int32_t) * ne * k, cudaMemcpyDeviceToHost, c->stream);
+  if ((st = cuda_check(cudaStreamSynchronize(c->stream), "read back"))) return st;
+  if (c->perm_h.empty()) {
+    for (int64_t i = 0; i <= nn; ++i) row_ptr_host[i] = rp[i];
+    for (int64_t q = 0; q < ne * k; ++q) ent_host[q] = en[q];
+    return FE_OK;
+  }
+  // translate to the caller's numbering: caller node iu is device node iperm[iu]
+  std::vector<int32_t> iperm(nn);
+  for (int64_t i = 0; i < nn; ++i) iperm[c->perm_h[i]] = (int32_t)i;
+  row_ptr_host[0] = 0;
+  for (int64_t iu = 0; iu < nn; ++iu) {
+    const int32_t i = iperm[iu];
+    const int64_t len = rp[i + 1] - rp[i];
+    int64_t* out = ent_host + row_ptr_host[iu];
+    for (int64_t t = 0; t < len; ++t) {
+      const int32_t v = en[rp[i] + t];
+      out[t] = (int64_t)c->eperm_h[v / k] * k + v % k;
+    }
+    std::sort(out, out + len);
+    row_ptr_host[iu + 1] = row_ptr_host[iu] + len;
+  }
+  return FE_OK;
+}
+
+fe_status fe_get_load_vector(fe_ctx* c, double* b_host) {
+  fe_status st = check_ready(c, false);
+  if (st) return st;
+  if (!b_host) return set_error(FE_EINVAL, "null argument");
+  DeviceGuard g(c->device);
+  const int64_t nn = c->nn, d = c->d;
+  std::vector<double> bd(nn * d);
+  cudaMemcpyAsync(bd.data(), c->b, sizeof(double) * nn * d, cudaMemcpyDeviceToHost, c->stream);
+  if ((st = cuda_check(cudaStreamSynchronize(c->stream), "read back"))) return st;
+  for (int64_t i = 0; i < nn; ++i) {
+    const int64_t dst = c->perm_h.empty() ? i : c->perm_h[i];
+    for (int j = 0; j < d; ++j) b_host[dst * d + j] = bd[i * d + j];
+  }
+  return FE_OK;
+}
+
+fe_status fe_profile_enable(fe_ctx* c, int enable) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  c->prof = enable != 0;
+  for (int k = 0; k < FE_PROFILE_STAGES; ++k) c->prof_n[k] = 0;
+  return FE_OK;
+}
+
+fe_status fe_profile_read(fe_ctx* c, double* ms, int64_t* launches, int n_stages) {
+  if (!c || !ms || !launches) return set_error(FE_EINVAL, "null argument");
+  if (n_stages < 0 || n_stages > FE_PROFILE_STAGES) return set_error(FE_EINVAL, "bad n_stages");
+  DeviceGuard g(c->device);
+  fe_status st = cuda_check(cudaStreamSynchronize(c->stream), "profile sync");
+  if (st) return st;
+  for (int k = 0; k < n_stages; ++k) {
+    double tot = 0.0;
+    for (int i = 0; i < c->prof_n[k]; ++i) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, c->prof_ev[k][2 * i], c->prof_ev[k][2 * i + 1]) == cudaSuccess) tot += t;
+    }
+    ms[k] = tot;
+    launches[k] = c->prof_n[k];
+  }
+  for (int k = 0; k < FE_PROFILE_STAGES; ++k) c->prof_n[k] = 0;
+  return FE_OK;
+}
+
+fe_status fe_launch_count(const fe_ctx* c, int64_t* count) {
+  if (!c || !count) return set_error(FE_EINVAL, "null argument");
+  *count = c->launches;
+  return FE_OK;
+}
+
+}  // extern "C"

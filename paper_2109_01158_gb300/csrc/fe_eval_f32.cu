@@ -1,0 +1,384 @@
+// fe_eval_f32.cu -- FP32 element arithmetic with compensated reductions (not in the paper).
+//
+// The element work of Sec. 5 / 6.2 in float, written in displacement form so that no
+// O(1) quantities cancel: with F = I + H (H = grad u, u = v - X),
+//   delta = det F - 1 = tr H + i2(H) + det H      (i2: sum of principal 2x2 minors; 2D: tr H + det H)
+//   I1 - dim - 2 log det F = |H|^2 - 2 (i2(H) + det H) + 2 phi(delta),   phi(x) = x - log(1+x)
+//   dW/dF = 2 C1 (F - F^{-T}) + 2 D1 delta cof F,   F - F^{-T} = H + cof(F) H^T / det F
+// phi uses the series of 2 atanh: with s = x/(2+x), log(1+x) = 2(s + s^3/3 + s^5/5 + ...),
+// so phi(x) = s x - 2 s^3 (1/3 + s^2/5 + s^4/7 + ...).  Where |delta| > 1/2, or det F is
+// close to 0, delta and log det F are taken in FP64.
+//
+// Reductions: each thread accumulates |T| W in a float pair (TwoSum, Knuth), the pair is
+// converted to double per thread, and the block/global trees run in double.  The patch
+// sums of the gradient are float pairs converted to double per node.  No floating-point
+// operation is done in FP64 per element except in the rare FP64 branch above.
+#include "fe_internal.cuh"
+
+namespace fe {
+namespace {
+
+// ---- float-pair accumulation (error-free TwoSum) ---------------------------------------
+struct FPair {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__device__ __forceinline__ double block_sum(double x, double* sh) {
+  x = warp_sum(x);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = x;
+  __syncthreads();
+  x = (threadIdx.x < kThreads / 32) ? sh[threadIdx.x] : 0.0;
+  if (warp == 0) x = warp_sum(x);
+  __syncthreads();
+  return x;
+}
+
+__device__ __forceinline__ void finish_energy(double block_total, double* partials, int n_elem_blocks,
+                                              const double* node_partials, int n_node_blocks,
+                                              unsigned* counter, double* J, double* sh) {
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = block_total;
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    am_last = (t == (unsigned)n_elem_blocks - 1u);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  double s = 0.0, t = 0.0;
+  for (int k = threadIdx.x; k < n_elem_blocks; k += kThreads) s += __ldcg(partials + k);
+  for (int k = threadIdx.x; k < n_node_blocks; k += kThreads) t += __ldcg(node_partials + k);
+  s = block_sum(s, sh);
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) {
+    *J = s - t;
+    *counter = 0u;
+  }
+}
+
+// phi(x) = x - log(1+x) for |x| <= 1/2 by the atanh series (|s| <= 1/3, 8 terms).
+__device__ __forceinline__ float phi_series(float x) {
+  const float s = x / (2.0f + x);
+  const float s2 = s * s;
+  float t = 1.0f / 17.0f;
+  t = fmaf(t, s2, 1.0f / 15.0f);
+  t = fmaf(t, s2, 1.0f / 13.0f);
+  t = fmaf(t, s2, 1.0f / 11.0f);
+  t = fmaf(t, s2, 1.0f / 9.0f);
+  t = fmaf(t, s2, 1.0f / 7.0f);
+  t = fmaf(t, s2, 1.0f / 5.0f);
+  t = fmaf(t, s2, 1.0f / 3.0f);
+  return fmaf(s, x, -2.0f * s * s2 * t);
+}
+
+template <int D>
+__device__ __forceinline__ void load_u32(const float* __restrict__ u, int32_t n, float* out) {
+  if (D == 1) {
+    out[0] = __ldg(u + n);
+  } else if (D == 2) {
+    float2 a = __ldg(reinterpret_cast<const float2*>(u) + n);
+    out[0] = a.x;
+    out[1] = a.y;
+  } else {
+    float4 a = __ldg(reinterpret_cast<const float4*>(u) + n);
+    out[0] = a.x;
+    out[1] = a.y;
+    out[2] = a.z;
+  }
+}
+
+template <int D, bool NH, int DIM>
+__global__ void __launch_bounds__(kThreads) k_node_prep32(int64_t nn, const double* __restrict__ v,
+                                                          const double* __restrict__ X,
+                                                          const int32_t* __restrict__ perm,
+                                                          const double* __restrict__ b,
+                                                          float* __restrict__ u,
+                                                          double* __restrict__ node_partials) {
+  __shared__ double sh[kThreads / 32];
+  constexpr int DP = D == 3 ? 4 : D;
+  double dot = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
+    const int64_t src = perm ? (int64_t)perm[i] : i;
+    float w[DP];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const double vj = v[src * D + j];
+      dot += b[i * D + j] * vj;
+      w[j] = (float)(NH ? vj - X[i * DIM + j] : vj);
+    }
+    if (DP == 4) w[3] = 0.f;
+    if (DP == 1) u[i] = w[0];
+    else if (DP == 2) reinterpret_cast<float2*>(u)[i] = make_float2(w[0], w[1]);
+    else reinterpret_cast<float4*>(u)[i] = make_float4(w[0], w[1], w[2], w[3]);
+  }
+  dot = block_sum(dot, sh);
+  if (threadIdx.x == 0) node_partials[blockIdx.x] = dot;
+}
+
+template <int DIM, int D, int MODEL, bool ENERGY, bool GRAD, bool DENS>
+__global__ void __launch_bounds__(kThreads) k_elem_f32(
+    int64_t ne, const int32_t* __restrict__ elems, const float* __restrict__ dphi,
+    const float* __restrict__ vol, const float* __restrict__ u, const int32_t* __restrict__ slot,
+    const int32_t* __restrict__ eperm, ModelParams mp, float* __restrict__ r,
+    double* __restrict__ dens, double* partials, const double* node_partials, int n_node_blocks,
+    unsigned* counter, double* J, int* status) {
+  constexpr int K = DIM + 1;
+  __shared__ double sh[kThreads / 32];
+  FPair acc;
+  bool bad = false;
+  const float C1 = (float)mp.C1, D1 = (float)mp.D1;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
+    float ul[K][D];
+#pragma unroll
+    for (int l = 0; l < K; ++l) load_u32<D>(u, __ldg(elems + (int64_t)l * ne + e), ul[l]);
+    float g[DIM][DIM];
+#pragma unroll
+    for (int l = 0; l < DIM; ++l)
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) g[l][m] = __ldg(dphi + ((int64_t)l * DIM + m) * ne + e);
+    const float vT = __ldg(vol + e);
+    float H[D][DIM];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float a[DIM];
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) a[l] = ul[l + 1][j] - ul[0][j];
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) {
+        float s = a[0] * g[0][m];
+#pragma unroll
+        for (int l = 1; l < DIM; ++l) s = fmaf(a[l], g[l][m], s);
+        H[j][m] = s;
+      }
+    }
+    float W = 0.f;
+    float P[D][DIM];
+    if (MODEL == FE_NEOHOOKE) {
+      float hsq = 0.f;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) hsq = fmaf(H[j][m], H[j][m], hsq);
+      float tr, i2, dH, C[DIM][DIM];  // C = cof(I + H)
+      if (DIM == 3) {
+        tr = H[0][0] + H[1][1] + H[2][2];
+        i2 = (H[0][0] * H[1][1] - H[0][1] * H[1][0]) + (H[0][0] * H[2][2] - H[0][2] * H[2][0]) +
+             (H[1][1] * H[2][2] - H[1][2] * H[2][1]);
+        const float m00 = H[1][1] * H[2][2] - H[1][2] * H[2][1];
+        const float m01 = H[1][2] * H[2][0] - H[1][0] * H[2][2];
+        const float m02 = H[1][0] * H[2][1] - H[1][1] * H[2][0];
+        dH = H[0][0] * m00 + H[0][1] * m01 + H[0][2] * m02;
+        if (GRAD) {
+          const float F00 = 1.f + H[0][0], F11 = 1.f + H[1][1], F22 = 1.f + H[2][2];
+          C[0][0] = F11 * F22 - H[1][2] * H[2][1];
+          C[0][1] = H[1][2] * H[2][0] - H[1][0] * F22;
+          C[0][2] = H[1][0] * H[2][1] - F11 * H[2][0];
+          C[1][0] = H[0][2] * H[2][1] - H[0][1] * F22;
+          C[1][1] = F00 * F22 - H[0][2] * H[2][0];
+          C[1][2] = H[0][1] * H[2][0] - F00 * H[2][1];
+          C[2][0] = H[0][1] * H[1][2] - H[0][2] * F11;
+          C[2][1] = H[0][2] * H[1][0] - F00 * H[1][2];
+          C[2][2] = F00 * F11 - H[0][1] * H[1][0];
+        }
+      } else {
+        tr = H[0][0] + H[1][1];
+        dH = H[0][0] * H[1][1] - H[0][1] * H[1][0];
+        i2 = 0.f;
+        if (GRAD) {
+          C[0][0] = 1.f + H[1][1];
+          C[0][1] = -H[1][0];
+          C[1][0] = -H[0][1];
+          C[1][1] = 1.f + H[0][0];
+        }
+      }
+      float delta = tr + i2 + dH;
+      bool ebad = false;
+      float phi2;      // 2 phi(delta)
+      float inv_det;   // 1 / det F
+      if (fabsf(delta) <= 0.5f) {
+        phi2 = 2.f * phi_series(delta);
+        inv_det = 1.f / (1.f + delta);
+      } else {
+        // far from F = I: det F and log det F in FP64 from the float entries of H
+        double Hd[DIM][DIM];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j)
+#pragma unroll
+          for (int m = 0; m < DIM; ++m) Hd[j][m] = (double)H[j][m];
+        double detd;
+        if (DIM == 3) {
+          const double F00 = 1.0 + Hd[0][0], F11 = 1.0 + Hd[1][1], F22 = 1.0 + Hd[2][2];
+          detd = F00 * (F11 * F22 - Hd[1][2] * Hd[2][1]) + Hd[0][1] * (Hd[1][2] * Hd[2][0] - Hd[1][0] * F22) +
+                 Hd[0][2] * (Hd[1][0] * Hd[2][1] - F11 * Hd[2][0]);
+        } else {
+          detd = (1.0 + Hd[0][0]) * (1.0 + Hd[1][1]) - Hd[0][1] * Hd[1][0];
+        }
+        if (!(detd > 0.0)) {
+          ebad = true;
+          detd = 1.0;
+        }
+        const double dd = detd - 1.0;
+        delta = (float)dd;
+        phi2 = (float)(2.0 * (dd - log(detd)));
+        inv_det = (float)(1.0 / detd);
+      }
+      if (ENERGY || DENS) W = C1 * (hsq - 2.f * (i2 + dH) + phi2) + D1 * delta * delta;
+      if (ebad) {
+        W = CUDART_INF_F;
+        bad = true;
+      }
+      if (GRAD) {
+        // P = 2 C1 (H + C H^T / det F) + 2 D1 delta C, scaled by |T|
+        const float a = 2.f * C1 * vT, c = 2.f * D1 * delta * vT, ai = a * inv_det;
+#pragma unroll
+        for (int j = 0; j < DIM; ++j)
+#pragma unroll
+          for (int m = 0; m < DIM; ++m) {
+            float ch = 0.f;  // (C H^T)_jm = sum_k C_jk H_mk
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) ch = fmaf(C[j][k], H[m][k], ch);
+            P[j][m] = fmaf(a, H[j][m], fmaf(ai, ch, c * C[j][m]));
+          }
+      }
+    } else {
+      float s = 0.f;
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) s = fmaf(H[0][m], H[0][m], s);
+      if (ENERGY || DENS) {
+        if (mp.pcase == 2) W = 0.5f * s;
+        else if (mp.pcase == 3) W = s * sqrtf(s) * (1.f / 3.f);
+        else W = s > 0.f ? powf(s, 0.5f * (float)mp.p) / (float)mp.p : 0.f;
+      }
+      if (GRAD) {
+        float cf = (mp.pcase == 2) ? 1.f : (mp.pcase == 3) ? sqrtf(s)
+                                     : (s > 0.f ? powf(s, 0.5f * (float)(mp.p - 2.0)) : 0.f);
+        cf *= vT;
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) P[0][m] = cf * H[0][m];
+      }
+    }
+    if (ENERGY) acc.add(vT * W);
+    if (DENS) dens[eperm ? (int64_t)eperm[e] : e] = (double)W;
+    if (GRAD) {
+      float r0[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) r0[j] = 0.f;
+#pragma unroll
+      for (int l = 1; l <= DIM; ++l) {
+        const int64_t q = __ldg(slot + (int64_t)l * ne + e);
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          float s = P[j][0] * g[l - 1][0];
+#pragma unroll
+          for (int m = 1; m < DIM; ++m) s = fmaf(P[j][m], g[l - 1][m], s);
+          r[q * D + j] = s;
+          r0[j] -= s;
+        }
+      }
+      const int64_t q0 = __ldg(slot + e);
+#pragma unroll
+      for (int j = 0; j < D; ++j) r[q0 * D + j] = r0[j];
+    }
+  }
+  if (bad) atomicOr(status, kStatusDomain);
+  if (ENERGY) {
+    double t = block_sum(acc.value(), sh);
+    finish_energy(t, partials, gridDim.x, node_partials, n_node_blocks, counter, J, sh);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_gather32(int64_t nn, const int32_t* __restrict__ row_ptr,
+                                                       const float* __restrict__ r,
+                                                       const double* __restrict__ b,
+                                                       const uint8_t* __restrict__ dir,
+                                                       const int32_t* __restrict__ perm,
+                                                       double* __restrict__ g) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
+    FPair s[D];
+    const int32_t q1 = __ldg(row_ptr + i + 1);
+    for (int32_t q = __ldg(row_ptr + i); q < q1; ++q)
+#pragma unroll
+      for (int j = 0; j < D; ++j) s[j].add(__ldg(r + (int64_t)q * D + j));
+    const int64_t dst = perm ? (int64_t)__ldg(perm + i) : i;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const double val = s[j].value() - b[i * D + j];
+      g[dst * D + j] = dir[i * D + j] ? 0.0 : val;
+    }
+  }
+}
+
+template <int DIM, int D, int MODEL>
+fe_status eval32_t(fe_ctx* c, const double* v, double* J, double* dens, double* g, bool want_energy,
+                   bool want_grad) {
+  cudaStream_t s = c->stream;
+  const ModelParams mp = model_params(c);
+  const int nb_node = grid_for(c->nn, kMaxNodeBlocks);
+  const int nb_elem = grid_for(c->ne, kMaxElemBlocks);
+  double* node_partials = c->partials + kMaxElemBlocks;
+  prof_begin(c, kStagePrep);
+  k_node_prep32<D, MODEL == FE_NEOHOOKE, DIM><<<nb_node, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b,
+                                                                           c->u32, node_partials);
+  prof_end(c, kStagePrep);
+  c->launches++;
+  const bool E = want_energy, G = want_grad, Dn = dens != nullptr;
+#define FE_ELEM32(EN, GR, DE)                                                                        \
+  k_elem_f32<DIM, D, MODEL, EN, GR, DE><<<nb_elem, kThreads, 0, s>>>(                                \
+      c->ne, c->elems, c->dphi32, c->vol32, c->u32, c->slot, c->eperm, mp, c->r32, dens, c->partials, \
+      node_partials, nb_node, c->counter, J, c->status)
+  if (c->ne > 0 || E) {
+    prof_begin(c, kStageElem);
+    if (E && G && Dn) FE_ELEM32(true, true, true);
+    else if (E && G) FE_ELEM32(true, true, false);
+    else if (E && Dn) FE_ELEM32(true, false, true);
+    else if (E) FE_ELEM32(true, false, false);
+    else if (G && Dn) FE_ELEM32(false, true, true);
+    else if (G) FE_ELEM32(false, true, false);
+    else FE_ELEM32(false, false, true);
+    prof_end(c, kStageElem);
+    c->launches++;
+  }
+#undef FE_ELEM32
+  if (G) {
+    prof_begin(c, kStageGather);
+    k_gather32<D><<<grid_for(c->nn, 4 * kMaxNodeBlocks), kThreads, 0, s>>>(c->nn, c->row_ptr, c->r32, c->b,
+                                                                           c->dir, c->perm, g);
+    prof_end(c, kStageGather);
+    c->launches++;
+  }
+  return cuda_check(cudaGetLastError(), "eval f32 launch");
+}
+
+}  // namespace
+
+fe_status launch_eval_f32(fe_ctx* c, const double* v, double* J, double* dens, double* g,
+                          bool want_energy, bool want_grad) {
+  if (c->model == FE_NEOHOOKE) {
+    if (c->dim == 2) return eval32_t<2, 2, FE_NEOHOOKE>(c, v, J, dens, g, want_energy, want_grad);
+    return eval32_t<3, 3, FE_NEOHOOKE>(c, v, J, dens, g, want_energy, want_grad);
+  }
+  if (c->dim == 2) return eval32_t<2, 1, FE_PLAPLACE>(c, v, J, dens, g, want_energy, want_grad);
+  return eval32_t<3, 1, FE_PLAPLACE>(c, v, J, dens, g, want_energy, want_grad);
+}
+
+}  // namespace fe

@@ -1,0 +1,669 @@
+// fe_eval_f64.cu -- FP64 evaluation of the energy J(v) = sum |T| W(F_T) - b.v, its exact
+// gradient and the patch-local central-difference gradient (Sec. 5, 6.1 and 6.2).
+//
+// Pipeline of one call (all on the context stream):
+//   k_node_prep   v (caller order) -> u (device order): u = v - X for Neo-Hookean
+//                 (displacement form of F = grad v), u = v for the p-Laplacian; also the
+//                 block partials of b.v.
+//   k_elem_f64    one thread per element (grid-stride, fixed grid): gathers u at the
+//                 dim+1 vertices, forms F = I + sum_{l>=1} (u_l - u_0) grad(phi_l)^T (the
+//                 same matrix as eq. Dv because sum_l grad(phi_l) = 0 and
+//                 sum_l X_l grad(phi_l)^T = I), evaluates W (and dW/dF), accumulates
+//                 |T| W, and writes the local forces r_{T,l} = |T| dW/dF grad(phi_l) to the
+//                 CSR position of (T, l); the last block to finish reduces the partials.
+//   k_gather      one thread per node: g_i = sum of its CSR segment - b_i (0 on Dirichlet
+//                 dofs), written in the caller's dof order.
+// Every reduction has a fixed order, so results are bitwise reproducible.
+#include "fe_internal.cuh"
+
+namespace fe {
+namespace {
+
+// ---- block reduction helpers -----------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Sum over the block in a fixed tree; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double x, double* sh) {
+  x = warp_sum(x);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = x;
+  __syncthreads();
+  x = (threadIdx.x < kThreads / 32) ? sh[threadIdx.x] : 0.0;
+  if (warp == 0) x = warp_sum(x);
+  __syncthreads();
+  return x;
+}
+
+// The block that finishes last sums the element partials and the b.v partials in a fixed
+// order and writes J = sum |T| W - b.v.
+__device__ __forceinline__ void finish_energy(double block_total, double* partials, int n_elem_blocks,
+                                              const double* node_partials, int n_node_blocks,
+                                              unsigned* counter, double* J, double* sh) {
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = block_total;
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    am_last = (t == (unsigned)n_elem_blocks - 1u);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  double s = 0.0, t = 0.0;
+  for (int k = threadIdx.x; k < n_elem_blocks; k += kThreads) s += __ldcg(partials + k);
+  for (int k = threadIdx.x; k < n_node_blocks; k += kThreads) t += __ldcg(node_partials + k);
+  s = block_sum(s, sh);
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) {
+    *J = s - t;
+    *counter = 0u;
+  }
+}
+
+// ---- densities --------------------------------------------------------------------------
+
+// Compressible Neo-Hookean (eq. neoHook) for F = I + H in 3D, with its derivative
+// dW/dF = 2 C1 F + (2 D1 (det F - 1) - 2 C1 / det F) cof F, where cof F_jm = d det/dF_jm
+// = (-1)^(j+m) det(F^sub_jm) (Sec. 6.2).
+struct NH3 {
+  double F[3][3], C[3][3], det;
+  __device__ __forceinline__ void setup(const double H[3][3]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) F[j][m] = (j == m) ? 1.0 + H[j][m] : H[j][m];
+    C[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+    C[0][1] = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+    C[0][2] = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+    C[1][0] = F[0][2] * F[2][1] - F[0][1] * F[2][2];
+    C[1][1] = F[0][0] * F[2][2] - F[0][2] * F[2][0];
+    C[1][2] = F[0][1] * F[2][0] - F[0][0] * F[2][1];
+    C[2][0] = F[0][1] * F[1][2] - F[0][2] * F[1][1];
+    C[2][1] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
+    C[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+    det = F[0][0] * C[0][0] + F[0][1] * C[0][1] + F[0][2] * C[0][2];
+  }
+};
+
+__device__ __forceinline__ double nh_density(double I1, double det, int dim, const ModelParams& mp) {
+  const double dm1 = det - 1.0;
+  return mp.C1 * (I1 - (double)dim - 2.0 * log(det)) + mp.D1 * dm1 * dm1;
+}
+
+__device__ __forceinline__ double plap_density(double s, const ModelParams& mp) {
+  if (mp.pcase == 2) return 0.5 * s;
+  if (mp.pcase == 3) return s * sqrt(s) * (1.0 / 3.0);
+  return s > 0.0 ? pow(s, 0.5 * mp.p) / mp.p : 0.0;
+}
+
+__device__ __forceinline__ double plap_coef(double s, const ModelParams& mp) {
+  if (mp.pcase == 2) return 1.0;
+  if (mp.pcase == 3) return sqrt(s);
+  return s > 0.0 ? pow(s, 0.5 * (mp.p - 2.0)) : 0.0;
+}
+
+// Load the displacement of one node: stride DP doubles (16-byte aligned for DP >= 2).
+template <int D>
+__device__ __forceinline__ void load_u(const double* __restrict__ u, int32_t n, double* out) {
+  if (D == 1) {
+    out[0] = __ldg(u + n);
+  } else if (D == 2) {
+    double2 a = __ldg(reinterpret_cast<const double2*>(u) + n);
+    out[0] = a.x;
+    out[1] = a.y;
+  } else {
+    const double2* p = reinterpret_cast<const double2*>(u) + 2 * (int64_t)n;
+    double2 a = __ldg(p), b = __ldg(p + 1);
+    out[0] = a.x;
+    out[1] = a.y;
+    out[2] = b.x;
+  }
+}
+
+// ---- kernels ------------------------------------------------------------------------------
+
+template <int D, bool NH, int DIM>
+__global__ void __launch_bounds__(kThreads) k_node_prep(int64_t nn, const double* __restrict__ v,
+                                                        const double* __restrict__ X,
+                                                        const int32_t* __restrict__ perm,
+                                                        const double* __restrict__ b,
+                                                        double* __restrict__ u,
+                                                        double* __restrict__ node_partials) {
+  __shared__ double sh[kThreads / 32];
+  constexpr int DP = D == 3 ? 4 : D;
+  double dot = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
+    const int64_t src = perm ? (int64_t)perm[i] : i;
+    double w[DP];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const double vj = v[src * D + j];
+      dot += b[i * D + j] * vj;
+      w[j] = NH ? vj - X[i * DIM + j] : vj;
+    }
+    if (DP == 4) w[3] = 0.0;
+    if (DP == 1) {
+      u[i] = w[0];
+    } else {
+      double2* o = reinterpret_cast<double2*>(u) + i * (DP / 2);
+      o[0] = make_double2(w[0], w[1]);
+      if (DP == 4) o[1] = make_double2(w[2], w[3]);
+    }
+  }
+  dot = block_sum(dot, sh);
+  if (threadIdx.x == 0) node_partials[blockIdx.x] = dot;
+}
+
+// Element kernel: energy partials, densities, and/or local forces.
+template <int DIM, int D, int MODEL, bool ENERGY, bool GRAD, bool DENS>
+__global__ void __launch_bounds__(kThreads) k_elem_f64(
+    int64_t ne, const int32_t* __restrict__ elems, const double* __restrict__ dphi,
+    const double* __restrict__ vol, const double* __restrict__ u, const int32_t* __restrict__ slot,
+    const int32_t* __restrict__ eperm, ModelParams mp, double* __restrict__ r,
+    double* __restrict__ dens, double* partials, const double* node_partials, int n_node_blocks,
+    unsigned* counter, double* J, int* status) {
+  constexpr int K = DIM + 1;
+  __shared__ double sh[kThreads / 32];
+  double acc = 0.0;
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
+    double ul[K][D];
+#pragma unroll
+    for (int l = 0; l < K; ++l) load_u<D>(u, __ldg(elems + (int64_t)l * ne + e), ul[l]);
+    double g[DIM][DIM];  // grad(phi_l), l = 1..DIM
+#pragma unroll
+    for (int l = 0; l < DIM; ++l)
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) g[l][m] = __ldg(dphi + ((int64_t)l * DIM + m) * ne + e);
+    const double vT = __ldg(vol + e);
+    // H_jm = sum_{l>=1} (u_l - u_0)_j dphi_lm
+    double H[D][DIM];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double a[DIM];
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) a[l] = ul[l + 1][j] - ul[0][j];
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) {
+        double s = a[0] * g[0][m];
+#pragma unroll
+        for (int l = 1; l < DIM; ++l) s = fma(a[l], g[l][m], s);
+        H[j][m] = s;
+      }
+    }
+    double W = 0.0;
+    double P[D][DIM];
+    if (MODEL == FE_NEOHOOKE) {
+      double det, I1 = 0.0, Fm[DIM][DIM], Cm[DIM][DIM];
+      if (DIM == 3) {
+        NH3 nh;
+        double H3[3][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int m = 0; m < 3; ++m) H3[j][m] = H[j][m];
+        nh.setup(H3);
+        det = nh.det;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            Fm[j][m] = nh.F[j][m];
+            Cm[j][m] = nh.C[j][m];
+          }
+      } else {
+        Fm[0][0] = 1.0 + H[0][0];
+        Fm[0][1] = H[0][1];
+        Fm[1][0] = H[1][0];
+        Fm[1][1] = 1.0 + H[1][1];
+        Cm[0][0] = Fm[1][1];
+        Cm[0][1] = -Fm[1][0];
+        Cm[1][0] = -Fm[0][1];
+        Cm[1][1] = Fm[0][0];
+        det = Fm[0][0] * Fm[1][1] - Fm[0][1] * Fm[1][0];
+      }
+#pragma unroll
+      for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) I1 = fma(Fm[j][m], Fm[j][m], I1);
+      if (!(det > 0.0)) {
+        bad = true;
+        W = CUDART_INF;
+      } else if (ENERGY || DENS) {
+        W = nh_density(I1, det, DIM, mp);
+      }
+      if (GRAD) {
+        const double a = 2.0 * mp.C1 * vT;
+        const double c = vT * (2.0 * mp.D1 * (det - 1.0) - 2.0 * mp.C1 / det);
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+          for (int m = 0; m < DIM; ++m) P[j][m] = fma(a, Fm[j][m], c * Cm[j][m]);
+      }
+    } else {
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) s = fma(H[0][m], H[0][m], s);
+      if (ENERGY || DENS) W = plap_density(s, mp);
+      if (GRAD) {
+        const double c = vT * plap_coef(s, mp);
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) P[0][m] = c * H[0][m];
+      }
+    }
+    if (ENERGY) acc = fma(vT, W, acc);
+    if (DENS) dens[eperm ? (int64_t)eperm[e] : e] = W;
+    if (GRAD) {
+      // r_l = |T| P grad(phi_l) for l >= 1, r_0 = -sum_{l>=1} r_l (grad(phi_0) = -sum grad(phi_l))
+      double r0[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) r0[j] = 0.0;
+#pragma unroll
+      for (int l = 1; l <= DIM; ++l) {
+        const int64_t q = __ldg(slot + (int64_t)l * ne + e);
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          double s = P[j][0] * g[l - 1][0];
+#pragma unroll
+          for (int m = 1; m < DIM; ++m) s = fma(P[j][m], g[l - 1][m], s);
+          r[q * D + j] = s;
+          r0[j] -= s;
+        }
+      }
+      const int64_t q0 = __ldg(slot + e);
+#pragma unroll
+      for (int j = 0; j < D; ++j) r[q0 * D + j] = r0[j];
+    }
+  }
+  if (bad) atomicOr(status, kStatusDomain);
+  if (ENERGY) {
+    acc = block_sum(acc, sh);
+    finish_energy(acc, partials, gridDim.x, node_partials, n_node_blocks, counter, J, sh);
+  }
+}
+
+// g_i = sum of the CSR segment of node i - b_i, 0 on Dirichlet dofs, caller's order.
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_gather(int64_t nn, const int32_t* __restrict__ row_ptr,
+                                                     const double* __restrict__ r,
+                                                     const double* __restrict__ b,
+                                                     const uint8_t* __restrict__ dir,
+                                                     const int32_t* __restrict__ perm,
+                                                     double* __restrict__ g) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
+    double s[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) s[j] = 0.0;
+    const int32_t q1 = __ldg(row_ptr + i + 1);
+    for (int32_t q = __ldg(row_ptr + i); q < q1; ++q)
+#pragma unroll
+      for (int j = 0; j < D; ++j) s[j] += __ldg(r + (int64_t)q * D + j);
+    const int64_t dst = perm ? (int64_t)__ldg(perm + i) : i;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const double val = s[j] - b[i * D + j];
+      g[dst * D + j] = dir[i * D + j] ? 0.0 : val;
+    }
+  }
+}
+
+// ---- central differences over patches (Sec. 6.1) ------------------------------------------
+
+// W at F_T with row j recomputed from nodal values whose entry (local lc, component j) is
+// shifted by delta (the GG layer of component j).  ul: element nodal values.
+template <int DIM, int D, int MODEL>
+__device__ __forceinline__ double fd_density(double ul[DIM + 1][D], const double g[DIM][DIM],
+                                             const double H[D][DIM], int lc, int j, double delta,
+                                             const ModelParams& mp, bool& bad) {
+  double row[DIM];
+  double a[DIM];
+  const double u0 = (lc == 0) ? ul[0][j] + delta : ul[0][j];
+#pragma unroll
+  for (int l = 0; l < DIM; ++l) a[l] = ((lc == l + 1) ? ul[l + 1][j] + delta : ul[l + 1][j]) - u0;
+#pragma unroll
+  for (int m = 0; m < DIM; ++m) {
+    double s = a[0] * g[0][m];
+#pragma unroll
+    for (int l = 1; l < DIM; ++l) s = fma(a[l], g[l][m], s);
+    row[m] = s;
+  }
+  if (MODEL == FE_NEOHOOKE) {
+    double F[DIM][DIM];
+#pragma unroll
+    for (int jj = 0; jj < DIM; ++jj)
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) {
+        const double h = (jj == j) ? row[m] : H[jj][m];
+        F[jj][m] = (jj == m) ? 1.0 + h : h;
+      }
+    double det, I1 = 0.0;
+    if (DIM == 3) {
+      det = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) +
+            F[0][1] * (F[1][2] * F[2][0] - F[1][0] * F[2][2]) +
+            F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+    } else {
+      det = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+    }
+#pragma unroll
+    for (int jj = 0; jj < DIM; ++jj)
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) I1 = fma(F[jj][m], F[jj][m], I1);
+    if (!(det > 0.0)) {
+      bad = true;
+      return CUDART_INF;
+    }
+    return nh_density(I1, det, DIM, mp);
+  } else {
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) s = fma(row[m], row[m], s);
+    return plap_density(s, mp);
+  }
+}
+
+template <int DIM, int D>
+__device__ __forceinline__ void element_state(int64_t e, int64_t ne, const int32_t* __restrict__ elems,
+                                              const double* __restrict__ dphi,
+                                              const double* __restrict__ u, double ul[DIM + 1][D],
+                                              double g[DIM][DIM], double H[D][DIM]) {
+#pragma unroll
+  for (int l = 0; l <= DIM; ++l) load_u<D>(u, __ldg(elems + (int64_t)l * ne + e), ul[l]);
+#pragma unroll
+  for (int l = 0; l < DIM; ++l)
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) g[l][m] = __ldg(dphi + ((int64_t)l * DIM + m) * ne + e);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    double a[DIM];
+#pragma unroll
+    for (int l = 0; l < DIM; ++l) a[l] = ul[l + 1][j] - ul[0][j];
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) {
+      double s = a[0] * g[0][m];
+#pragma unroll
+      for (int l = 1; l < DIM; ++l) s = fma(a[l], g[l][m], s);
+      H[j][m] = s;
+    }
+  }
+}
+
+// Full mode: |T| W(F^{+-}) for every (element, local node, component), written to the CSR
+// position of (T, l): plus values in rp, minus values in rm.
+template <int DIM, int D, int MODEL>
+__global__ void __launch_bounds__(kThreads) k_elem_fd_f64(int64_t ne, const int32_t* __restrict__ elems,
+                                                          const double* __restrict__ dphi,
+                                                          const double* __restrict__ vol,
+                                                          const double* __restrict__ u,
+                                                          const int32_t* __restrict__ slot, ModelParams mp,
+                                                          double eps, double* __restrict__ rp,
+                                                          double* __restrict__ rm, int* status) {
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
+    double ul[DIM + 1][D], g[DIM][DIM], H[D][DIM];
+    element_state<DIM, D>(e, ne, elems, dphi, u, ul, g, H);
+    const double vT = __ldg(vol + e);
+#pragma unroll
+    for (int lc = 0; lc <= DIM; ++lc) {
+      const int64_t q = __ldg(slot + (int64_t)lc * ne + e);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        rp[q * D + j] = vT * fd_density<DIM, D, MODEL>(ul, g, H, lc, j, eps, mp, bad);
+        rm[q * D + j] = vT * fd_density<DIM, D, MODEL>(ul, g, H, lc, j, -eps, mp, bad);
+      }
+    }
+  }
+  if (bad) atomicOr(status, kStatusDomain);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_gather_fd(int64_t nn, const int32_t* __restrict__ row_ptr,
+                                                        const double* __restrict__ rp,
+                                                        const double* __restrict__ rm, double eps,
+                                                        const double* __restrict__ b,
+                                                        const uint8_t* __restrict__ dir,
+                                                        const int32_t* __restrict__ perm,
+                                                        double* __restrict__ g) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
+    double sp[D], sm[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) sp[j] = sm[j] = 0.0;
+    const int32_t q1 = row_ptr[i + 1];
+    for (int32_t q = row_ptr[i]; q < q1; ++q)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        sp[j] += rp[(int64_t)q * D + j];
+        sm[j] += rm[(int64_t)q * D + j];
+      }
+    const int64_t dst = perm ? (int64_t)perm[i] : i;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const double val = (sp[j] - sm[j]) / (2.0 * eps) - b[i * D + j];
+      g[dst * D + j] = dir[i * D + j] ? 0.0 : val;
+    }
+  }
+}
+
+// Subset mode: one thread per requested dof walks the patch of its node.
+template <int DIM, int D, int MODEL>
+__global__ void __launch_bounds__(kThreads) k_fd_subset(int64_t ndofs, const int64_t* __restrict__ dofs,
+                                                        const int32_t* __restrict__ iperm, int64_t nn,
+                                                        int64_t ne, const int32_t* __restrict__ row_ptr,
+                                                        const int32_t* __restrict__ ent,
+                                                        const int32_t* __restrict__ elems,
+                                                        const double* __restrict__ dphi,
+                                                        const double* __restrict__ vol,
+                                                        const double* __restrict__ u,
+                                                        const double* __restrict__ b,
+                                                        const uint8_t* __restrict__ dir, ModelParams mp,
+                                                        double eps, double* __restrict__ g,
+                                                        int* status) {
+  constexpr int K = DIM + 1;
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ndofs; t += stride) {
+    const int64_t n = dofs[t];
+    if (n < 0 || n >= nn * D) {
+      g[t] = CUDART_NAN;
+      continue;
+    }
+    const int64_t iu = n / D;
+    const int j = (int)(n % D);
+    const int64_t i = iperm ? (int64_t)iperm[iu] : iu;
+    if (dir[i * D + j]) {
+      g[t] = 0.0;
+      continue;
+    }
+    double sp = 0.0, sm = 0.0;
+    for (int32_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+      const int32_t en = ent[q];
+      const int64_t e = en / K;
+      const int lc = en % K;
+      double ul[DIM + 1][D], gg[DIM][DIM], H[D][DIM];
+      element_state<DIM, D>(e, ne, elems, dphi, u, ul, gg, H);
+      const double vT = vol[e];
+      sp += vT * fd_density<DIM, D, MODEL>(ul, gg, H, lc, j, eps, mp, bad);
+      sm += vT * fd_density<DIM, D, MODEL>(ul, gg, H, lc, j, -eps, mp, bad);
+    }
+    g[t] = (sp - sm) / (2.0 * eps) - b[i * D + j];
+  }
+  if (bad) atomicOr(status, kStatusDomain);
+}
+
+// Expand the stored gradients (l = 1..dim) to the paper's full dphi layout in the caller's
+// element order; grad(phi_0) = -sum_{l>=1} grad(phi_l).
+template <int DIM>
+__global__ void k_expand(int64_t ne, const double* __restrict__ dphi, const double* __restrict__ vol,
+                         const int32_t* __restrict__ eperm, double* __restrict__ out,
+                         double* __restrict__ vol_out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
+    const int64_t eu = eperm ? (int64_t)eperm[e] : e;
+    double* o = out + eu * (DIM + 1) * DIM;
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) {
+      double s0 = 0.0;
+#pragma unroll
+      for (int l = 1; l <= DIM; ++l) {
+        const double x = dphi[((int64_t)(l - 1) * DIM + m) * ne + e];
+        o[l * DIM + m] = x;
+        s0 = __dsub_rn(s0, x);
+      }
+      o[m] = s0;
+    }
+    vol_out[eu] = vol[e];
+  }
+}
+
+// ---- dispatch -------------------------------------------------------------------------------
+
+template <int DIM, int D, int MODEL>
+fe_status eval_t(fe_ctx* c, const double* v, double* J, double* dens, double* g, bool want_energy,
+                 bool want_grad) {
+  cudaStream_t s = c->stream;
+  const ModelParams mp = model_params(c);
+  const int nb_node = grid_for(c->nn, kMaxNodeBlocks);
+  const int nb_elem = grid_for(c->ne, kMaxElemBlocks);
+  double* node_partials = c->partials + kMaxElemBlocks;
+  prof_begin(c, kStagePrep);
+  k_node_prep<D, MODEL == FE_NEOHOOKE, DIM><<<nb_node, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b,
+                                                                         c->u, node_partials);
+  prof_end(c, kStagePrep);
+  c->launches++;
+  const bool E = want_energy, G = want_grad, Dn = dens != nullptr;
+#define FE_ELEM(EN, GR, DE)                                                                         \
+  k_elem_f64<DIM, D, MODEL, EN, GR, DE><<<nb_elem, kThreads, 0, s>>>(                               \
+      c->ne, c->elems, c->dphi, c->vol, c->u, c->slot, c->eperm, mp, c->r, dens, c->partials,       \
+      node_partials, nb_node, c->counter, J, c->status)
+  if (c->ne > 0 || E) {
+    prof_begin(c, kStageElem);
+    if (E && G && Dn) FE_ELEM(true, true, true);
+    else if (E && G) FE_ELEM(true, true, false);
+    else if (E && Dn) FE_ELEM(true, false, true);
+    else if (E) FE_ELEM(true, false, false);
+    else if (G && Dn) FE_ELEM(false, true, true);
+    else if (G) FE_ELEM(false, true, false);
+    else FE_ELEM(false, false, true);
+    prof_end(c, kStageElem);
+    c->launches++;
+  }
+#undef FE_ELEM
+  if (G) {
+    prof_begin(c, kStageGather);
+    k_gather<D><<<grid_for(c->nn, 4 * kMaxNodeBlocks), kThreads, 0, s>>>(c->nn, c->row_ptr, c->r, c->b,
+                                                                         c->dir, c->perm, g);
+    prof_end(c, kStageGather);
+    c->launches++;
+  }
+  return cuda_check(cudaGetLastError(), "eval f64 launch");
+}
+
+template <int DIM, int D, int MODEL>
+fe_status fd_t(fe_ctx* c, const double* v, double eps, double* g, const int64_t* dofs, int64_t ndofs,
+               double* rfd, int32_t* iperm) {
+  cudaStream_t s = c->stream;
+  const ModelParams mp = model_params(c);
+  const int nb_node = grid_for(c->nn, kMaxNodeBlocks);
+  prof_begin(c, kStagePrep);
+  k_node_prep<D, MODEL == FE_NEOHOOKE, DIM><<<nb_node, kThreads, 0, s>>>(
+      c->nn, v, c->X, c->perm, c->b, c->u, c->partials + kMaxElemBlocks);
+  prof_end(c, kStagePrep);
+  c->launches++;
+  if (dofs) {
+    if (ndofs > 0) {
+      prof_begin(c, kStageFdGather);
+      k_fd_subset<DIM, D, MODEL><<<grid_for(ndofs, 4 * kMaxNodeBlocks), kThreads, 0, s>>>(
+          ndofs, dofs, iperm, c->nn, c->ne, c->row_ptr, c->ent, c->elems, c->dphi, c->vol, c->u, c->b,
+          c->dir, mp, eps, g, c->status);
+      prof_end(c, kStageFdGather);
+      c->launches++;
+    }
+  } else {
+    const int64_t nslot = c->ne * (DIM + 1) * D;
+    if (c->ne > 0) {
+      prof_begin(c, kStageFdElem);
+      k_elem_fd_f64<DIM, D, MODEL><<<grid_for(c->ne, kMaxElemBlocks), kThreads, 0, s>>>(
+          c->ne, c->elems, c->dphi, c->vol, c->u, c->slot, mp, eps, rfd, rfd + nslot, c->status);
+      prof_end(c, kStageFdElem);
+      c->launches++;
+    }
+    prof_begin(c, kStageFdGather);
+    k_gather_fd<D><<<grid_for(c->nn, 4 * kMaxNodeBlocks), kThreads, 0, s>>>(
+        c->nn, c->row_ptr, rfd, rfd + nslot, eps, c->b, c->dir, c->perm, g);
+    prof_end(c, kStageFdGather);
+    c->launches++;
+  }
+  return cuda_check(cudaGetLastError(), "fd f64 launch");
+}
+
+}  // namespace
+
+ModelParams model_params(const fe_ctx* c) {
+  ModelParams mp;
+  mp.p = c->p;
+  mp.C1 = c->C1;
+  mp.D1 = c->D1;
+  mp.pcase = (c->p == 2.0) ? 2 : (c->p == 3.0) ? 3 : 0;
+  return mp;
+}
+
+fe_status launch_eval_f64(fe_ctx* c, const double* v, double* J, double* dens, double* g,
+                          bool want_energy, bool want_grad) {
+  if (c->model == FE_NEOHOOKE) {
+    if (c->dim == 2) return eval_t<2, 2, FE_NEOHOOKE>(c, v, J, dens, g, want_energy, want_grad);
+    return eval_t<3, 3, FE_NEOHOOKE>(c, v, J, dens, g, want_energy, want_grad);
+  }
+  if (c->dim == 2) return eval_t<2, 1, FE_PLAPLACE>(c, v, J, dens, g, want_energy, want_grad);
+  return eval_t<3, 1, FE_PLAPLACE>(c, v, J, dens, g, want_energy, want_grad);
+}
+
+fe_status launch_fd_f64(fe_ctx* c, const double* v, double eps, double* g, const int64_t* dofs,
+                        int64_t ndofs) {
+  double* rfd = nullptr;
+  int32_t* iperm = nullptr;
+  cudaStream_t s = c->stream;
+  fe_status st;
+  if (!dofs) {
+    const size_t bytes = sizeof(double) * 2 * (size_t)c->ne * (c->dim + 1) * c->d;
+    if ((st = cuda_check(cudaMallocAsync((void**)&rfd, bytes > 0 ? bytes : 8, s), "alloc fd"))) return st;
+  } else if (c->perm) {
+    if ((st = cuda_check(cudaMallocAsync((void**)&iperm, sizeof(int32_t) * c->nn, s), "alloc iperm")))
+      return st;
+    std::vector<int32_t> ip(c->nn);
+    for (int64_t k = 0; k < c->nn; ++k) ip[c->perm_h[k]] = (int32_t)k;
+    cudaMemcpyAsync(iperm, ip.data(), sizeof(int32_t) * c->nn, cudaMemcpyHostToDevice, s);
+    if ((st = cuda_check(cudaStreamSynchronize(s), "iperm"))) return st;
+  }
+  if (c->model == FE_NEOHOOKE)
+    st = (c->dim == 2) ? fd_t<2, 2, FE_NEOHOOKE>(c, v, eps, g, dofs, ndofs, rfd, iperm)
+                       : fd_t<3, 3, FE_NEOHOOKE>(c, v, eps, g, dofs, ndofs, rfd, iperm);
+  else
+    st = (c->dim == 2) ? fd_t<2, 1, FE_PLAPLACE>(c, v, eps, g, dofs, ndofs, rfd, iperm)
+                       : fd_t<3, 1, FE_PLAPLACE>(c, v, eps, g, dofs, ndofs, rfd, iperm);
+  if (rfd) cudaFreeAsync(rfd, s);
+  if (iperm) cudaFreeAsync(iperm, s);
+  return st;
+}
+
+fe_status launch_expand_dphi(fe_ctx* c, double* dphi_full, double* vol_user) {
+  if (c->ne == 0) return FE_OK;
+  if (c->dim == 2)
+    k_expand<2><<<grid_for(c->ne, kMaxElemBlocks), kThreads, 0, c->stream>>>(c->ne, c->dphi, c->vol,
+                                                                             c->eperm, dphi_full, vol_user);
+  else
+    k_expand<3><<<grid_for(c->ne, kMaxElemBlocks), kThreads, 0, c->stream>>>(c->ne, c->dphi, c->vol,
+                                                                             c->eperm, dphi_full, vol_user);
+  c->launches++;
+  return cuda_check(cudaGetLastError(), "expand launch");
+}
+
+}  // namespace fe

@@ -1,0 +1,128 @@
+// fe_internal.cuh -- device layout, context and kernel entry points shared by the
+// translation units of libfemenergy.so.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "femenergy.h"
+
+namespace fe {
+
+// Fixed launch shapes.  The element and node reductions use a grid that depends only on
+// the problem size (never on the device), so every run sums the same partials in the same
+// order and results are bitwise reproducible.
+constexpr int kThreads = 256;
+constexpr int kMaxElemBlocks = 1216;  // 8 x 152 SMs
+constexpr int kMaxNodeBlocks = 608;   // 4 x 152 SMs
+
+// Device status bits (accumulated until fe_sync_status).
+constexpr int kStatusDomain = 1;      // det F <= 0 seen
+constexpr int kStatusDegenerate = 2;  // |T| == 0 at precompute
+
+// Model parameters passed by value to the element kernels.
+struct ModelParams {
+  double p, C1, D1;
+  int pcase;  // p-Laplacian: 2 -> p == 2, 3 -> p == 3, 0 -> general pow
+};
+
+inline int grid_for(int64_t n, int max_blocks) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  if (b < 1) b = 1;
+  return (int)(b < max_blocks ? b : max_blocks);
+}
+
+// Padded stride (in components) of the per-node displacement buffer: 1, 2 or 4.
+inline int padded_d(int d) { return d == 3 ? 4 : d; }
+
+}  // namespace fe
+
+// Context: all device buffers are in the internal ("device") numbering.
+struct fe_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+
+  // mesh
+  int dim = 0, d = 0, order = 0;
+  int64_t nn = 0, ne = 0;
+  bool have_mesh = false, have_pre = false;
+  unsigned pre_mask = 0;
+  int precision = FE_F64;
+  int model = FE_NEOHOOKE;
+  double p = 2.0, C1 = 0.0, D1 = 0.0;
+  bool model_set = false;
+  std::vector<double> f_host;   // load in the caller's dof order (empty = 0)
+  std::vector<int32_t> perm_h;  // device node -> caller node (empty = identity)
+  std::vector<int32_t> eperm_h; // device element -> caller element (empty = identity)
+
+  // device: mesh
+  double* X = nullptr;         // nn*dim, device node order
+  int32_t* elems = nullptr;    // (dim+1) SoA arrays of ne node ids
+  uint8_t* dir = nullptr;      // nn*d Dirichlet mask, device order
+  int32_t* perm = nullptr;     // nn (null = identity)
+  int32_t* eperm = nullptr;    // ne (null = identity)
+
+  // device: precompute
+  double* dphi = nullptr;      // dim*dim SoA arrays of ne: index (l-1)*dim + m, l = 1..dim
+  double* vol = nullptr;       // ne
+  int32_t* row_ptr = nullptr;  // nn+1
+  int32_t* ent = nullptr;      // ne*(dim+1): e*(dim+1)+l, rows in increasing element order
+  int32_t* slot = nullptr;     // (dim+1) SoA arrays of ne: CSR position of (e, l)
+  double* b = nullptr;         // nn*d, device order
+  float* dphi32 = nullptr;     // FP32 copy of dphi
+  float* vol32 = nullptr;      // FP32 copy of vol
+
+  // device: work buffers
+  double* u = nullptr;         // nn*padded_d(d): displacement (Neo-Hookean) or v
+  float* u32 = nullptr;        // nn*padded_d(d), FP32 displacement
+  double* r = nullptr;         // ne*(dim+1)*d slot-ordered local forces (x2 for FD)
+  float* r32 = nullptr;        // ne*(dim+1)*d, FP32 local forces
+  double* partials = nullptr;  // element partials [kMaxElemBlocks] then node partials
+  unsigned* counter = nullptr; // last-block ticket
+  int* status = nullptr;       // device status bits
+  double* stage_v = nullptr;   // staging for the *_host call
+  double* stage_g = nullptr;
+  double* stage_J = nullptr;
+
+  int64_t launches = 0;
+  size_t bytes = 0;
+
+  // kernel timing: per stage, a pool of event pairs recorded around each launch
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev[FE_PROFILE_STAGES];
+  int prof_n[FE_PROFILE_STAGES] = {0};
+};
+
+namespace fe {
+
+// error reporting (thread-local message)
+fe_status set_error(fe_status st, const std::string& msg);
+fe_status cuda_check(cudaError_t e, const char* what);
+
+// fe_precompute.cu
+fe_status launch_precompute(fe_ctx* c);
+fe_status launch_load_vector(fe_ctx* c);
+
+// fe_eval_f64.cu
+fe_status launch_eval_f64(fe_ctx* c, const double* v, double* J, double* dens, double* g,
+                          bool want_energy, bool want_grad);
+fe_status launch_fd_f64(fe_ctx* c, const double* v, double eps, double* g,
+                        const int64_t* dofs, int64_t ndofs);
+fe_status launch_expand_dphi(fe_ctx* c, double* dphi_full, double* vol_user);
+
+// fe_eval_f32.cu
+fe_status launch_eval_f32(fe_ctx* c, const double* v, double* J, double* dens, double* g,
+                          bool want_energy, bool want_grad);
+
+ModelParams model_params(const fe_ctx* c);
+
+// Bracket a launch with profiling events when timing is enabled (no-op otherwise).
+enum Stage { kStagePrep = 0, kStageElem = 1, kStageGather = 2, kStageFdElem = 3, kStageFdGather = 4 };
+void prof_begin(fe_ctx* c, int stage);
+void prof_end(fe_ctx* c, int stage);
+
+}  // namespace fe

@@ -1,0 +1,335 @@
+"""Python binding of libfemenergy.so (argument marshalling only).
+
+The module-level functions carry the names of the C ABI in ``include/femenergy.h`` and take
+plain integers for device pointers; :class:`FEMesh` wraps a context for torch tensors, and
+:class:`EnergyFunction` is the ``torch.autograd.Function`` whose forward is the energy kernel
+and whose backward is the exact-gradient kernel.  Every step of the evaluation runs in the
+CUDA library; there is no CPU fallback: if the library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfemenergy.so")
+
+FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_EDOMAIN, FE_ETIMEOUT, FE_EBUSY = range(7)
+FE_PLAPLACE, FE_NEOHOOKE = 0, 1
+FE_F64, FE_F32_COMP = 0, 1
+FE_ORDER_NONE, FE_ORDER_MORTON = 0, 1
+
+_STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "FE_EDOMAIN",
+                 5: "FE_ETIMEOUT", 6: "FE_EBUSY"}
+
+
+class FEError(RuntimeError):
+    """A libfemenergy call returned a status other than FE_OK."""
+
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+
+# name -> argtypes (restype is int = fe_status unless listed in _RESTYPE)
+_SIGNATURES = {
+    "fe_version": [],
+    "fe_last_error": [],
+    "fe_create": [_vp, _int, _vp],
+    "fe_destroy": [_vp],
+    "fe_set_stream": [_vp, _vp],
+    "fe_mesh_upload": [_vp, _int, _int, _i64, _vp, _i64, _vp, _vp, _int],
+    "fe_set_model": [_vp, _int, _dbl, _dbl, _dbl],
+    "fe_set_load": [_vp, _vp],
+    "fe_precompute": [_vp, ctypes.c_uint],
+    "fe_set_precision": [_vp, _int],
+    "fe_footprint": [_vp, _vp],
+    "fe_energy": [_vp, _vp, _vp, _vp],
+    "fe_gradient_exact": [_vp, _vp, _vp],
+    "fe_energy_gradient": [_vp, _vp, _vp, _vp],
+    "fe_gradient_fd": [_vp, _vp, _dbl, _vp, _vp, _i64],
+    "fe_energy_gradient_host": [_vp, _vp, _vp, _vp],
+    "fe_sync_status": [_vp],
+    "fe_get_shape_gradients": [_vp, _vp, _vp],
+    "fe_get_patches": [_vp, _vp, _vp],
+    "fe_get_load_vector": [_vp, _vp],
+    "fe_launch_count": [_vp, _vp],
+    "fe_profile_enable": [_vp, _int],
+    "fe_profile_read": [_vp, _vp, _vp, _int],
+}
+_RESTYPE = {"fe_version": ctypes.c_int, "fe_last_error": ctypes.c_char_p}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfemenergy.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"{path} is missing: build it with `python -m paper_2109_01158_gb300.build` "
+                "(there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, args in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = _RESTYPE.get(name, ctypes.c_int)
+        _lib = lib
+    return _lib
+
+
+def _call(name: str, *args) -> int:
+    st = getattr(load_library(), name)(*args)
+    if st != FE_OK:
+        raise FEError(st, name, fe_last_error())
+    return st
+
+
+def _checked(name):
+    def f(*args):
+        return _call(name, *args)
+    f.__name__ = name
+    f.__doc__ = f"C ABI `{name}` (raises FEError on a status other than FE_OK)."
+    return f
+
+
+def fe_version() -> int:
+    return load_library().fe_version()
+
+
+def fe_last_error() -> str:
+    msg = load_library().fe_last_error()
+    return msg.decode() if msg else ""
+
+
+fe_create = _checked("fe_create")
+fe_destroy = _checked("fe_destroy")
+fe_set_stream = _checked("fe_set_stream")
+fe_mesh_upload = _checked("fe_mesh_upload")
+fe_set_model = _checked("fe_set_model")
+fe_set_load = _checked("fe_set_load")
+fe_precompute = _checked("fe_precompute")
+fe_set_precision = _checked("fe_set_precision")
+fe_footprint = _checked("fe_footprint")
+fe_energy = _checked("fe_energy")
+fe_gradient_exact = _checked("fe_gradient_exact")
+fe_energy_gradient = _checked("fe_energy_gradient")
+fe_gradient_fd = _checked("fe_gradient_fd")
+fe_energy_gradient_host = _checked("fe_energy_gradient_host")
+fe_get_shape_gradients = _checked("fe_get_shape_gradients")
+fe_get_patches = _checked("fe_get_patches")
+fe_get_load_vector = _checked("fe_get_load_vector")
+fe_launch_count = _checked("fe_launch_count")
+fe_profile_enable = _checked("fe_profile_enable")
+fe_profile_read = _checked("fe_profile_read")
+
+FE_PROFILE_STAGES = 5
+PROFILE_STAGE_NAMES = ("node_prep", "element", "gather", "fd_element", "fd_gather")
+
+
+def fe_sync_status(ctx) -> int:
+    """Returns FE_OK or FE_EDOMAIN; raises on other errors."""
+    st = load_library().fe_sync_status(ctx)
+    if st not in (FE_OK, FE_EDOMAIN):
+        raise FEError(st, "fe_sync_status", fe_last_error())
+    return st
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class FEMesh:
+    """One resident mesh with its precompute on a CUDA device.
+
+    Arguments mirror ``fe_mesh_upload`` / ``fe_set_model`` / ``fe_set_load`` /
+    ``fe_precompute``; arrays are host numpy arrays in the paper's layout.
+    """
+
+    def __init__(self, dim, d, coords, elems, dirichlet=None, *, model, p=2.0, C1=0.0, D1=0.0,
+                 f=None, device=0, order=FE_ORDER_NONE, precisions=(FE_F64,)):
+        if not torch.cuda.is_available():
+            raise RuntimeError("FEMesh needs a CUDA device")
+        self.device = torch.device("cuda", device)
+        self.dim, self.d = int(dim), int(d)
+        self._coords = np.ascontiguousarray(coords, dtype=np.float64)
+        self._elems = np.ascontiguousarray(elems, dtype=np.int32)
+        self.nn, self.ne = self._coords.shape[0], self._elems.shape[0]
+        self.ndof = self.nn * self.d
+        dirichlet = None if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8)
+        self.dirichlet = dirichlet
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            self._stream = torch.cuda.current_stream(self.device).cuda_stream
+            fe_create(ctypes.byref(h), device, ctypes.c_void_p(self._stream))
+        self.ctx = h
+        fe_mesh_upload(self.ctx, self.dim, self.d, self.nn, _ptr(self._coords), self.ne,
+                       _ptr(self._elems), _ptr(dirichlet), int(order))
+        fe_set_model(self.ctx, int(model), float(p), float(C1), float(D1))
+        if f is not None:
+            f = np.ascontiguousarray(f, dtype=np.float64)
+            fe_set_load(self.ctx, _ptr(f))
+        mask = 0
+        for prec in precisions:
+            mask |= 1 << int(prec)
+        fe_precompute(self.ctx, mask)
+        self.precision = int(precisions[0])
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.dim, w.d, w.coords, w.elems, w.dirichlet, model=w.model, p=w.p, C1=w.C1,
+                   D1=w.D1, f=w.f, **kw)
+
+    # -- plumbing ------------------------------------------------------------------------
+    def _sync_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        if s != self._stream:
+            fe_set_stream(self.ctx, ctypes.c_void_p(s))
+            self._stream = s
+
+    def _vec(self, v):
+        if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == torch.float64):
+            raise TypeError("v must be a float64 CUDA tensor")
+        if v.numel() != self.ndof:
+            raise ValueError(f"v has {v.numel()} entries, expected {self.ndof}")
+        return v.contiguous()
+
+    def set_precision(self, prec):
+        fe_set_precision(self.ctx, int(prec))
+        self.precision = int(prec)
+
+    # -- evaluation ----------------------------------------------------------------------
+    def energy(self, v, densities=False):
+        v = self._vec(v)
+        self._sync_stream()
+        J = torch.empty((), dtype=torch.float64, device=self.device)
+        dens = torch.empty(self.ne, dtype=torch.float64, device=self.device) if densities else None
+        fe_energy(self.ctx, _ptr(v), _ptr(J), _ptr(dens))
+        return (J, dens) if densities else J
+
+    def gradient_exact(self, v, out=None):
+        v = self._vec(v)
+        self._sync_stream()
+        g = out if out is not None else torch.empty(self.ndof, dtype=torch.float64, device=self.device)
+        fe_gradient_exact(self.ctx, _ptr(v), _ptr(g))
+        return g
+
+    def energy_gradient(self, v, J=None, g=None):
+        v = self._vec(v)
+        self._sync_stream()
+        J = J if J is not None else torch.empty((), dtype=torch.float64, device=self.device)
+        g = g if g is not None else torch.empty(self.ndof, dtype=torch.float64, device=self.device)
+        fe_energy_gradient(self.ctx, _ptr(v), _ptr(J), _ptr(g))
+        return J, g
+
+    def gradient_fd(self, v, eps, dofs=None):
+        v = self._vec(v)
+        self._sync_stream()
+        if dofs is None:
+            g = torch.empty(self.ndof, dtype=torch.float64, device=self.device)
+            fe_gradient_fd(self.ctx, _ptr(v), float(eps), _ptr(g), None, 0)
+        else:
+            dofs = torch.as_tensor(dofs, dtype=torch.int64).to(self.device).contiguous()
+            g = torch.empty(dofs.numel(), dtype=torch.float64, device=self.device)
+            fe_gradient_fd(self.ctx, _ptr(v), float(eps), _ptr(g), _ptr(dofs), dofs.numel())
+        return g
+
+    def energy_gradient_host(self, v_host, g_host=None):
+        """End-to-end call on host buffers (numpy float64; pinned memory is fastest)."""
+        v_host = np.ascontiguousarray(v_host, dtype=np.float64) if isinstance(v_host, np.ndarray) else v_host
+        J = ctypes.c_double(0.0)
+        if g_host is None:
+            g_host = np.empty(self.ndof, dtype=np.float64)
+        st = load_library().fe_energy_gradient_host(self.ctx, _ptr(v_host), ctypes.byref(J), _ptr(g_host))
+        if st not in (FE_OK, FE_EDOMAIN):
+            raise FEError(st, "fe_energy_gradient_host", fe_last_error())
+        return J.value, g_host, st
+
+    def sync_status(self) -> int:
+        return fe_sync_status(self.ctx)
+
+    # -- inspection ----------------------------------------------------------------------
+    def shape_gradients(self):
+        dphi = np.empty(self.ne * (self.dim + 1) * self.dim)
+        vol = np.empty(self.ne)
+        fe_get_shape_gradients(self.ctx, _ptr(dphi), _ptr(vol))
+        return dphi, vol
+
+    def patches(self):
+        row_ptr = np.empty(self.nn + 1, dtype=np.int64)
+        ent = np.empty(max(self.ne * (self.dim + 1), 1), dtype=np.int64)
+        fe_get_patches(self.ctx, _ptr(row_ptr), _ptr(ent))
+        return row_ptr, ent[: self.ne * (self.dim + 1)]
+
+    def load_vector(self):
+        b = np.empty(self.ndof)
+        fe_get_load_vector(self.ctx, _ptr(b))
+        return b
+
+    def footprint(self) -> int:
+        n = ctypes.c_size_t(0)
+        fe_footprint(self.ctx, ctypes.byref(n))
+        return n.value
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int64(0)
+        fe_launch_count(self.ctx, ctypes.byref(n))
+        return n.value
+
+    def profile(self, enable: bool = True):
+        fe_profile_enable(self.ctx, 1 if enable else 0)
+
+    def profile_read(self):
+        """{stage: (total ms, launches)} since the last read; synchronises the stream."""
+        ms = np.zeros(FE_PROFILE_STAGES)
+        n = np.zeros(FE_PROFILE_STAGES, dtype=np.int64)
+        fe_profile_read(self.ctx, _ptr(ms), _ptr(n), FE_PROFILE_STAGES)
+        return {PROFILE_STAGE_NAMES[k]: (float(ms[k]), int(n[k])) for k in range(FE_PROFILE_STAGES)}
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            fe_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class EnergyFunction(torch.autograd.Function):
+    """J = energy(v) with the exact-gradient kernel as its backward.
+
+    The gradient is taken with respect to the free dofs: Dirichlet dofs are data of the
+    problem and receive 0 (Remark 1 of the paper restricts the gradient to free dofs)."""
+
+    @staticmethod
+    def forward(ctx, v, mesh: FEMesh):
+        ctx.mesh = mesh
+        ctx.save_for_backward(v)
+        return mesh.energy(v)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (v,) = ctx.saved_tensors
+        g = ctx.mesh.gradient_exact(v)
+        return grad_out * g, None
+
+
+def energy(v, mesh: FEMesh):
+    """Differentiable energy: ``energy(v, mesh).backward()`` runs the exact-gradient kernel."""
+    return EnergyFunction.apply(v, mesh)

@@ -1,0 +1,325 @@
+"""GPU (libfemenergy.so, through the C ABI) against the CPU oracle, element by element.
+
+Sizes span several 256-thread tiles with ragged tails; the full-size workloads are the
+2D p-Laplacian 64x64x2, the 2D Neo-Hookean 1024x512x2 and the 3D Neo-Hookean 128^3x6 mesh,
+run in the same launch configuration the benchmark times.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_01158_gb300 import meshgen as mg
+from parity import (check_energy, check_grad, energy_scale, fd_extra)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2109_01158_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _fem():
+    from paper_2109_01158_gb300 import fem
+    return fem
+
+
+def _gpu(w, **kw):
+    return _fem().FEMesh.from_workload(w, **kw)
+
+
+def _v(w):
+    return torch.from_numpy(np.ascontiguousarray(w.v)).cuda()
+
+
+# ----------------------------------------------------------------------------------------
+# a1: precompute, patches, load vector
+# ----------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("maker", [
+    lambda: mg.random_small(1, 2, mg.MODEL_PLAPLACE, 23, 17),
+    lambda: mg.random_small(2, 3, mg.MODEL_NEOHOOKE, 9, 7, 5),
+    lambda: mg.twisted_bar(1),
+])
+@pytest.mark.parametrize("order", [0, 1])
+def test_precompute_patches_and_load_vector(maker, order):
+    w = maker()
+    if w.f is None:
+        w.f = mg.uniform(99, np.arange(w.ndof), -1, 1)
+    om = oracle.OracleMesh(w)
+    gm = _gpu(w, order=order)
+    dphi, vol = gm.shape_gradients()
+    # the precompute uses the same correctly rounded operations as the oracle
+    np.testing.assert_array_equal(vol, om.vol)
+    np.testing.assert_array_equal(dphi, om.dphi)
+    row_ptr, ent = gm.patches()
+    np.testing.assert_array_equal(row_ptr, om.row_ptr)
+    np.testing.assert_array_equal(ent, om.ent)
+    b = gm.load_vector()
+    if order == 0:
+        np.testing.assert_array_equal(b, om.b)
+    else:   # the patch order of a renumbered mesh can differ: sums in another order
+        np.testing.assert_allclose(b, om.b, rtol=1e-13, atol=1e-15 * np.abs(om.b).max())
+
+
+# ----------------------------------------------------------------------------------------
+# a2-a6: energy and exact gradient, FP64
+# ----------------------------------------------------------------------------------------
+
+def _parity(w, order=0, check_dens=True):
+    om = oracle.OracleMesh(w)
+    gm = _gpu(w, order=order)
+    v = _v(w)
+    J, dens = gm.energy(v, densities=True)
+    Jg, g = gm.energy_gradient(v)
+    g2 = gm.gradient_exact(v)
+    assert gm.sync_status() == 0
+    Jref, st, dref = om.energy(w.v, densities=True)
+    gref, st2 = om.gradient_exact(w.v)
+    assert st == st2 == oracle.OK
+    scale = energy_scale(om, w.v)
+    e1 = check_energy(J.item(), Jref, scale)
+    check_energy(Jg.item(), Jref, scale)
+    e2 = check_grad(g.cpu().numpy(), gref)
+    np.testing.assert_array_equal(g.cpu().numpy(), g2.cpu().numpy())
+    assert Jg.item() == J.item()
+    if check_dens:
+        np.testing.assert_allclose(dens.cpu().numpy(), dref, rtol=1e-9,
+                                   atol=1e-12 * np.abs(dref).max())
+    return e1, e2
+
+
+@pytest.mark.parametrize("seed,dim,model,n", [
+    (1, 2, mg.MODEL_PLAPLACE, (13, 11)), (2, 2, mg.MODEL_NEOHOOKE, (19, 23)),
+    (3, 3, mg.MODEL_NEOHOOKE, (7, 5, 9)), (4, 3, mg.MODEL_PLAPLACE, (6, 6, 5)),
+    (5, 2, mg.MODEL_NEOHOOKE, (1, 1)), (6, 3, mg.MODEL_NEOHOOKE, (1, 1, 1)),
+])
+@pytest.mark.parametrize("order", [0, 1])
+def test_random_meshes(seed, dim, model, n, order):
+    w = mg.random_small(seed, dim, model, *n)
+    _parity(w, order)
+
+
+@pytest.mark.parametrize("p", [1.5, 2.0, 3.0, 4.5])
+def test_plaplace_exponents(p):
+    w = mg.plaplace_square(17, p=p)
+    _parity(w)
+
+
+def test_c1_plaplace_64():
+    _parity(mg.plaplace_square(64))
+
+
+def test_shuffled_nodes_3d():
+    w = mg.shuffle_nodes(mg.neohooke_cube3d(9), seed=4)
+    _parity(w, order=0)
+    _parity(w, order=1)
+
+
+def test_c2_neohooke_2d_full():
+    """2D Neo-Hookean 1024x512x2 (1,048,576 triangles) with the benchmark's launch shape."""
+    w = mg.neohooke_rect2d()
+    _parity(w, check_dens=False)
+
+
+def test_c3_neohooke_3d_full():
+    """3D Neo-Hookean 128^3 x 6 (12,582,912 tetrahedra), energy and exact gradient against
+    the oracle on every dof, in the launch configuration of the benchmark."""
+    w = mg.neohooke_cube3d(128)
+    e1, e2 = _parity(w, check_dens=False)
+    print(f"C3 energy rel-to-condition {e1:.2e}, gradient rel {e2:.2e}")
+
+
+def test_twisted_bar_matches_table2():
+    """The GPU reproduces Benchmark 2 Table 2 (levels 1-3) to the printed 4 decimals."""
+    for level, ref in [(1, 12.6623), (2, 7.9083), (3, 6.7219)]:
+        w = mg.twisted_bar(level)
+        J = _gpu(w).energy(_v(w)).item()
+        assert abs(J - ref) <= 0.5e-4
+
+
+def test_deterministic_bitwise():
+    w = mg.neohooke_cube3d(24)
+    gm = _gpu(w)
+    v = _v(w)
+    J1, g1 = gm.energy_gradient(v)
+    J2, g2 = gm.energy_gradient(v)
+    assert J1.item() == J2.item()
+    assert torch.equal(g1, g2)
+
+
+# ----------------------------------------------------------------------------------------
+# edge cases
+# ----------------------------------------------------------------------------------------
+
+def test_no_elements_and_all_dirichlet():
+    w = mg.plaplace_square(4)
+    w0 = mg.Workload("empty", 2, 1, w.coords, np.zeros((0, 3), np.int32), w.dirichlet,
+                     mg.MODEL_PLAPLACE, p=3.0, f=None, v=w.v)
+    gm = _gpu(w0)
+    J, g = gm.energy_gradient(_v(w0))
+    assert J.item() == 0.0 and float(g.abs().max()) == 0.0
+    w.dirichlet[:] = 1
+    om = oracle.OracleMesh(w)
+    J, g = _gpu(w).energy_gradient(_v(w))
+    assert float(g.abs().max()) == 0.0
+    check_energy(J.item(), om.energy(w.v)[0], energy_scale(om, w.v))
+
+
+def test_inverted_element_reports_domain_error():
+    fem = _fem()
+    w = mg.neohooke_cube3d(3)
+    v = w.coords.ravel().copy()
+    v[3 * 21] += 2.0
+    w.v = v
+    gm = _gpu(w)
+    J = gm.energy(_v(w))
+    assert gm.sync_status() == fem.FE_EDOMAIN
+    assert J.item() == math.inf
+    assert gm.sync_status() == fem.FE_OK         # status is cleared
+    _, _, st = gm.energy_gradient_host(w.v)
+    assert st == fem.FE_EDOMAIN
+
+
+def test_bad_arguments_are_rejected():
+    fem = _fem()
+    w = mg.plaplace_square(4)
+    with pytest.raises(fem.FEError):
+        fem.FEMesh(2, 1, w.coords, np.array([[0, 1, 99]], np.int32), model=fem.FE_PLAPLACE, p=3.0)
+    with pytest.raises(fem.FEError):
+        fem.FEMesh(2, 1, w.coords, np.array([[0, 1, 1]], np.int32), model=fem.FE_PLAPLACE, p=3.0)
+    with pytest.raises(fem.FEError):   # Neo-Hookean needs d = dim
+        fem.FEMesh(2, 1, w.coords, w.elems, model=fem.FE_NEOHOOKE, C1=1.0, D1=1.0)
+    with pytest.raises(fem.FEError):   # degenerate element
+        c = np.array([[0, 0], [1, 0], [2, 0]], float)
+        fem.FEMesh(2, 1, c, np.array([[0, 1, 2]], np.int32), model=fem.FE_PLAPLACE, p=3.0)
+    gm = _gpu(w)
+    with pytest.raises(fem.FEError):
+        gm.gradient_fd(_v(w), -1.0)
+
+
+# ----------------------------------------------------------------------------------------
+# a7: central differences over patches
+# ----------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed,dim,model,n", [
+    (7, 2, mg.MODEL_PLAPLACE, (9, 7)), (8, 2, mg.MODEL_NEOHOOKE, (8, 9)),
+    (9, 3, mg.MODEL_NEOHOOKE, (4, 5, 3)),
+])
+@pytest.mark.parametrize("order", [0, 1])
+def test_fd_patch_gradient(seed, dim, model, n, order):
+    w = mg.random_small(seed, dim, model, *n)
+    om = oracle.OracleMesh(w)
+    gm = _gpu(w, order=order)
+    eps = 1e-6
+    gref, _ = om.gradient_fd(w.v, eps)
+    extra = fd_extra(om, w.v, eps)
+    check_grad(gm.gradient_fd(_v(w), eps).cpu().numpy(), gref, extra_abs=extra)
+    dofs = np.array([0, 3, w.ndof - 1, 5, 3], dtype=np.int64)
+    gs = gm.gradient_fd(_v(w), eps, dofs).cpu().numpy()
+    check_grad(gs, om.gradient_fd(w.v, eps, dofs)[0], extra_abs=extra)
+
+
+def test_c1_fd_full():
+    """2D p-Laplacian 64x64x2: central-difference gradient on every dof, eps = 1e-6."""
+    w = mg.plaplace_square(64)
+    om = oracle.OracleMesh(w)
+    g = _gpu(w).gradient_fd(_v(w), 1e-6).cpu().numpy()
+    gref, _ = om.gradient_fd(w.v, 1e-6)
+    check_grad(g, gref, extra_abs=fd_extra(om, w.v, 1e-6))
+
+
+def test_c3_fd_subset_10k():
+    """3D Neo-Hookean 128^3x6: central differences on 10^4 random free dofs (seed 2)
+    against the oracle, and against the exact gradient within O(eps^2) + rounding."""
+    w = mg.neohooke_cube3d(128)
+    free = np.flatnonzero(w.dirichlet == 0)
+    pick = np.argsort(mg.splitmix64(2, np.arange(free.size)))[:10000]
+    dofs = free[np.sort(pick)].astype(np.int64)
+    om = oracle.OracleMesh(w)
+    gm = _gpu(w)
+    v = _v(w)
+    g = gm.gradient_fd(v, 1e-6, dofs).cpu().numpy()
+    gref, _ = om.gradient_fd(w.v, 1e-6, dofs)
+    extra = fd_extra(om, w.v, 1e-6)
+    check_grad(g, gref, extra_abs=extra)
+    gex = gm.gradient_exact(v).cpu().numpy()[dofs]
+    check_grad(g, gex, rtol=1e-6, extra_abs=extra)
+
+
+# ----------------------------------------------------------------------------------------
+# a8: autograd
+# ----------------------------------------------------------------------------------------
+
+def test_autograd_backward_is_exact_gradient():
+    fem = _fem()
+    w = mg.random_small(31, 3, mg.MODEL_NEOHOOKE, 5, 4, 3)
+    gm = _gpu(w)
+    v = _v(w).requires_grad_(True)
+    J = fem.energy(v, gm)
+    J.backward()
+    gref, _ = oracle.OracleMesh(w).gradient_exact(w.v)
+    check_grad(v.grad.cpu().numpy(), gref)
+    v.grad = None
+    (3.0 * fem.energy(v, gm)).backward()
+    check_grad(v.grad.cpu().numpy(), 3.0 * gref)
+
+
+def test_autograd_gradcheck_free_dofs():
+    fem = _fem()
+    w = mg.random_small(37, 2, mg.MODEL_NEOHOOKE, 3, 2)
+    gm = _gpu(w)
+    free = torch.from_numpy(np.flatnonzero(w.dirichlet == 0)).cuda()
+    base = _v(w)
+
+    def f(x):
+        full = base.clone().index_put((free,), x)
+        return fem.energy(full, gm)
+
+    x = base[free].clone().requires_grad_(True)
+    assert torch.autograd.gradcheck(f, (x,), eps=1e-6, atol=1e-5, rtol=1e-4)
+
+
+# ----------------------------------------------------------------------------------------
+# a9: FP32 element arithmetic with compensated reductions
+# ----------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("maker,jtol,gtol", [
+    (lambda: mg.neohooke_rect2d(256, 128), 2e-6, 2e-5),
+    (lambda: mg.neohooke_cube3d(32), 2e-6, 2e-5),
+    (lambda: mg.plaplace_square(64), 2e-6, 2e-5),
+])
+def test_fp32_compensated_error(maker, jtol, gtol):
+    fem = _fem()
+    w = maker()
+    om = oracle.OracleMesh(w)
+    gm = _gpu(w, precisions=(fem.FE_F32_COMP, fem.FE_F64))
+    J, g = gm.energy_gradient(_v(w))
+    Jref, _ = om.energy(w.v)
+    gref, _ = om.gradient_exact(w.v)
+    ej = check_energy(J.item(), Jref, energy_scale(om, w.v), rtol=jtol)
+    eg = check_grad(g.cpu().numpy(), gref, rtol=gtol)
+    print(f"{w.name}: FP32-comp energy err/condition {ej:.2e}, gradient rel {eg:.2e}")
+    gm.set_precision(fem.FE_F64)
+    J64, _ = gm.energy_gradient(_v(w))
+    check_energy(J64.item(), Jref, energy_scale(om, w.v))
+
+
+# ----------------------------------------------------------------------------------------
+# end-to-end host call
+# ----------------------------------------------------------------------------------------
+
+def test_host_call_matches_device_call():
+    w = mg.neohooke_cube3d(16)
+    gm = _gpu(w)
+    J, g = gm.energy_gradient(_v(w))
+    Jh, gh, st = gm.energy_gradient_host(w.v)
+    assert st == 0
+    assert Jh == J.item()
+    np.testing.assert_array_equal(gh, g.cpu().numpy())
