@@ -128,6 +128,23 @@ def test_c2_neohooke_2d_full():
     _parity(w, check_dens=False)
 
 
+def test_c2_literal_noise_folds_the_same_elements():
+    """With U[-1e-3,1e-3] noise (51% of the spacing) the 1024x512x2 mesh folds: GPU and oracle
+    find exactly the same inverted triangles (W = +Inf), J = +Inf and FE_EDOMAIN."""
+    fem = _fem()
+    w = mg.neohooke_rect2d(noise=1e-3)
+    om = oracle.OracleMesh(w)
+    Jref, st, dref = om.energy(w.v, densities=True)
+    assert st == oracle.EDOMAIN and Jref == math.inf
+    gm = _gpu(w)
+    J, dens = gm.energy(_v(w), densities=True)
+    assert gm.sync_status() == fem.FE_EDOMAIN
+    assert J.item() == math.inf
+    bad_gpu = np.isinf(dens.cpu().numpy())
+    np.testing.assert_array_equal(bad_gpu, np.isinf(dref))
+    assert int(bad_gpu.sum()) == 28819
+
+
 def test_c3_neohooke_3d_full():
     """3D Neo-Hookean 128^3 x 6 (12,582,912 tetrahedra), energy and exact gradient against
     the oracle on every dof, in the launch configuration of the benchmark."""
