@@ -177,6 +177,32 @@ fe_status fe_launch_count(const fe_ctx* ctx, int64_t* count);
 fe_status fe_profile_enable(fe_ctx* ctx, int enable);
 fe_status fe_profile_read(fe_ctx* ctx, double* ms_host, int64_t* launches_host, int n_stages);
 
+
+/* Energy without any allocation (the paper has no counterpart: this is an interface for
+ * callers that cannot let this library allocate device memory -- a host program whose GPU
+ * memory is owned entirely by its own pool allocator, or one whose time-critical loop must
+ * not call cudaMalloc, which can synchronise the device).  It evaluates the same
+ * J = sum_k |T_k| W(F_k) - b.v as fe_energy, needs no context and no fe_precompute, and
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   device, cuda_stream   the device holding every array, and the stream to enqueue on
+ *   dim, d, model, p, C1, D1   as in fe_mesh_upload / fe_set_model
+ *   coords_dev  n_nodes*dim doubles;  elems_dev  n_elems*(dim+1) int32 (caller layouts of
+ *               fe_mesh_upload, on the device)
+ *   dphi_dev    n_elems*(dim+1)*dim doubles, vol_dev n_elems doubles: the shape gradients
+ *               and volumes in the layout fe_get_shape_gradients returns
+ *   b_dev       NULL or n_nodes*d doubles (b = M f);  v_dev  n_nodes*d doubles
+ *   J_dev       one double receiving J (+Inf if some det F <= 0)
+ * Its only scratch (block partial sums and a ticket, 19,472 bytes) is a static device array
+ * that every GPU loading the library keeps until the process exits.  The first call on a
+ * device looks up that array's address; make it before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race and must be serialised by the
+ * caller.  Sizes beyond the maximum (n_elems*(dim+1) >= 2^31 or n_nodes*d >= 2^31) are
+ * rejected with FE_EINVAL. */
+fe_status fe_energy_noalloc(int device, void* cuda_stream, int dim, int d, int model, double p,
+                            double C1, double D1, int64_t n_nodes, const double* coords_dev,
+                            int64_t n_elems, const int32_t* elems_dev, const double* dphi_dev,
+                            const double* vol_dev, const double* b_dev, const double* v_dev,
+                            double* J_dev);
 #ifdef __cplusplus
 }
 #endif

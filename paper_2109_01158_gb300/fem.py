@@ -64,6 +64,8 @@ _SIGNATURES = {
     "fe_launch_count": [_vp, _vp],
     "fe_profile_enable": [_vp, _int],
     "fe_profile_read": [_vp, _vp, _vp, _int],
+    "fe_energy_noalloc": [_int, _vp, _int, _int, _int, _dbl, _dbl, _dbl, _i64, _vp, _i64, _vp, _vp,
+                          _vp, _vp, _vp, _vp],
 }
 _RESTYPE = {"fe_version": ctypes.c_int, "fe_last_error": ctypes.c_char_p}
 
@@ -131,6 +133,7 @@ fe_get_load_vector = _checked("fe_get_load_vector")
 fe_launch_count = _checked("fe_launch_count")
 fe_profile_enable = _checked("fe_profile_enable")
 fe_profile_read = _checked("fe_profile_read")
+fe_energy_noalloc = _checked("fe_energy_noalloc")
 
 FE_PROFILE_STAGES = 5
 PROFILE_STAGE_NAMES = ("node_prep", "element", "gather", "fd_element", "fd_gather")
