@@ -105,8 +105,9 @@ fe_status fe_set_load(fe_ctx* ctx, const double* f_host);
 /* Per-mesh precompute on the device (Sec. 4.1-4.2, done once per mesh): element volumes
  * |T| and shape-function gradients dphi, the nodal-patch CSR (node -> (element, local
  * index)) in increasing element order, b = M f, and the device buffers of the requested
- * precisions.  precisions: bit mask, 1 << FE_F64 and/or 1 << FE_F32_COMP.  The first
- * requested precision becomes the active one.  FE_EINVAL if an element is degenerate. */
+ * precisions.  precisions: bit mask, 1 << FE_F64 and/or 1 << FE_F32_COMP.  FE_F64 becomes
+ * the active precision when it is in the mask, FE_F32_COMP otherwise; fe_set_precision
+ * switches between precomputed ones.  FE_EINVAL if an element is degenerate. */
 fe_status fe_precompute(fe_ctx* ctx, unsigned precisions);
 
 /* Choose the arithmetic of later evaluation calls (must have been precomputed). */

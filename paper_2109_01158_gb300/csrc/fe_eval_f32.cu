@@ -87,6 +87,31 @@ __device__ __forceinline__ float phi_series(float x) {
   return fmaf(s, x, -2.0f * s * s2 * t);
 }
 
+// det F, 2 (delta - log det F) and 1 / det F in FP64 from the float entries of H (F = I + H);
+// returns false if det F <= 0.
+__device__ __noinline__ bool far_from_identity_f64(const float* Hf, int dim, float* delta, float* phi2,
+                                                   float* inv_det) {
+  double detd;
+  if (dim == 3) {
+    const double F00 = 1.0 + Hf[0], F11 = 1.0 + Hf[4], F22 = 1.0 + Hf[8];
+    const double H01 = Hf[1], H02 = Hf[2], H10 = Hf[3], H12 = Hf[5], H20 = Hf[6], H21 = Hf[7];
+    detd = F00 * (F11 * F22 - H12 * H21) + H01 * (H12 * H20 - H10 * F22) + H02 * (H10 * H21 - F11 * H20);
+  } else {
+    detd = (1.0 + Hf[0]) * (1.0 + Hf[3]) - (double)Hf[1] * (double)Hf[2];
+  }
+  if (!(detd > 0.0)) {
+    *delta = 0.f;
+    *phi2 = 0.f;
+    *inv_det = 1.f;
+    return false;
+  }
+  const double dd = detd - 1.0;
+  *delta = (float)dd;
+  *phi2 = (float)(2.0 * (dd - log(detd)));
+  *inv_det = (float)(1.0 / detd);
+  return true;
+}
+
 template <int D>
 __device__ __forceinline__ void load_u32(const float* __restrict__ u, int32_t n, float* out) {
   if (D == 1) {
@@ -213,32 +238,20 @@ __global__ void __launch_bounds__(kThreads) k_elem_f32(
       bool ebad = false;
       float phi2;      // 2 phi(delta)
       float inv_det;   // 1 / det F
-      if (fabsf(delta) <= 0.5f) {
+      const bool far = !(fabsf(delta) <= 0.5f);
+      if (!far) {
         phi2 = 2.f * phi_series(delta);
         inv_det = 1.f / (1.f + delta);
-      } else {
-        // far from F = I: det F and log det F in FP64 from the float entries of H
-        double Hd[DIM][DIM];
+      }
+      // Far from F = I: det F and log det F in FP64, in a called function behind a warp
+      // vote so that the compiler cannot if-convert it into every element's path.
+      if (__any_sync(__activemask(), far) && far) {
+        float Hf[9];
 #pragma unroll
         for (int j = 0; j < DIM; ++j)
 #pragma unroll
-          for (int m = 0; m < DIM; ++m) Hd[j][m] = (double)H[j][m];
-        double detd;
-        if (DIM == 3) {
-          const double F00 = 1.0 + Hd[0][0], F11 = 1.0 + Hd[1][1], F22 = 1.0 + Hd[2][2];
-          detd = F00 * (F11 * F22 - Hd[1][2] * Hd[2][1]) + Hd[0][1] * (Hd[1][2] * Hd[2][0] - Hd[1][0] * F22) +
-                 Hd[0][2] * (Hd[1][0] * Hd[2][1] - F11 * Hd[2][0]);
-        } else {
-          detd = (1.0 + Hd[0][0]) * (1.0 + Hd[1][1]) - Hd[0][1] * Hd[1][0];
-        }
-        if (!(detd > 0.0)) {
-          ebad = true;
-          detd = 1.0;
-        }
-        const double dd = detd - 1.0;
-        delta = (float)dd;
-        phi2 = (float)(2.0 * (dd - log(detd)));
-        inv_det = (float)(1.0 / detd);
+          for (int m = 0; m < DIM; ++m) Hf[j * DIM + m] = H[j][m];
+        ebad = !far_from_identity_f64(Hf, DIM, &delta, &phi2, &inv_det);
       }
       if (ENERGY || DENS) W = C1 * (hsq - 2.f * (i2 + dH) + phi2) + D1 * delta * delta;
       if (ebad) {

@@ -189,6 +189,7 @@ class FEMesh:
         for prec in precisions:
             mask |= 1 << int(prec)
         fe_precompute(self.ctx, mask)
+        fe_set_precision(self.ctx, int(precisions[0]))
         self.precision = int(precisions[0])
 
     @classmethod

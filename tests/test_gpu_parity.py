@@ -317,12 +317,14 @@ def test_fp32_compensated_error(maker, jtol, gtol):
     w = maker()
     om = oracle.OracleMesh(w)
     gm = _gpu(w, precisions=(fem.FE_F32_COMP, fem.FE_F64))
+    assert gm.precision == fem.FE_F32_COMP
     J, g = gm.energy_gradient(_v(w))
     Jref, _ = om.energy(w.v)
     gref, _ = om.gradient_exact(w.v)
     ej = check_energy(J.item(), Jref, energy_scale(om, w.v), rtol=jtol)
     eg = check_grad(g.cpu().numpy(), gref, rtol=gtol)
     print(f"{w.name}: FP32-comp energy err/condition {ej:.2e}, gradient rel {eg:.2e}")
+    assert eg > 1e-12, "the FP32 path returned FP64-accurate gradients: wrong kernel ran"
     gm.set_precision(fem.FE_F64)
     J64, _ = gm.energy_gradient(_v(w))
     check_energy(J64.item(), Jref, energy_scale(om, w.v))
