@@ -36,6 +36,8 @@ FALLBACK_HBM_GBS = 6800.0
 ELEM_BYTES = {  # (dim, precision) -> (bytes per element, bytes per node)
     (3, "f64"): (12 * 8 + 8 + 4 * 4, 24),
     (2, "f64"): (6 * 8 + 8 + 3 * 4, 16),
+    (3, "df64"): (12 * 8 + 8 + 4 * 4, 24),
+    (2, "df64"): (6 * 8 + 8 + 3 * 4, 16),
     (3, "f32"): (12 * 4 + 4 + 4 * 4, 12),
     (2, "f32"): (6 * 4 + 4 + 3 * 4, 8),
 }
@@ -222,7 +224,9 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = mg.config_workload(args.workload)
-    precs = (fem.FE_F64, fem.FE_F32_COMP) if args.precision == "f64" else (fem.FE_F32_COMP, fem.FE_F64)
+    code = {"f64": fem.FE_F64, "f32": fem.FE_F32_COMP, "df64": fem.FE_DF64}
+    others = [k for k in ("df64", "f64", "f32") if k != args.precision]
+    precs = tuple(code[k] for k in [args.precision] + others)
     gm = fem.FEMesh.from_workload(w, device=local, order=args.order, precisions=precs)
     v = torch.from_numpy(w.v).to(dev)
     J = torch.empty((), dtype=torch.float64, device=dev)
@@ -306,17 +310,19 @@ def run_ours(args, rank, world, local):
            "h2d_bytes_per_step": w.ndof * 8, "d2h_bytes_per_step": w.ndof * 8 + 8,
            "api": "fe_energy_gradient_host"}
 
-    # other precision (same mesh), for context
-    other = "f32" if prec == "f64" else "f64"
-    gm.set_precision(fem.FE_F32_COMP if other == "f32" else fem.FE_F64)
-    steps(3)
-    oms, _, oprof = timed(max(5, args.steps // 4), profile=True)
-    o_elem = oprof["element"][0] / max(oprof["element"][1], 1)
-    ob, on = ELEM_BYTES[(w.dim, other)]
-    variants = {other: {"value": w.ne * max(5, args.steps // 4) / (oms / 1e3) / 1e9, "unit": "Gelem/s",
-                        "element_kernel_ms": o_elem,
-                        "element_hbm_frac": (w.ne * ob + w.nn * on) / (o_elem / 1e3) / 1e9 / hbm_peak}}
-    gm.set_precision(fem.FE_F64 if prec == "f64" else fem.FE_F32_COMP)
+    # the other precisions (same mesh), for context
+    variants = {}
+    for other in others:
+        gm.set_precision(code[other])
+        steps(3)
+        nst = max(5, args.steps // 4)
+        oms, _, oprof = timed(nst, profile=True)
+        o_elem = oprof["element"][0] / max(oprof["element"][1], 1)
+        ob, on = ELEM_BYTES[(w.dim, other)]
+        variants[other] = {"value": w.ne * nst / (oms / 1e3) / 1e9, "unit": "Gelem/s",
+                           "ms_per_step": oms / nst, "element_kernel_ms": o_elem,
+                           "element_hbm_frac": (w.ne * ob + w.nn * on) / (o_elem / 1e3) / 1e9 / hbm_peak}
+    gm.set_precision(code[prec])
 
     line = {
         "metric": "energy+grad throughput", "value": value, "unit": "Gelem/s", "n_gpus": world,
@@ -349,7 +355,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="C3")
-    ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--precision", choices=["f64", "f32", "df64"], default="f64")
     ap.add_argument("--order", type=int, default=0, help="0 generator order, 1 Morton")
     ap.add_argument("--sample-fraction", type=float, default=0.125)
     ap.add_argument("--no-cpu-baseline", action="store_true")

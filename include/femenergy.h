@@ -51,11 +51,15 @@ typedef enum {
 
 typedef enum { FE_PLAPLACE = 0, FE_NEOHOOKE = 1 } fe_model;
 
-/* Arithmetic of the element kernels.  FE_F64: IEEE double throughout.  FE_F32_COMP:
- * per-element float arithmetic in displacement form with double-precision patch sums and
- * compensated double-precision energy reductions (not in the paper; its error against the
- * FP64 result is reported per result by the caller's tests). */
-typedef enum { FE_F64 = 0, FE_F32_COMP = 1 } fe_precision;
+/* Arithmetic of the element kernels (none is prescribed by the paper, which runs MATLAB
+ * doubles).  FE_F64: IEEE double throughout.  FE_F32_COMP: per-element float arithmetic in
+ * displacement form with double-precision patch sums and compensated double-precision energy
+ * reductions; its error against the FP64 result is of float order (about 1e-7 relative).
+ * FE_DF64: every per-element operation in double-float arithmetic (pairs of floats, about
+ * 48 significand bits) on the FP32 pipes, with FP64 block and grid reductions; meets the
+ * FP64 tolerances (energy 1e-12 of its condition number, gradient 1e-10 of its max norm)
+ * for values within about 1e-30..1e30 in magnitude. */
+typedef enum { FE_F64 = 0, FE_F32_COMP = 1, FE_DF64 = 2 } fe_precision;
 
 /* Internal node/element numbering used for the device layout (invisible to callers). */
 typedef enum { FE_ORDER_NONE = 0, FE_ORDER_MORTON = 1 } fe_order;
@@ -105,9 +109,10 @@ fe_status fe_set_load(fe_ctx* ctx, const double* f_host);
 /* Per-mesh precompute on the device (Sec. 4.1-4.2, done once per mesh): element volumes
  * |T| and shape-function gradients dphi, the nodal-patch CSR (node -> (element, local
  * index)) in increasing element order, b = M f, and the device buffers of the requested
- * precisions.  precisions: bit mask, 1 << FE_F64 and/or 1 << FE_F32_COMP.  FE_F64 becomes
- * the active precision when it is in the mask, FE_F32_COMP otherwise; fe_set_precision
- * switches between precomputed ones.  FE_EINVAL if an element is degenerate. */
+ * precisions.  precisions: bit mask of 1 << FE_F64, 1 << FE_F32_COMP, 1 << FE_DF64.  The
+ * active precision becomes FE_F64 if it is in the mask, else FE_DF64, else FE_F32_COMP;
+ * fe_set_precision switches between precomputed ones.  The central-difference gradient needs
+ * FE_F64.  FE_EINVAL if an element is degenerate. */
 fe_status fe_precompute(fe_ctx* ctx, unsigned precisions);
 
 /* Choose the arithmetic of later evaluation calls (must have been precomputed). */
@@ -163,6 +168,11 @@ fe_status fe_get_patches(fe_ctx* ctx, int64_t* row_ptr_host, int64_t* ent_host);
 
 /* Read back b = M f in dof order (synchronous, host output of n_nodes*d doubles). */
 fe_status fe_get_load_vector(fe_ctx* ctx, double* b_host);
+
+/* Diagnostic: y_dev[i] = log(x_dev[i]) computed by the double-float logarithm of the
+ * FE_DF64 kernels (x > 0, n doubles, device), so that its accuracy can be checked against a
+ * reference logarithm.  Needs the FE_DF64 precompute. */
+fe_status fe_diag_df64_log(fe_ctx* ctx, const double* x_dev, double* y_dev, int64_t n);
 
 /* Number of kernels this context has launched since creation (instrumentation). */
 fe_status fe_launch_count(const fe_ctx* ctx, int64_t* count);

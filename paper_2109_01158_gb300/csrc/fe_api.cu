@@ -92,6 +92,11 @@ void free_precompute(fe_ctx* c) {
   dev_free(c, &c->b, nn * c->d);
   dev_free(c, &c->dphi32, ne * c->dim * c->dim);
   dev_free(c, &c->vol32, ne);
+  dev_free(c, &c->dphi_df, ne * c->dim * c->dim);
+  dev_free(c, &c->vol_df, ne);
+  dev_free(c, &c->log_tab, kLogTable);
+  dev_free(c, &c->u_df, nn * padded_d(c->d));
+  dev_free(c, &c->r_df, ne * k * c->d);
   dev_free(c, &c->u, nn * padded_d(c->d));
   dev_free(c, &c->u32, nn * padded_d(c->d));
   dev_free(c, &c->r, ne * k * c->d);
@@ -163,6 +168,7 @@ fe_status check_ready(fe_ctx* c, bool need_model = true) {
 fe_status eval(fe_ctx* c, const double* v, double* J, double* dens, double* g, bool want_energy,
                bool want_grad) {
   if (c->precision == FE_F32_COMP) return launch_eval_f32(c, v, J, dens, g, want_energy, want_grad);
+  if (c->precision == FE_DF64) return launch_eval_df64(c, v, J, dens, g, want_energy, want_grad);
   return launch_eval_f64(c, v, J, dens, g, want_energy, want_grad);
 }
 
@@ -360,7 +366,7 @@ fe_status fe_set_load(fe_ctx* c, const double* f_host) {
 fe_status fe_precompute(fe_ctx* c, unsigned precisions) {
   if (!c) return set_error(FE_EINVAL, "null context");
   if (!c->have_mesh) return set_error(FE_EINVAL, "no mesh uploaded");
-  if (precisions == 0 || (precisions & ~3u)) return set_error(FE_EINVAL, "bad precision mask");
+  if (precisions == 0 || (precisions & ~7u)) return set_error(FE_EINVAL, "bad precision mask");
   DeviceGuard g(c->device);
   if (!g.ok) return set_error(FE_ECUDA, "cudaSetDevice failed");
   cudaStreamSynchronize(c->stream);
@@ -387,9 +393,18 @@ fe_status fe_precompute(fe_ctx* c, unsigned precisions) {
       return st;
     }
   }
+  if (precisions & (1u << FE_DF64)) {
+    if ((st = dev_alloc(c, &c->dphi_df, ne * c->dim * c->dim)) || (st = dev_alloc(c, &c->vol_df, ne)) ||
+        (st = dev_alloc(c, &c->log_tab, kLogTable)) || (st = dev_alloc(c, &c->u_df, nn * dp)) ||
+        (st = dev_alloc(c, &c->r_df, ne * k * c->d))) {
+      free_precompute(c);
+      return st;
+    }
+  }
   c->pre_mask = precisions;
   cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
-  if ((st = launch_precompute(c)) || (st = launch_load_vector(c))) {
+  if ((st = launch_precompute(c)) || (st = launch_load_vector(c)) ||
+      ((precisions & (1u << FE_DF64)) && (st = launch_precompute_df(c)))) {
     free_precompute(c);
     return st;
   }
@@ -405,13 +420,14 @@ fe_status fe_precompute(fe_ctx* c, unsigned precisions) {
     return set_error(FE_EINVAL, "degenerate element (zero volume)");
   }
   c->have_pre = true;
-  c->precision = (precisions & 1u) ? FE_F64 : FE_F32_COMP;
+  c->precision = (precisions & 1u) ? FE_F64 : (precisions & 4u) ? FE_DF64 : FE_F32_COMP;
   return FE_OK;
 }
 
 fe_status fe_set_precision(fe_ctx* c, int precision) {
   if (!c) return set_error(FE_EINVAL, "null context");
-  if (precision != FE_F64 && precision != FE_F32_COMP) return set_error(FE_EINVAL, "bad precision");
+  if (precision != FE_F64 && precision != FE_F32_COMP && precision != FE_DF64)
+    return set_error(FE_EINVAL, "bad precision");
   if (!c->have_pre || !(c->pre_mask & (1u << precision)))
     return set_error(FE_EINVAL, "precision was not precomputed");
   c->precision = precision;
@@ -588,6 +604,15 @@ fe_status fe_profile_read(fe_ctx* c, double* ms, int64_t* launches, int n_stages
   }
   for (int k = 0; k < FE_PROFILE_STAGES; ++k) c->prof_n[k] = 0;
   return FE_OK;
+}
+
+fe_status fe_diag_df64_log(fe_ctx* c, const double* x, double* y, int64_t n) {
+  fe_status st = check_ready(c, false);
+  if (st) return st;
+  if (!c->log_tab) return set_error(FE_EINVAL, "needs the FE_DF64 precompute");
+  if (n < 0 || (n > 0 && (!x || !y))) return set_error(FE_EINVAL, "bad arguments");
+  DeviceGuard g(c->device);
+  return launch_diag_df_log(c->log_tab, x, y, n, c->stream);
 }
 
 fe_status fe_launch_count(const fe_ctx* c, int64_t* count) {

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "df64.cuh"
 #include "femenergy.h"
 
 namespace fe {
@@ -75,12 +76,17 @@ struct fe_ctx {
   double* b = nullptr;         // nn*d, device order
   float* dphi32 = nullptr;     // FP32 copy of dphi
   float* vol32 = nullptr;      // FP32 copy of vol
+  float2* dphi_df = nullptr;   // double-float copy of dphi (hi, lo)
+  float2* vol_df = nullptr;    // double-float copy of vol
+  fe::LogEntry* log_tab = nullptr;  // table of the double-float logarithm
 
   // device: work buffers
   double* u = nullptr;         // nn*padded_d(d): displacement (Neo-Hookean) or v
   float* u32 = nullptr;        // nn*padded_d(d), FP32 displacement
   double* r = nullptr;         // ne*(dim+1)*d slot-ordered local forces (x2 for FD)
   float* r32 = nullptr;        // ne*(dim+1)*d, FP32 local forces
+  float2* u_df = nullptr;      // nn*padded_d(d) double-float displacement
+  float2* r_df = nullptr;      // ne*(dim+1)*d double-float local forces
   double* partials = nullptr;  // element partials [kMaxElemBlocks] then node partials
   unsigned* counter = nullptr; // last-block ticket
   int* status = nullptr;       // device status bits
@@ -113,6 +119,12 @@ fe_status launch_eval_f64(fe_ctx* c, const double* v, double* J, double* dens, d
 fe_status launch_fd_f64(fe_ctx* c, const double* v, double eps, double* g,
                         const int64_t* dofs, int64_t ndofs);
 fe_status launch_expand_dphi(fe_ctx* c, double* dphi_full, double* vol_user);
+
+// fe_eval_df64.cu
+fe_status launch_precompute_df(fe_ctx* c);
+fe_status launch_eval_df64(fe_ctx* c, const double* v, double* J, double* dens, double* g,
+                           bool want_energy, bool want_grad);
+fe_status launch_diag_df_log(const LogEntry* tab, const double* x, double* y, int64_t n, cudaStream_t s);
 
 // fe_eval_f32.cu
 fe_status launch_eval_f32(fe_ctx* c, const double* v, double* J, double* dens, double* g,

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libfemenergy.so")
 
 FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_EDOMAIN, FE_ETIMEOUT, FE_EBUSY = range(7)
 FE_PLAPLACE, FE_NEOHOOKE = 0, 1
-FE_F64, FE_F32_COMP = 0, 1
+FE_F64, FE_F32_COMP, FE_DF64 = 0, 1, 2
 FE_ORDER_NONE, FE_ORDER_MORTON = 0, 1
 
 _STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "FE_EDOMAIN",
@@ -64,6 +64,7 @@ _SIGNATURES = {
     "fe_launch_count": [_vp, _vp],
     "fe_profile_enable": [_vp, _int],
     "fe_profile_read": [_vp, _vp, _vp, _int],
+    "fe_diag_df64_log": [_vp, _vp, _vp, _i64],
     "fe_energy_noalloc": [_int, _vp, _int, _int, _int, _dbl, _dbl, _dbl, _i64, _vp, _i64, _vp, _vp,
                           _vp, _vp, _vp, _vp],
 }
@@ -134,6 +135,7 @@ fe_launch_count = _checked("fe_launch_count")
 fe_profile_enable = _checked("fe_profile_enable")
 fe_profile_read = _checked("fe_profile_read")
 fe_energy_noalloc = _checked("fe_energy_noalloc")
+fe_diag_df64_log = _checked("fe_diag_df64_log")
 
 FE_PROFILE_STAGES = 5
 PROFILE_STAGE_NAMES = ("node_prep", "element", "gather", "fd_element", "fd_gather")
@@ -282,6 +284,14 @@ class FEMesh:
         b = np.empty(self.ndof)
         fe_get_load_vector(self.ctx, _ptr(b))
         return b
+
+    def diag_df64_log(self, x):
+        """log(x) by the double-float logarithm of the FE_DF64 kernels (diagnostic)."""
+        x = torch.as_tensor(x, dtype=torch.float64).to(self.device).contiguous()
+        y = torch.empty_like(x)
+        self._sync_stream()
+        fe_diag_df64_log(self.ctx, _ptr(x), _ptr(y), x.numel())
+        return y
 
     def footprint(self) -> int:
         n = ctypes.c_size_t(0)

@@ -72,9 +72,9 @@ def test_precompute_patches_and_load_vector(maker, order):
 # a2-a6: energy and exact gradient, FP64
 # ----------------------------------------------------------------------------------------
 
-def _parity(w, order=0, check_dens=True):
+def _parity(w, order=0, check_dens=True, precision=0):
     om = oracle.OracleMesh(w)
-    gm = _gpu(w, order=order)
+    gm = _gpu(w, order=order, precisions=(precision,))
     v = _v(w)
     J, dens = gm.energy(v, densities=True)
     Jg, g = gm.energy_gradient(v)
@@ -101,31 +101,37 @@ def _parity(w, order=0, check_dens=True):
     (5, 2, mg.MODEL_NEOHOOKE, (1, 1)), (6, 3, mg.MODEL_NEOHOOKE, (1, 1, 1)),
 ])
 @pytest.mark.parametrize("order", [0, 1])
-def test_random_meshes(seed, dim, model, n, order):
+@pytest.mark.parametrize("precision", [0, 2], ids=["f64", "df64"])
+def test_random_meshes(seed, dim, model, n, order, precision):
     w = mg.random_small(seed, dim, model, *n)
-    _parity(w, order)
+    _parity(w, order, precision=precision)
 
 
-@pytest.mark.parametrize("p", [1.5, 2.0, 3.0, 4.5])
-def test_plaplace_exponents(p):
+@pytest.mark.parametrize("p", [1.5, 2.0, 3.0, 4.0, 4.5])
+@pytest.mark.parametrize("precision", [0, 2], ids=["f64", "df64"])
+def test_plaplace_exponents(p, precision):
     w = mg.plaplace_square(17, p=p)
-    _parity(w)
+    _parity(w, precision=precision)
 
 
-def test_c1_plaplace_64():
-    _parity(mg.plaplace_square(64))
+@pytest.mark.parametrize("precision", [0, 2], ids=["f64", "df64"])
+def test_c1_plaplace_64(precision):
+    _parity(mg.plaplace_square(64), precision=precision)
 
 
-def test_shuffled_nodes_3d():
+@pytest.mark.parametrize("precision", [0, 2], ids=["f64", "df64"])
+def test_shuffled_nodes_3d(precision):
     w = mg.shuffle_nodes(mg.neohooke_cube3d(9), seed=4)
-    _parity(w, order=0)
-    _parity(w, order=1)
+    _parity(w, order=0, precision=precision)
+    _parity(w, order=1, precision=precision)
 
 
-def test_c2_neohooke_2d_full():
+@pytest.mark.parametrize("precision", [0, 2], ids=["f64", "df64"])
+def test_c2_neohooke_2d_full(precision):
     """2D Neo-Hookean 1024x512x2 (1,048,576 triangles) with the benchmark's launch shape."""
     w = mg.neohooke_rect2d()
-    _parity(w, check_dens=False)
+    e1, e2 = _parity(w, check_dens=False, precision=precision)
+    print(f"C2 precision {precision}: energy err/condition {e1:.2e}, gradient rel {e2:.2e}")
 
 
 def test_c2_literal_noise_folds_the_same_elements():
@@ -145,12 +151,41 @@ def test_c2_literal_noise_folds_the_same_elements():
     assert int(bad_gpu.sum()) == 28819
 
 
-def test_c3_neohooke_3d_full():
+@pytest.mark.parametrize("precision", [0, 2], ids=["f64", "df64"])
+def test_c3_neohooke_3d_full(precision):
     """3D Neo-Hookean 128^3 x 6 (12,582,912 tetrahedra), energy and exact gradient against
     the oracle on every dof, in the launch configuration of the benchmark."""
     w = mg.neohooke_cube3d(128)
-    e1, e2 = _parity(w, check_dens=False)
-    print(f"C3 energy rel-to-condition {e1:.2e}, gradient rel {e2:.2e}")
+    e1, e2 = _parity(w, check_dens=False, precision=precision)
+    print(f"C3 precision {precision}: energy err/condition {e1:.2e}, gradient rel {e2:.2e}")
+
+
+def test_twisted_bar_df64_levels():
+    """Double-float energies of Benchmark 2 (E = 2e8, volumes down to 1e-10) against the
+    oracle at the FP64 tolerance, levels 1-4."""
+    fem = _fem()
+    for level in (1, 2, 3, 4):
+        w = mg.twisted_bar(level)
+        om = oracle.OracleMesh(w)
+        gm = _gpu(w, precisions=(fem.FE_DF64,))
+        J, g = gm.energy_gradient(_v(w))
+        check_energy(J.item(), om.energy(w.v)[0], energy_scale(om, w.v))
+        check_grad(g.cpu().numpy(), om.gradient_exact(w.v)[0])
+
+
+def test_df64_log_accuracy():
+    """The double-float logarithm of the FE_DF64 kernels against numpy's FP64 log:
+    |y - log x| <= 2^-47 |log x| + 2^-51 over 12 decades and around 1."""
+    fem = _fem()
+    w = mg.neohooke_cube3d(2)
+    gm = _gpu(w, precisions=(fem.FE_DF64,))
+    u = mg.uniform(5, np.arange(200000), 0.0, 1.0)
+    x = np.concatenate([10.0 ** (12 * u - 6), 1.0 + (u - 0.5) * 1e-3, 1.0 + (u - 0.5) * 1e-9,
+                        0.5 + 1.5 * u, [1.0, 2.0, 0.5, 1.4142135, 0.70710678, 1.0 + 2.0 ** -30]])
+    y = gm.diag_df64_log(torch.from_numpy(x)).cpu().numpy()
+    ref = np.log(x)
+    err = np.abs(y - ref) / (2.0 ** -47 * np.abs(ref) + 2.0 ** -51)
+    assert err.max() <= 1.0, (err.max(), x[err.argmax()])
 
 
 def test_twisted_bar_matches_table2():
@@ -161,9 +196,10 @@ def test_twisted_bar_matches_table2():
         assert abs(J - ref) <= 0.5e-4
 
 
-def test_deterministic_bitwise():
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["f64", "f32", "df64"])
+def test_deterministic_bitwise(precision):
     w = mg.neohooke_cube3d(24)
-    gm = _gpu(w)
+    gm = _gpu(w, precisions=(precision,))
     v = _v(w)
     J1, g1 = gm.energy_gradient(v)
     J2, g2 = gm.energy_gradient(v)
