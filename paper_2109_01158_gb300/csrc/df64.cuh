@@ -29,30 +29,38 @@ struct df {
   float hi, lo;
 };
 
+// Every addition and multiplication inside the error-free transformations below is written
+// with the _rn intrinsics: nvcc would otherwise fuse a product into a following sum (FMA
+// contraction), which breaks the exactness of TwoSum / FastTwoSum and makes the result
+// depend on how the compiler schedules each kernel.
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+
 __device__ __forceinline__ df df_from(float a) { return {a, 0.f}; }
 
 // Round a double to the nearest double-float (hi = fl(x), lo = fl(x - hi)).
 __device__ __forceinline__ df df_from_double(double x) {
   const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
+  return {h, __double2float_rn(__dsub_rn(x, (double)h))};
 }
 
-__device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ double df_to_double(df x) { return __dadd_rn((double)x.hi, (double)x.lo); }
 
 __device__ __forceinline__ df two_sum(float a, float b) {
-  const float s = a + b;
-  const float bp = s - a;
-  const float e = (a - (s - bp)) + (b - bp);
+  const float s = fadd(a, b);
+  const float bp = fsub(s, a);
+  const float e = fadd(fsub(a, fsub(s, bp)), fsub(b, bp));
   return {s, e};
 }
 
 __device__ __forceinline__ df fast_two_sum(float a, float b) {
-  const float s = a + b;
-  return {s, b - (s - a)};
+  const float s = fadd(a, b);
+  return {s, fsub(b, fsub(s, a))};
 }
 
 __device__ __forceinline__ df two_prod(float a, float b) {
-  const float p = a * b;
+  const float p = fmul(a, b);
   return {p, fmaf(a, b, -p)};
 }
 
@@ -61,7 +69,7 @@ __device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
 // x + y, "sloppy" double-word sum (11 flops).
 __device__ __forceinline__ df df_add(df x, df y) {
   const df s = two_sum(x.hi, y.hi);
-  return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+  return fast_two_sum(s.hi, fadd(s.lo, fadd(x.lo, y.lo)));
 }
 
 __device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
@@ -69,12 +77,12 @@ __device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); 
 // x + b for a float b (10 flops).
 __device__ __forceinline__ df df_add_f(df x, float b) {
   const df s = two_sum(x.hi, b);
-  return fast_two_sum(s.hi, s.lo + x.lo);
+  return fast_two_sum(s.hi, fadd(s.lo, x.lo));
 }
 
 // x * y (DW x DW with FMA, 7 flops).
 __device__ __forceinline__ df df_mul(df x, df y) {
-  const float p = x.hi * y.hi;
+  const float p = fmul(x.hi, y.hi);
   float e = fmaf(x.hi, y.hi, -p);
   e = fmaf(x.hi, y.lo, e);
   e = fmaf(x.lo, y.hi, e);
@@ -83,35 +91,35 @@ __device__ __forceinline__ df df_mul(df x, df y) {
 
 // x * b for a float b (5 flops).
 __device__ __forceinline__ df df_mul_f(df x, float b) {
-  const float p = x.hi * b;
+  const float p = fmul(x.hi, b);
   float e = fmaf(x.hi, b, -p);
   e = fmaf(x.lo, b, e);
   return fast_two_sum(p, e);
 }
 
 // x * 2^k is exact: scale both words.
-__device__ __forceinline__ df df_scale(df x, float pow2) { return {x.hi * pow2, x.lo * pow2}; }
+__device__ __forceinline__ df df_scale(df x, float pow2) { return {fmul(x.hi, pow2), fmul(x.lo, pow2)}; }
 
 __device__ __forceinline__ df df_sqr(df x) {
-  const float p = x.hi * x.hi;
+  const float p = fmul(x.hi, x.hi);
   float e = fmaf(x.hi, x.hi, -p);
-  e = fmaf(2.f * x.hi, x.lo, e);
+  e = fmaf(fmul(2.f, x.hi), x.lo, e);
   return fast_two_sum(p, e);
 }
 
 // x * y + z (the product's leading part is exact; 15 flops).
 __device__ __forceinline__ df df_fma(df x, df y, df z) {
-  const float p = x.hi * y.hi;
+  const float p = fmul(x.hi, y.hi);
   float e = fmaf(x.hi, y.hi, -p);
   e = fmaf(x.hi, y.lo, e);
   e = fmaf(x.lo, y.hi, e);
   const df s = two_sum(p, z.hi);
-  return fast_two_sum(s.hi, s.lo + (e + z.lo));
+  return fast_two_sum(s.hi, fadd(s.lo, fadd(e, z.lo)));
 }
 
 // a*b + c*d with both leading products exact and one TwoSum (about 19 flops).
 __device__ __forceinline__ df df_dot2(df a, df b, df c, df d) {
-  const float p = a.hi * b.hi, q = c.hi * d.hi;
+  const float p = fmul(a.hi, b.hi), q = fmul(c.hi, d.hi);
   float e = fmaf(a.hi, b.hi, -p);
   float f = fmaf(c.hi, d.hi, -q);
   e = fmaf(a.hi, b.lo, e);
@@ -119,7 +127,7 @@ __device__ __forceinline__ df df_dot2(df a, df b, df c, df d) {
   f = fmaf(c.hi, d.lo, f);
   f = fmaf(c.lo, d.hi, f);
   const df s = two_sum(p, q);
-  return fast_two_sum(s.hi, s.lo + (e + f));
+  return fast_two_sum(s.hi, fadd(s.lo, fadd(e, f)));
 }
 
 // a*b - c*d
@@ -127,7 +135,7 @@ __device__ __forceinline__ df df_det2(df a, df b, df c, df d) { return df_dot2(a
 
 // a0*b0 + a1*b1 + a2*b2 (leading products exact, two TwoSums; about 31 flops).
 __device__ __forceinline__ df df_dot3(df a0, df b0, df a1, df b1, df a2, df b2) {
-  const float p0 = a0.hi * b0.hi, p1 = a1.hi * b1.hi, p2 = a2.hi * b2.hi;
+  const float p0 = fmul(a0.hi, b0.hi), p1 = fmul(a1.hi, b1.hi), p2 = fmul(a2.hi, b2.hi);
   float e0 = fmaf(a0.hi, b0.hi, -p0);
   float e1 = fmaf(a1.hi, b1.hi, -p1);
   float e2 = fmaf(a2.hi, b2.hi, -p2);
@@ -139,24 +147,24 @@ __device__ __forceinline__ df df_dot3(df a0, df b0, df a1, df b1, df a2, df b2) 
   e2 = fmaf(a2.lo, b2.hi, e2);
   const df s = two_sum(p0, p1);
   const df t = two_sum(s.hi, p2);
-  return fast_two_sum(t.hi, (t.lo + s.lo) + (e0 + (e1 + e2)));
+  return fast_two_sum(t.hi, fadd(fadd(t.lo, s.lo), fadd(e0, fadd(e1, e2))));
 }
 
 // 1/x by one Newton step from the float reciprocal (about 12 flops).
 __device__ __forceinline__ df df_rcp(df x) {
-  const float r = 1.0f / x.hi;
-  const df p = df_mul_f(x, r);              // ~ 1
-  const float e = (1.0f - p.hi) - p.lo;     // 1 - p.hi is exact (Sterbenz)
-  return fast_two_sum(r, r * e);
+  const float r = __frcp_rn(x.hi);
+  const df p = df_mul_f(x, r);                    // ~ 1
+  const float e = fsub(fsub(1.0f, p.hi), p.lo);   // 1 - p.hi is exact (Sterbenz)
+  return fast_two_sum(r, fmul(r, e));
 }
 
 // sqrt(x) for x >= 0 by one Newton step from the float square root.
 __device__ __forceinline__ df df_sqrt(df x) {
   if (!(x.hi > 0.f)) return {0.f, 0.f};
-  const float y = sqrtf(x.hi);
+  const float y = __fsqrt_rn(x.hi);
   const df yy = two_prod(y, y);
-  const float r = ((x.hi - yy.hi) - yy.lo) + x.lo;   // x - y^2 to float precision
-  return fast_two_sum(y, r * (0.5f / y));
+  const float r = fadd(fsub(fsub(x.hi, yy.hi), yy.lo), x.lo);   // x - y^2 to float precision
+  return fast_two_sum(y, fmul(r, __fdiv_rn(0.5f, y)));
 }
 
 // ---- natural logarithm ---------------------------------------------------------------------
@@ -186,8 +194,14 @@ __device__ __forceinline__ df df_log(df x, const LogEntry* tab) {
   int i = __float2int_rn((m.hi - kLogC0) * 256.0f);
   i = i < 0 ? 0 : (i > kLogTable - 1 ? kLogTable - 1 : i);
   const LogEntry T = tab[i];
-  const df p = df_mul_f(m, T.r);
-  const df t = fast_two_sum(p.hi - 1.0f, p.lo);                  // p.hi - 1 is exact
+  // t = m r - 1 formed exactly up to the last, tiny term: both partial products are exact
+  // (TwoProd) and pa.hi - 1 is exact (Sterbenz), so t keeps its full relative precision
+  // even though m r is close to 1.
+  const df pa = two_prod(m.hi, T.r);
+  const df pb = two_prod(m.lo, T.r);
+  df t = two_sum(fsub(pa.hi, 1.0f), pa.lo);
+  t = df_add_f(t, pb.hi);
+  t = df_add_f(t, pb.lo);
   // log(1 + t) = t - t^2/2 + t^3/3 - t^4/4 + t^5/5 - t^6/6 + ...
   const df t2 = df_sqr(t);
   const df t3 = df_mul(t2, t);

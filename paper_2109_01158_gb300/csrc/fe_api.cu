@@ -60,9 +60,13 @@ struct DeviceGuard {
   }
 };
 
+// Device allocation rounded up to 256 bytes plus 256 bytes of slack: bulk copies read whole
+// 16-byte units, so a range that ends inside the last unit of a buffer stays in bounds.
+inline size_t alloc_bytes(size_t bytes) { return ((bytes + 255) / 256) * 256 + 256; }
+
 template <typename T>
 fe_status dev_alloc(fe_ctx* c, T** p, size_t count) {
-  size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+  size_t bytes = alloc_bytes(sizeof(T) * (count > 0 ? count : 1));
   cudaError_t e = cudaMalloc((void**)p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -76,7 +80,7 @@ template <typename T>
 void dev_free(fe_ctx* c, T** p, size_t count) {
   if (*p) {
     cudaFree(*p);
-    size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+    size_t bytes = alloc_bytes(sizeof(T) * (count > 0 ? count : 1));
     c->bytes = c->bytes >= bytes ? c->bytes - bytes : 0;
   }
   *p = nullptr;
@@ -98,7 +102,6 @@ void free_precompute(fe_ctx* c) {
   dev_free(c, &c->u_df, nn * padded_d(c->d));
   dev_free(c, &c->r_df, ne * k * c->d);
   dev_free(c, &c->u, nn * padded_d(c->d));
-  dev_free(c, &c->u32, nn * padded_d(c->d));
   dev_free(c, &c->r, ne * k * c->d);
   dev_free(c, &c->r32, ne * k * c->d);
   dev_free(c, &c->stage_v, nn * c->d);
@@ -388,15 +391,18 @@ fe_status fe_precompute(fe_ctx* c, unsigned precisions) {
   }
   if (precisions & (1u << FE_F32_COMP)) {
     if ((st = dev_alloc(c, &c->dphi32, ne * c->dim * c->dim)) || (st = dev_alloc(c, &c->vol32, ne)) ||
-        (st = dev_alloc(c, &c->u32, nn * dp)) || (st = dev_alloc(c, &c->r32, ne * k * c->d))) {
+        (st = dev_alloc(c, &c->r32, ne * k * c->d))) {
       free_precompute(c);
       return st;
     }
   }
+  if ((precisions & ((1u << FE_DF64) | (1u << FE_F32_COMP))) && (st = dev_alloc(c, &c->u_df, nn * dp))) {
+    free_precompute(c);
+    return st;
+  }
   if (precisions & (1u << FE_DF64)) {
     if ((st = dev_alloc(c, &c->dphi_df, ne * c->dim * c->dim)) || (st = dev_alloc(c, &c->vol_df, ne)) ||
-        (st = dev_alloc(c, &c->log_tab, kLogTable)) || (st = dev_alloc(c, &c->u_df, nn * dp)) ||
-        (st = dev_alloc(c, &c->r_df, ne * k * c->d))) {
+        (st = dev_alloc(c, &c->log_tab, kLogTable)) || (st = dev_alloc(c, &c->r_df, ne * k * c->d))) {
       free_precompute(c);
       return st;
     }
@@ -503,6 +509,7 @@ fe_status fe_sync_status(fe_ctx* c) {
     cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
     cudaStreamSynchronize(c->stream);
   }
+  if (hs & kStatusTimeout) return set_error(FE_ETIMEOUT, "a bounded device wait gave up");
   if (hs & kStatusDomain) return set_error(FE_EDOMAIN, "an element has det F <= 0");
   return FE_OK;
 }

@@ -10,9 +10,11 @@
 //                   eq. pLaplacian), dW/dF (Sec. 6.2), local forces to the CSR slots; the
 //                   energy is accumulated as a double-float per thread, then in FP64 over
 //                   the block and the grid (fixed order)
-//   k_gather_df     per node: double-float sum of its CSR segment, converted to FP64, - b
+//   gather          per node: double-float sum of its CSR segment (warp-cooperative, bulk
+//                   copies: gather_bulk.cuh), converted to FP64, - b
 #include "df64.cuh"
 #include "fe_internal.cuh"
+#include "gather_bulk.cuh"
 
 namespace fe {
 namespace {
@@ -84,17 +86,17 @@ __device__ __forceinline__ void load_u_df(const float2* __restrict__ u, int32_t 
 // Sum of squares of N double-floats: exact leading products, TwoSum chain.
 template <int N>
 __device__ __forceinline__ df df_sumsq(const df* x) {
-  float s = x[0].hi * x[0].hi;
+  float s = fmul(x[0].hi, x[0].hi);
   float e = fmaf(x[0].hi, x[0].hi, -s);
-  e = fmaf(2.f * x[0].hi, x[0].lo, e);
+  e = fmaf(fmul(2.f, x[0].hi), x[0].lo, e);
 #pragma unroll
   for (int i = 1; i < N; ++i) {
-    const float p = x[i].hi * x[i].hi;
-    e += fmaf(x[i].hi, x[i].hi, -p);
-    e = fmaf(2.f * x[i].hi, x[i].lo, e);
+    const float p = fmul(x[i].hi, x[i].hi);
+    e = fadd(e, fmaf(x[i].hi, x[i].hi, -p));
+    e = fmaf(fmul(2.f, x[i].hi), x[i].lo, e);
     const df t = two_sum(s, p);
     s = t.hi;
-    e += t.lo;
+    e = fadd(e, t.lo);
   }
   return fast_two_sum(s, e);
 }
@@ -292,31 +294,6 @@ __global__ void __launch_bounds__(kThreads) k_elem_df(
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(kThreads) k_gather_df(int64_t nn, const int32_t* __restrict__ row_ptr,
-                                                        const float2* __restrict__ r,
-                                                        const double* __restrict__ b,
-                                                        const uint8_t* __restrict__ dir,
-                                                        const int32_t* __restrict__ perm,
-                                                        double* __restrict__ g) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
-    df s[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) s[j] = {0.f, 0.f};
-    const int32_t q1 = __ldg(row_ptr + i + 1);
-    for (int32_t q = __ldg(row_ptr + i); q < q1; ++q)
-#pragma unroll
-      for (int j = 0; j < D; ++j) s[j] = df_add(s[j], ld_df(r, (int64_t)q * D + j));
-    const int64_t dst = perm ? (int64_t)__ldg(perm + i) : i;
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      const double val = df_to_double(s[j]) - b[i * D + j];
-      g[dst * D + j] = dir[i * D + j] ? 0.0 : val;
-    }
-  }
-}
-
 __global__ void k_to_df(int64_t n, const double* __restrict__ a, float2* __restrict__ o) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -390,9 +367,9 @@ fe_status evaldf_t(fe_ctx* c, const double* v, double* J, double* dens, double* 
 #undef FE_ELEMDF
   if (G) {
     prof_begin(c, kStageGather);
-    k_gather_df<D><<<grid_for(c->nn, 4 * kMaxNodeBlocks), kThreads, 0, s>>>(c->nn, c->row_ptr, c->r_df, c->b,
-                                                                            c->dir, c->perm, g);
+    const fe_status gs = launch_gather_bulk<D, AccDF>(c, c->r_df, g);
     prof_end(c, kStageGather);
+    if (gs) return gs;
     c->launches++;
   }
   return cuda_check(cudaGetLastError(), "eval df64 launch");

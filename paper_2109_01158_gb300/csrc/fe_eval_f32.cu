@@ -14,6 +14,7 @@
 // sums of the gradient are float pairs converted to double per node.  No floating-point
 // operation is done in FP64 per element except in the rare FP64 branch above.
 #include "fe_internal.cuh"
+#include "gather_bulk.cuh"
 
 namespace fe {
 namespace {
@@ -22,11 +23,9 @@ namespace {
 struct FPair {
   float hi = 0.f, lo = 0.f;
   __device__ __forceinline__ void add(float x) {
-    const float s = hi + x;
-    const float bp = s - hi;
-    const float err = (hi - (s - bp)) + (x - bp);
-    hi = s;
-    lo += err;
+    const df t = two_sum(hi, x);
+    hi = t.hi;
+    lo = fadd(lo, t.lo);
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
@@ -112,19 +111,25 @@ __device__ __noinline__ bool far_from_identity_f64(const float* Hf, int dim, flo
   return true;
 }
 
+// Node record of the displacement as double-float pairs (D pairs, padded to 4 in 3D).  The
+// float path rounds only the differences u_l - u_0 to float: the displacement itself can be
+// hundreds of times larger than its differences across an element, and rounding it first
+// would lose that factor in grad u.
 template <int D>
-__device__ __forceinline__ void load_u32(const float* __restrict__ u, int32_t n, float* out) {
+__device__ __forceinline__ void load_u_pairs(const float2* __restrict__ u, int32_t n, df* out) {
   if (D == 1) {
-    out[0] = __ldg(u + n);
+    const float2 a = __ldg(u + n);
+    out[0] = {a.x, a.y};
   } else if (D == 2) {
-    float2 a = __ldg(reinterpret_cast<const float2*>(u) + n);
-    out[0] = a.x;
-    out[1] = a.y;
+    const float4 a = __ldg(reinterpret_cast<const float4*>(u) + n);
+    out[0] = {a.x, a.y};
+    out[1] = {a.z, a.w};
   } else {
-    float4 a = __ldg(reinterpret_cast<const float4*>(u) + n);
-    out[0] = a.x;
-    out[1] = a.y;
-    out[2] = a.z;
+    const float4* p = reinterpret_cast<const float4*>(u) + 2 * (int64_t)n;
+    const float4 a = __ldg(p), b = __ldg(p + 1);
+    out[0] = {a.x, a.y};
+    out[1] = {a.z, a.w};
+    out[2] = {b.x, b.y};
   }
 }
 
@@ -133,7 +138,7 @@ __global__ void __launch_bounds__(kThreads) k_node_prep32(int64_t nn, const doub
                                                           const double* __restrict__ X,
                                                           const int32_t* __restrict__ perm,
                                                           const double* __restrict__ b,
-                                                          float* __restrict__ u,
+                                                          float2* __restrict__ u,
                                                           double* __restrict__ node_partials) {
   __shared__ double sh[kThreads / 32];
   constexpr int DP = D == 3 ? 4 : D;
@@ -141,17 +146,21 @@ __global__ void __launch_bounds__(kThreads) k_node_prep32(int64_t nn, const doub
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
     const int64_t src = perm ? (int64_t)perm[i] : i;
-    float w[DP];
+    df w[DP];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       const double vj = v[src * D + j];
       dot += b[i * D + j] * vj;
-      w[j] = (float)(NH ? vj - X[i * DIM + j] : vj);
+      w[j] = df_from_double(NH ? vj - X[i * DIM + j] : vj);
     }
-    if (DP == 4) w[3] = 0.f;
-    if (DP == 1) u[i] = w[0];
-    else if (DP == 2) reinterpret_cast<float2*>(u)[i] = make_float2(w[0], w[1]);
-    else reinterpret_cast<float4*>(u)[i] = make_float4(w[0], w[1], w[2], w[3]);
+    if (DP == 4) w[3] = {0.f, 0.f};
+    if (DP == 1) {
+      u[i] = make_float2(w[0].hi, w[0].lo);
+    } else {
+      float4* o = reinterpret_cast<float4*>(u) + i * (DP / 2);
+      o[0] = make_float4(w[0].hi, w[0].lo, w[1].hi, w[1].lo);
+      if (DP == 4) o[1] = make_float4(w[2].hi, w[2].lo, w[3].hi, w[3].lo);
+    }
   }
   dot = block_sum(dot, sh);
   if (threadIdx.x == 0) node_partials[blockIdx.x] = dot;
@@ -160,7 +169,7 @@ __global__ void __launch_bounds__(kThreads) k_node_prep32(int64_t nn, const doub
 template <int DIM, int D, int MODEL, bool ENERGY, bool GRAD, bool DENS>
 __global__ void __launch_bounds__(kThreads) k_elem_f32(
     int64_t ne, const int32_t* __restrict__ elems, const float* __restrict__ dphi,
-    const float* __restrict__ vol, const float* __restrict__ u, const int32_t* __restrict__ slot,
+    const float* __restrict__ vol, const float2* __restrict__ u, const int32_t* __restrict__ slot,
     const int32_t* __restrict__ eperm, ModelParams mp, float* __restrict__ r,
     double* __restrict__ dens, double* partials, const double* node_partials, int n_node_blocks,
     unsigned* counter, double* J, int* status) {
@@ -171,9 +180,9 @@ __global__ void __launch_bounds__(kThreads) k_elem_f32(
   const float C1 = (float)mp.C1, D1 = (float)mp.D1;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
-    float ul[K][D];
+    df ul[K][D];
 #pragma unroll
-    for (int l = 0; l < K; ++l) load_u32<D>(u, __ldg(elems + (int64_t)l * ne + e), ul[l]);
+    for (int l = 0; l < K; ++l) load_u_pairs<D>(u, __ldg(elems + (int64_t)l * ne + e), ul[l]);
     float g[DIM][DIM];
 #pragma unroll
     for (int l = 0; l < DIM; ++l)
@@ -185,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) k_elem_f32(
     for (int j = 0; j < D; ++j) {
       float a[DIM];
 #pragma unroll
-      for (int l = 0; l < DIM; ++l) a[l] = ul[l + 1][j] - ul[0][j];
+      for (int l = 0; l < DIM; ++l) a[l] = df_sub(ul[l + 1][j], ul[0][j]).hi;
 #pragma unroll
       for (int m = 0; m < DIM; ++m) {
         float s = a[0] * g[0][m];
@@ -318,29 +327,6 @@ __global__ void __launch_bounds__(kThreads) k_elem_f32(
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(kThreads) k_gather32(int64_t nn, const int32_t* __restrict__ row_ptr,
-                                                       const float* __restrict__ r,
-                                                       const double* __restrict__ b,
-                                                       const uint8_t* __restrict__ dir,
-                                                       const int32_t* __restrict__ perm,
-                                                       double* __restrict__ g) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
-    FPair s[D];
-    const int32_t q1 = __ldg(row_ptr + i + 1);
-    for (int32_t q = __ldg(row_ptr + i); q < q1; ++q)
-#pragma unroll
-      for (int j = 0; j < D; ++j) s[j].add(__ldg(r + (int64_t)q * D + j));
-    const int64_t dst = perm ? (int64_t)__ldg(perm + i) : i;
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      const double val = s[j].value() - b[i * D + j];
-      g[dst * D + j] = dir[i * D + j] ? 0.0 : val;
-    }
-  }
-}
-
 template <int DIM, int D, int MODEL>
 fe_status eval32_t(fe_ctx* c, const double* v, double* J, double* dens, double* g, bool want_energy,
                    bool want_grad) {
@@ -351,13 +337,13 @@ fe_status eval32_t(fe_ctx* c, const double* v, double* J, double* dens, double* 
   double* node_partials = c->partials + kMaxElemBlocks;
   prof_begin(c, kStagePrep);
   k_node_prep32<D, MODEL == FE_NEOHOOKE, DIM><<<nb_node, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b,
-                                                                           c->u32, node_partials);
+                                                                           c->u_df, node_partials);
   prof_end(c, kStagePrep);
   c->launches++;
   const bool E = want_energy, G = want_grad, Dn = dens != nullptr;
 #define FE_ELEM32(EN, GR, DE)                                                                        \
   k_elem_f32<DIM, D, MODEL, EN, GR, DE><<<nb_elem, kThreads, 0, s>>>(                                \
-      c->ne, c->elems, c->dphi32, c->vol32, c->u32, c->slot, c->eperm, mp, c->r32, dens, c->partials, \
+      c->ne, c->elems, c->dphi32, c->vol32, c->u_df, c->slot, c->eperm, mp, c->r32, dens, c->partials, \
       node_partials, nb_node, c->counter, J, c->status)
   if (c->ne > 0 || E) {
     prof_begin(c, kStageElem);
@@ -374,9 +360,9 @@ fe_status eval32_t(fe_ctx* c, const double* v, double* J, double* dens, double* 
 #undef FE_ELEM32
   if (G) {
     prof_begin(c, kStageGather);
-    k_gather32<D><<<grid_for(c->nn, 4 * kMaxNodeBlocks), kThreads, 0, s>>>(c->nn, c->row_ptr, c->r32, c->b,
-                                                                           c->dir, c->perm, g);
+    const fe_status gs = launch_gather_bulk<D, AccF32>(c, c->r32, g);
     prof_end(c, kStageGather);
+    if (gs) return gs;
     c->launches++;
   }
   return cuda_check(cudaGetLastError(), "eval f32 launch");

@@ -24,6 +24,7 @@ constexpr int kMaxNodeBlocks = 608;   // 4 x 152 SMs
 // Device status bits (accumulated until fe_sync_status).
 constexpr int kStatusDomain = 1;      // det F <= 0 seen
 constexpr int kStatusDegenerate = 2;  // |T| == 0 at precompute
+constexpr int kStatusTimeout = 4;     // a bounded device wait gave up
 
 // Model parameters passed by value to the element kernels.
 struct ModelParams {
@@ -82,10 +83,9 @@ struct fe_ctx {
 
   // device: work buffers
   double* u = nullptr;         // nn*padded_d(d): displacement (Neo-Hookean) or v
-  float* u32 = nullptr;        // nn*padded_d(d), FP32 displacement
   double* r = nullptr;         // ne*(dim+1)*d slot-ordered local forces (x2 for FD)
   float* r32 = nullptr;        // ne*(dim+1)*d, FP32 local forces
-  float2* u_df = nullptr;      // nn*padded_d(d) double-float displacement
+  float2* u_df = nullptr;      // nn*padded_d(d) double-float displacement (FE_DF64, FE_F32_COMP)
   float2* r_df = nullptr;      // ne*(dim+1)*d double-float local forces
   double* partials = nullptr;  // element partials [kMaxElemBlocks] then node partials
   unsigned* counter = nullptr; // last-block ticket

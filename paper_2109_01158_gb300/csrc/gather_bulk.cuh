@@ -1,0 +1,130 @@
+// gather_bulk.cuh -- warp-cooperative patch gather with bulk (TMA) copies.
+//
+// g_i = sum over the CSR segment of node i of the local forces r_{T,l} (written by the
+// element kernel to the CSR positions), minus b_i, and 0 on Dirichlet dofs (Sec. 6.2,
+// Remark 1).  Each warp owns 32 consecutive nodes; their segments form one contiguous range
+// of r, which lane 0 copies into the warp's shared-memory buffer with one cp.async.bulk
+// completing on an mbarrier.  Each lane then sums its node's segment in slot order (the same
+// order as a plain per-node loop, so results do not depend on the launch shape).  A range
+// larger than the buffer is read directly from global memory.
+#pragma once
+
+#include "async_copy.cuh"
+#include "fe_internal.cuh"
+
+namespace fe {
+
+constexpr int kGatherWarps = 8;
+constexpr int kGatherCap = 20480;   // bytes of shared memory per warp
+constexpr int kGatherSmem = kGatherWarps * kGatherCap;
+
+// Double-float slots (float2 per component), double-float sums.
+struct AccDF {
+  using T = float2;
+  df s = {0.f, 0.f};
+  __device__ __forceinline__ void add(float2 x) { s = df_add(s, df{x.x, x.y}); }
+  __device__ __forceinline__ double value() const { return df_to_double(s); }
+};
+
+// Float slots, float-pair (TwoSum) sums.
+struct AccF32 {
+  using T = float;
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const df t = two_sum(hi, x);
+    hi = t.hi;
+    lo = fadd(lo, t.lo);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <int D, class Acc>
+__global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
+    int64_t nn, const int32_t* __restrict__ row_ptr, const typename Acc::T* __restrict__ r,
+    const double* __restrict__ b, const uint8_t* __restrict__ dir, const int32_t* __restrict__ perm,
+    double* __restrict__ g, int* status) {
+  using T = typename Acc::T;
+  extern __shared__ __align__(128) unsigned char gsmem[];
+  __shared__ __align__(8) uint64_t bars[kGatherWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* buf = gsmem + warp * kGatherCap;
+  uint64_t* bar = &bars[warp];
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  uint32_t phase = 0;
+  const int64_t nchunks = (nn + 31) / 32;
+  const int64_t wstride = (int64_t)gridDim.x * kGatherWarps;
+  for (int64_t c = (int64_t)blockIdx.x * kGatherWarps + warp; c < nchunks; c += wstride) {
+    const int64_t n0 = c * 32;
+    const int64_t n1 = (n0 + 32 < nn) ? n0 + 32 : nn;
+    const int64_t s0 = __ldg(row_ptr + n0), s1 = __ldg(row_ptr + n1);
+    const int64_t byte0 = s0 * D * (int64_t)sizeof(T), byte1 = s1 * D * (int64_t)sizeof(T);
+    const int64_t a0 = byte0 & ~15LL, a1 = (byte1 + 15) & ~15LL;
+    const bool staged = (a1 > a0) && (a1 - a0 <= kGatherCap);
+    if (staged) {
+      if (lane == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, (uint32_t)(a1 - a0));
+        bulk_g2s(buf, reinterpret_cast<const unsigned char*>(r) + a0, (uint32_t)(a1 - a0), bar);
+      }
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, phase));
+      if (!ok) {
+        // give up: record it, wait (bounded) for the copy still in flight, and stop
+        if (lane == 0) atomicOr(status, kStatusTimeout);
+        mbar_wait_bounded(bar, phase);
+        return;
+      }
+      phase ^= 1u;
+    }
+    const int64_t i = n0 + lane;
+    if (i < nn) {
+      const int32_t q0 = __ldg(row_ptr + i), q1 = __ldg(row_ptr + i + 1);
+      Acc acc[D];
+      if (staged) {
+        // element k of r is at sbuf[k - k0] (a0 is a multiple of 16, so of sizeof(T))
+        const T* sbuf = reinterpret_cast<const T*>(buf);
+        const int64_t k0 = a0 / (int64_t)sizeof(T);
+        for (int32_t q = q0; q < q1; ++q)
+#pragma unroll
+          for (int j = 0; j < D; ++j) acc[j].add(sbuf[(int64_t)q * D + j - k0]);
+      } else {
+        for (int32_t q = q0; q < q1; ++q)
+#pragma unroll
+          for (int j = 0; j < D; ++j) acc[j].add(__ldg(r + (int64_t)q * D + j));
+      }
+      const int64_t dst = perm ? (int64_t)__ldg(perm + i) : i;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const double val = acc[j].value() - b[i * D + j];
+        g[dst * D + j] = dir[i * D + j] ? 0.0 : val;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Launch on the context stream: one block of 8 warps per SM (160 KB of shared memory each).
+template <int D, class Acc>
+inline fe_status launch_gather_bulk(fe_ctx* c, const typename Acc::T* r, double* g) {
+  static bool configured[64] = {false};
+  if (c->device < 0 || c->device >= 64 || !configured[c->device]) {
+    cudaError_t e = cudaFuncSetAttribute(k_gather_bulk<D, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kGatherSmem);
+    if (e != cudaSuccess) return cuda_check(e, "gather smem attribute");
+    if (c->device >= 0 && c->device < 64) configured[c->device] = true;
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int64_t nchunks = (c->nn + 31) / 32;
+  int64_t blocks = (nchunks + kGatherWarps - 1) / kGatherWarps;
+  if (blocks > sms) blocks = sms;
+  if (blocks < 1) blocks = 1;
+  k_gather_bulk<D, Acc><<<(unsigned)blocks, kGatherWarps * 32, kGatherSmem, c->stream>>>(
+      c->nn, c->row_ptr, r, c->b, c->dir, c->perm, g, c->status);
+  return cuda_check(cudaGetLastError(), "gather launch");
+}
+
+}  // namespace fe
