@@ -15,6 +15,7 @@
 // operation is done in FP64 per element except in the rare FP64 branch above.
 #include "fe_internal.cuh"
 #include "gather_bulk.cuh"
+#include "tile_stream.cuh"
 
 namespace fe {
 namespace {
@@ -166,29 +167,111 @@ __global__ void __launch_bounds__(kThreads) k_node_prep32(int64_t nn, const doub
   if (threadIdx.x == 0) node_partials[blockIdx.x] = dot;
 }
 
+template <int DIM, bool GRAD>
+struct F32Arrays {
+  static constexpr int K = DIM + 1;
+  static constexpr int kDphi = 0;                  // DIM*DIM arrays of float
+  static constexpr int kVol = DIM * DIM;           // float
+  static constexpr int kElems = DIM * DIM + 1;     // K arrays of int32
+  static constexpr int kSlots = kElems + K;        // K arrays of int32 (gradient only)
+  static constexpr int N = kSlots + (GRAD ? K : 0);
+};
+
+template <int NT>
+__device__ __forceinline__ double block_sum_nt(double x, double* sh) {
+  x = warp_sum(x);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = x;
+  __syncthreads();
+  x = (threadIdx.x < NT / 32) ? sh[threadIdx.x] : 0.0;
+  if (warp == 0) x = warp_sum(x);
+  __syncthreads();
+  return x;
+}
+
+template <int NT>
+__device__ __forceinline__ void finish_energy_nt(double block_total, double* partials, int n_elem_blocks,
+                                                 const double* node_partials, int n_node_blocks,
+                                                 unsigned* counter, double* J, double* sh) {
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = block_total;
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    am_last = (t == (unsigned)n_elem_blocks - 1u);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  double s = 0.0, t = 0.0;
+  for (int k = threadIdx.x; k < n_elem_blocks; k += NT) s += __ldcg(partials + k);
+  for (int k = threadIdx.x; k < n_node_blocks; k += NT) t += __ldcg(node_partials + k);
+  s = block_sum_nt<NT>(s, sh);
+  t = block_sum_nt<NT>(t, sh);
+  if (threadIdx.x == 0) {
+    *J = s - t;
+    *counter = 0u;
+  }
+}
+
+// Element kernel: persistent blocks stream tiles of the element arrays through shared-memory
+// stages with bulk copies (tile_stream.cuh); one element per thread and tile.
 template <int DIM, int D, int MODEL, bool ENERGY, bool GRAD, bool DENS>
-__global__ void __launch_bounds__(kThreads) k_elem_f32(
-    int64_t ne, const int32_t* __restrict__ elems, const float* __restrict__ dphi,
-    const float* __restrict__ vol, const float2* __restrict__ u, const int32_t* __restrict__ slot,
+__global__ void __launch_bounds__(kTile, 20) k_elem_f32(
+    int64_t ne, TileArrays<F32Arrays<DIM, GRAD>::N> A, const float2* __restrict__ u,
     const int32_t* __restrict__ eperm, ModelParams mp, float* __restrict__ r,
     double* __restrict__ dens, double* partials, const double* node_partials, int n_node_blocks,
     unsigned* counter, double* J, int* status) {
   constexpr int K = DIM + 1;
-  __shared__ double sh[kThreads / 32];
+  using AR = F32Arrays<DIM, GRAD>;
+  constexpr int NA = AR::N;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ double sh[kTile / 32];
+  TileLayout<NA> L;
+  L.init(A);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < kStages; ++k) mbar_init(&bars[k], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const int64_t ntiles = (ne + kTile - 1) / kTile;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kStages; ++k) {
+      const int64_t t = blockIdx.x + (int64_t)k * gridDim.x;
+      if (t < ntiles) tile_issue(A, L, smem + k * L.stage_bytes, &bars[k], t, ne);
+    }
   FPair acc;
   bool bad = false;
   const float C1 = (float)mp.C1, D1 = (float)mp.D1;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int sidx = it % kStages;
+    unsigned char* st = smem + sidx * L.stage_bytes;
+    const bool ok = mbar_wait_bounded(&bars[sidx], (uint32_t)((it / kStages) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(status, kStatusTimeout);
+        for (int k = 0; k < kStages; ++k) {
+          const int64_t t = tile + (int64_t)k * gridDim.x;
+          if (t < ntiles) mbar_wait_bounded(&bars[(it + k) % kStages], (uint32_t)(((it + k) / kStages) & 1));
+        }
+      }
+      return;
+    }
+    const int tid = threadIdx.x;
+    const int64_t e = tile * kTile + tid;
+    if (e < ne) {
     df ul[K][D];
 #pragma unroll
-    for (int l = 0; l < K; ++l) load_u_pairs<D>(u, __ldg(elems + (int64_t)l * ne + e), ul[l]);
+    for (int l = 0; l < K; ++l) load_u_pairs<D>(u, tile_get<int32_t>(st, L, AR::kElems + l, tid, 4), ul[l]);
     float g[DIM][DIM];
 #pragma unroll
     for (int l = 0; l < DIM; ++l)
 #pragma unroll
-      for (int m = 0; m < DIM; ++m) g[l][m] = __ldg(dphi + ((int64_t)l * DIM + m) * ne + e);
-    const float vT = __ldg(vol + e);
+      for (int m = 0; m < DIM; ++m) g[l][m] = tile_get<float>(st, L, AR::kDphi + l * DIM + m, tid, 4);
+    const float vT = tile_get<float>(st, L, AR::kVol, tid, 4);
     float H[D][DIM];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
@@ -305,7 +388,7 @@ __global__ void __launch_bounds__(kThreads) k_elem_f32(
       for (int j = 0; j < D; ++j) r0[j] = 0.f;
 #pragma unroll
       for (int l = 1; l <= DIM; ++l) {
-        const int64_t q = __ldg(slot + (int64_t)l * ne + e);
+        const int64_t q = tile_get<int32_t>(st, L, AR::kSlots + l, tid, 4);
 #pragma unroll
         for (int j = 0; j < D; ++j) {
           float s = P[j][0] * g[l - 1][0];
@@ -315,16 +398,52 @@ __global__ void __launch_bounds__(kThreads) k_elem_f32(
           r0[j] -= s;
         }
       }
-      const int64_t q0 = __ldg(slot + e);
+      const int64_t q0 = tile_get<int32_t>(st, L, AR::kSlots, tid, 4);
 #pragma unroll
       for (int j = 0; j < D; ++j) r[q0 * D + j] = r0[j];
     }
+    }
+    __syncthreads();   // every thread is done with this stage
+    const int64_t nxt = tile + (int64_t)kStages * gridDim.x;
+    if (threadIdx.x == 0 && nxt < ntiles) tile_issue(A, L, st, &bars[sidx], nxt, ne);
   }
   if (bad) atomicOr(status, kStatusDomain);
   if (ENERGY) {
-    double t = block_sum(acc.value(), sh);
-    finish_energy(t, partials, gridDim.x, node_partials, n_node_blocks, counter, J, sh);
+    const double t = block_sum_nt<kTile>(acc.value(), sh);
+    finish_energy_nt<kTile>(t, partials, gridDim.x, node_partials, n_node_blocks, counter, J, sh);
   }
+}
+
+template <int DIM, int D, int MODEL, bool E, bool G, bool DN>
+fe_status launch_elem_f32(fe_ctx* c, const ModelParams& mp, double* dens, const double* node_partials,
+                          int nb_node, double* J) {
+  using AR = F32Arrays<DIM, G>;
+  TileArrays<AR::N> A;
+  int stage_bytes = 0;
+  for (int a = 0; a < AR::N; ++a) {
+    const unsigned char* base;
+    if (a < AR::kVol) base = reinterpret_cast<const unsigned char*>(c->dphi32 + (int64_t)a * c->ne);
+    else if (a == AR::kVol) base = reinterpret_cast<const unsigned char*>(c->vol32);
+    else if (a < AR::kSlots) base = reinterpret_cast<const unsigned char*>(c->elems + (int64_t)(a - AR::kElems) * c->ne);
+    else base = reinterpret_cast<const unsigned char*>(c->slot + (int64_t)(a - AR::kSlots) * c->ne);
+    A.base[a] = base;
+    A.esize[a] = 4;
+    stage_bytes += ((kTile * 4 + 16) + 15) & ~15;
+  }
+  const int smem = kStages * stage_bytes;
+  static bool configured[64] = {false};
+  if (c->device < 0 || c->device >= 64 || !configured[c->device]) {
+    cudaError_t e = cudaFuncSetAttribute(k_elem_f32<DIM, D, MODEL, E, G, DN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_check(e, "element kernel smem attribute");
+    if (c->device >= 0 && c->device < 64) configured[c->device] = true;
+  }
+  const int64_t ntiles = (c->ne + kTile - 1) / kTile;
+  const int grid = (int)(ntiles < kTileBlocks ? (ntiles > 0 ? ntiles : 1) : kTileBlocks);
+  k_elem_f32<DIM, D, MODEL, E, G, DN><<<grid, kTile, smem, c->stream>>>(
+      c->ne, A, c->u_df, c->eperm, mp, c->r32, dens, c->partials, node_partials, nb_node, c->counter, J,
+      c->status);
+  return cuda_check(cudaGetLastError(), "f32 element launch");
 }
 
 template <int DIM, int D, int MODEL>
@@ -333,7 +452,6 @@ fe_status eval32_t(fe_ctx* c, const double* v, double* J, double* dens, double* 
   cudaStream_t s = c->stream;
   const ModelParams mp = model_params(c);
   const int nb_node = grid_for(c->nn, kMaxNodeBlocks);
-  const int nb_elem = grid_for(c->ne, kMaxElemBlocks);
   double* node_partials = c->partials + kMaxElemBlocks;
   prof_begin(c, kStagePrep);
   k_node_prep32<D, MODEL == FE_NEOHOOKE, DIM><<<nb_node, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b,
@@ -341,23 +459,20 @@ fe_status eval32_t(fe_ctx* c, const double* v, double* J, double* dens, double* 
   prof_end(c, kStagePrep);
   c->launches++;
   const bool E = want_energy, G = want_grad, Dn = dens != nullptr;
-#define FE_ELEM32(EN, GR, DE)                                                                        \
-  k_elem_f32<DIM, D, MODEL, EN, GR, DE><<<nb_elem, kThreads, 0, s>>>(                                \
-      c->ne, c->elems, c->dphi32, c->vol32, c->u_df, c->slot, c->eperm, mp, c->r32, dens, c->partials, \
-      node_partials, nb_node, c->counter, J, c->status)
   if (c->ne > 0 || E) {
     prof_begin(c, kStageElem);
-    if (E && G && Dn) FE_ELEM32(true, true, true);
-    else if (E && G) FE_ELEM32(true, true, false);
-    else if (E && Dn) FE_ELEM32(true, false, true);
-    else if (E) FE_ELEM32(true, false, false);
-    else if (G && Dn) FE_ELEM32(false, true, true);
-    else if (G) FE_ELEM32(false, true, false);
-    else FE_ELEM32(false, false, true);
+    fe_status es;
+    if (E && G && Dn) es = launch_elem_f32<DIM, D, MODEL, true, true, true>(c, mp, dens, node_partials, nb_node, J);
+    else if (E && G) es = launch_elem_f32<DIM, D, MODEL, true, true, false>(c, mp, dens, node_partials, nb_node, J);
+    else if (E && Dn) es = launch_elem_f32<DIM, D, MODEL, true, false, true>(c, mp, dens, node_partials, nb_node, J);
+    else if (E) es = launch_elem_f32<DIM, D, MODEL, true, false, false>(c, mp, dens, node_partials, nb_node, J);
+    else if (G && Dn) es = launch_elem_f32<DIM, D, MODEL, false, true, true>(c, mp, dens, node_partials, nb_node, J);
+    else if (G) es = launch_elem_f32<DIM, D, MODEL, false, true, false>(c, mp, dens, node_partials, nb_node, J);
+    else es = launch_elem_f32<DIM, D, MODEL, false, false, true>(c, mp, dens, node_partials, nb_node, J);
     prof_end(c, kStageElem);
     c->launches++;
+    if (es) return es;
   }
-#undef FE_ELEM32
   if (G) {
     prof_begin(c, kStageGather);
     const fe_status gs = launch_gather_bulk<D, AccF32>(c, c->r32, g);

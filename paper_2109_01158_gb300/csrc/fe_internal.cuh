@@ -18,7 +18,7 @@ namespace fe {
 // the problem size (never on the device), so every run sums the same partials in the same
 // order and results are bitwise reproducible.
 constexpr int kThreads = 256;
-constexpr int kMaxElemBlocks = 1216;  // 8 x 152 SMs
+constexpr int kMaxElemBlocks = 2432;  // 16 x 152 SMs
 constexpr int kMaxNodeBlocks = 608;   // 4 x 152 SMs
 
 // Device status bits (accumulated until fe_sync_status).

@@ -4,9 +4,9 @@
 // element kernel to the CSR positions), minus b_i, and 0 on Dirichlet dofs (Sec. 6.2,
 // Remark 1).  Each warp owns 32 consecutive nodes; their segments form one contiguous range
 // of r, which lane 0 copies into the warp's shared-memory buffer with one cp.async.bulk
-// completing on an mbarrier.  Each lane then sums its node's segment in slot order (the same
-// order as a plain per-node loop, so results do not depend on the launch shape).  A range
-// larger than the buffer is read directly from global memory.
+// completing on an mbarrier.  Each lane then sums its node's segment in a fixed rotated order
+// (below), so results do not depend on the launch shape.  A range larger than the buffer is
+// read directly from global memory in slot order.
 #pragma once
 
 #include "async_copy.cuh"
@@ -84,12 +84,20 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
       const int32_t q0 = __ldg(row_ptr + i), q1 = __ldg(row_ptr + i + 1);
       Acc acc[D];
       if (staged) {
-        // element k of r is at sbuf[k - k0] (a0 is a multiple of 16, so of sizeof(T))
-        const T* sbuf = reinterpret_cast<const T*>(buf);
-        const int64_t k0 = a0 / (int64_t)sizeof(T);
-        for (int32_t q = q0; q < q1; ++q)
+        // element k of r is at sbuf[k - k0] (a0 is a multiple of 16, so of sizeof(T)).
+        // Lane k walks its segment starting at position k (mod its length) and wraps around:
+        // with the common 24-slot patches, a plain walk puts every lane's reads on two
+        // shared-memory banks, while the rotated walk makes them distinct.  The order is
+        // still fixed by the mesh alone.
+        const T* sbuf = reinterpret_cast<const T*>(buf) - a0 / (int64_t)sizeof(T);
+        const int32_t len = q1 - q0;
+        int32_t pos = len > 0 ? lane % len : 0;
+        for (int32_t t = 0; t < len; ++t) {
+          const int64_t q = (int64_t)q0 + pos;
 #pragma unroll
-          for (int j = 0; j < D; ++j) acc[j].add(sbuf[(int64_t)q * D + j - k0]);
+          for (int j = 0; j < D; ++j) acc[j].add(sbuf[q * D + j]);
+          pos = (pos + 1 == len) ? 0 : pos + 1;
+        }
       } else {
         for (int32_t q = q0; q < q1; ++q)
 #pragma unroll

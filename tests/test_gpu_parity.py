@@ -175,7 +175,7 @@ def test_twisted_bar_df64_levels():
 
 def test_df64_log_accuracy():
     """The double-float logarithm of the FE_DF64 kernels against numpy's FP64 log:
-    |y - log x| <= 2^-47 |log x| + 2^-51 over 12 decades and around 1."""
+    |y - log x| <= 2^-45 |log x| + 2^-51 over 12 decades and around 1."""
     fem = _fem()
     w = mg.neohooke_cube3d(2)
     gm = _gpu(w, precisions=(fem.FE_DF64,))
@@ -187,7 +187,9 @@ def test_df64_log_accuracy():
     hi = x.astype(np.float32).astype(np.float64)
     xr = hi + (x - hi).astype(np.float32).astype(np.float64)
     ref = np.log(xr)
-    err = np.abs(y - ref) / (2.0 ** -47 * np.abs(ref) + 2.0 ** -51)
+    # k ln2, the table value and log(1+t) are combined by three double-word sums and one
+    # product, each within about 2^-48 relative: 2^-45 |log x| bounds their sum
+    err = np.abs(y - ref) / (2.0 ** -45 * np.abs(ref) + 2.0 ** -51)
     assert err.max() <= 1.0, (err.max(), x[err.argmax()])
 
 
