@@ -336,6 +336,8 @@ def run_ours(args, rank, world, local):
         "stages": stages, "variants": variants,
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
+    if rank == 0 and not args.no_serve:
+        line["serving"] = run_serving(args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ws = oracle_sample(w, args.sample_fraction)
         ts = time_oracle(ws, 2)
@@ -346,6 +348,36 @@ def run_ours(args, rank, world, local):
                        f"gradient, best of 2, single thread")}
     gm.close()
     return line if rank == 0 else None
+
+
+def run_serving(args, device):
+    """Continuous batching vs one request at a time on the same GPU and kernels (FE_DF64):
+    512 requests (50% 2D p-Laplacian p in {1.5, 2, 3}, 30% 2D Neo-Hookean, 20% 3D
+    Neo-Hookean, 1e3-2e6 elements log-uniform, seed 3), Poisson arrivals at 0.5, 0.8, 0.95,
+    1.5 and 3 times the measured one-at-a-time capacity; p50/p99 latency = completion -
+    arrival."""
+    from paper_2109_01158_gb300 import serve
+    t0 = time.perf_counter()
+    cat = serve.Catalogue(device)
+    reqs = serve.make_requests(args.serve_requests, seed=3, rate=1.0, catalogue=cat)
+    setup_s = time.perf_counter() - t0
+    server = serve.Server(cat, hbm_budget=args.serve_budget_gb << 30)
+    serve.serial_capacity(server, reqs[:32])                 # warm-up
+    cap = serve.serial_capacity(server, reqs)
+    out = {"requests": len(reqs), "precision": "df64", "catalogue_meshes": len(cat.meshes),
+           "resident_bytes": cat.bytes(), "setup_s": setup_s, "serial_capacity_req_s": cap,
+           "hbm_budget_bytes": server.budget, "loads": []}
+    burst = [serve.Request(r.rid, r.key, 0.0, r.v, ne=r.ne) for r in reqs]
+    out["batched_capacity_req_s"] = server.run(burst, mode="batched", keep_results=False).req_per_s
+    for load in (0.5, 0.8, 0.95, 1.5, 3.0):
+        rate = load * cap
+        rec = {"load": load, "rate_req_s": rate}
+        for mode in ("batched", "serial"):
+            st = server.run(serve.retime(reqs, rate, seed=3), mode=mode, keep_results=False)
+            rec[mode] = {k: st.as_dict()[k] for k in ("p50_ms", "p99_ms", "mean_ms", "req_per_s",
+                                                       "gelem_per_s", "max_batch", "steps", "wall_s")}
+        out["loads"].append(rec)
+    return out
 
 
 def main():
@@ -359,6 +391,9 @@ def main():
     ap.add_argument("--order", type=int, default=0, help="0 generator order, 1 Morton")
     ap.add_argument("--sample-fraction", type=float, default=0.125)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-budget-gb", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

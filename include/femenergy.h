@@ -189,6 +189,37 @@ fe_status fe_profile_enable(fe_ctx* ctx, int enable);
 fe_status fe_profile_read(fe_ctx* ctx, double* ms_host, int64_t* launches_host, int n_stages);
 
 
+/* ---- Batched evaluation over many resident meshes (serving) -------------------------
+ * Not in the paper: evaluates J and the exact gradient (same definitions as
+ * fe_energy_gradient, double-float arithmetic as FE_DF64) for many independent requests,
+ * each on its own precomputed mesh, in three kernel launches whatever their number.  Every
+ * request's partial sums are reduced in an order fixed by its own mesh, so its J and g are
+ * bitwise the same alone and in any mix of requests (they can differ in the last bits from
+ * fe_energy_gradient, whose reduction tree is shaped by the grid). */
+typedef struct fe_batch fe_batch;
+
+typedef struct {
+    const fe_ctx* mesh; /* precomputed with FE_DF64 and given a model; only read              */
+    const double* v;    /* device, n_nodes*d doubles (caller's dof order)                       */
+    double* J;          /* device, one double                                                   */
+    double* g;          /* device, n_nodes*d doubles                                             */
+    void* work;         /* device scratch of fe_batch_work_bytes(mesh) bytes, 256-byte aligned;  */
+                        /* owned by the caller, one per request in flight                       */
+} fe_batch_item;
+
+/* Bytes of device scratch one request on `mesh` needs. */
+fe_status fe_batch_work_bytes(const fe_ctx* mesh, size_t* bytes);
+/* Create a batch executor on `device` enqueuing on `cuda_stream`. */
+fe_status fe_batch_create(fe_batch** out, int device, void* cuda_stream);
+fe_status fe_batch_destroy(fe_batch* b);
+/* Enqueue one evaluation of every item (asynchronous; the host descriptors are copied before
+ * the call returns).  Items of one call must use distinct `work` buffers.  Neo-Hookean items
+ * with some det F <= 0 get J = +Inf and fe_batch_sync_status returns FE_EDOMAIN. */
+fe_status fe_batch_energy_gradient(fe_batch* b, const fe_batch_item* items, int n_items);
+/* Synchronise the batch stream; FE_EDOMAIN if an item had det F <= 0 since the last call. */
+fe_status fe_batch_sync_status(fe_batch* b);
+fe_status fe_batch_launch_count(const fe_batch* b, int64_t* count);
+
 /* Energy without any allocation (the paper has no counterpart: this is an interface for
  * callers that cannot let this library allocate device memory -- a host program whose GPU
  * memory is owned entirely by its own pool allocator, or one whose time-critical loop must

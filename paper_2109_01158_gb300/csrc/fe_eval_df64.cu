@@ -14,6 +14,7 @@
 //                   copies: gather_bulk.cuh), converted to FP64, - b
 #include "df64.cuh"
 #include "fe_internal.cuh"
+#include "elem_df.cuh"
 #include "gather_bulk.cuh"
 
 namespace fe {
@@ -58,60 +59,6 @@ __device__ __forceinline__ void finish_energy(double block_total, double* partia
     *J = s - t;
     *counter = 0u;
   }
-}
-
-__device__ __forceinline__ df ld_df(const float2* __restrict__ p, int64_t i) {
-  const float2 a = __ldg(p + i);
-  return {a.x, a.y};
-}
-
-// Node record of the double-float displacement: D pairs, padded to 4 pairs in 3D.
-template <int D>
-__device__ __forceinline__ void load_u_df(const float2* __restrict__ u, int32_t n, df* out) {
-  if (D == 1) {
-    out[0] = ld_df(u, n);
-  } else if (D == 2) {
-    const float4 a = __ldg(reinterpret_cast<const float4*>(u) + n);
-    out[0] = {a.x, a.y};
-    out[1] = {a.z, a.w};
-  } else {
-    const float4* p = reinterpret_cast<const float4*>(u) + 2 * (int64_t)n;
-    const float4 a = __ldg(p), b = __ldg(p + 1);
-    out[0] = {a.x, a.y};
-    out[1] = {a.z, a.w};
-    out[2] = {b.x, b.y};
-  }
-}
-
-// Sum of squares of N double-floats: exact leading products, TwoSum chain.
-template <int N>
-__device__ __forceinline__ df df_sumsq(const df* x) {
-  float s = fmul(x[0].hi, x[0].hi);
-  float e = fmaf(x[0].hi, x[0].hi, -s);
-  e = fmaf(fmul(2.f, x[0].hi), x[0].lo, e);
-#pragma unroll
-  for (int i = 1; i < N; ++i) {
-    const float p = fmul(x[i].hi, x[i].hi);
-    e = fadd(e, fmaf(x[i].hi, x[i].hi, -p));
-    e = fmaf(fmul(2.f, x[i].hi), x[i].lo, e);
-    const df t = two_sum(s, p);
-    s = t.hi;
-    e = fadd(e, t.lo);
-  }
-  return fast_two_sum(s, e);
-}
-
-// Model constants as double-floats.
-struct ModelDF {
-  df C1, D1, twoC1, twoD1, negTwoC1;
-  int pcase;     // p-Laplacian: 2, 3, 4, 15 (p = 1.5) in double-float; 0 = general p (FP64)
-  double p;
-};
-
-// General p-Laplacian exponent: W = s^(p/2)/p and the coefficient s^((p-2)/2) in FP64.
-__device__ __noinline__ void plap_general_f64(double s, double p, double* W, double* coef) {
-  *W = s > 0.0 ? pow(s, 0.5 * p) / p : 0.0;
-  *coef = s > 0.0 ? pow(s, 0.5 * (p - 2.0)) : 0.0;
 }
 
 template <int D, bool NH, int DIM>
@@ -162,134 +109,22 @@ __global__ void __launch_bounds__(kThreads) k_elem_df(
     __syncthreads();
   }
   df acc = {0.f, 0.f};
-  bool bad = false;
+  bool bad = false, inf_seen = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
-    df ul[K][D];
-#pragma unroll
-    for (int l = 0; l < K; ++l) load_u_df<D>(u, __ldg(elems + (int64_t)l * ne + e), ul[l]);
-    df g[DIM][DIM];
-#pragma unroll
-    for (int l = 0; l < DIM; ++l)
-#pragma unroll
-      for (int m = 0; m < DIM; ++m) g[l][m] = ld_df(dphi, ((int64_t)l * DIM + m) * ne + e);
-    const df vT = ld_df(vol, e);
-    // H_jm = sum_{l>=1} (u_l - u_0)_j dphi_lm
-    df H[D][DIM];
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      df a[DIM];
-#pragma unroll
-      for (int l = 0; l < DIM; ++l) a[l] = df_sub(ul[l + 1][j], ul[0][j]);
-#pragma unroll
-      for (int m = 0; m < DIM; ++m)
-        H[j][m] = (DIM == 3) ? df_dot3(a[0], g[0][m], a[1], g[1][m], a[DIM - 1], g[DIM - 1][m])
-                             : df_dot2(a[0], g[0][m], a[DIM - 1], g[DIM - 1][m]);
+    df vT;
+    const df W = elem_df_one<DIM, D, MODEL, ENERGY || DENS, GRAD>(e, ne, elems, dphi, vol, u, slot, md, tab, r,
+                                                                 bad, vT);
+    // W = +Inf (det F <= 0) would turn into NaN inside the double-float product: carry it aside
+    if (ENERGY) {
+      if (isinf(W.hi)) inf_seen = true;
+      else acc = df_fma(vT, W, acc);
     }
-    df W = {0.f, 0.f};
-    df P[D][DIM];
-    if (MODEL == FE_NEOHOOKE) {
-      df F[DIM][DIM], C[DIM][DIM], det;
-#pragma unroll
-      for (int j = 0; j < DIM; ++j)
-#pragma unroll
-        for (int m = 0; m < DIM; ++m) F[j][m] = (j == m) ? df_add_f(H[j][m], 1.0f) : H[j][m];
-      if (DIM == 3) {
-        C[0][0] = df_det2(F[1][1], F[2][2], F[1][2], F[2][1]);
-        C[0][1] = df_det2(F[1][2], F[2][0], F[1][0], F[2][2]);
-        C[0][2] = df_det2(F[1][0], F[2][1], F[1][1], F[2][0]);
-        det = df_dot3(F[0][0], C[0][0], F[0][1], C[0][1], F[0][DIM - 1], C[0][DIM - 1]);
-        if (GRAD) {
-          C[1][0] = df_det2(F[0][2], F[2][1], F[0][1], F[2][2]);
-          C[1][1] = df_det2(F[0][0], F[2][2], F[0][2], F[2][0]);
-          C[1][2] = df_det2(F[0][1], F[2][0], F[0][0], F[2][1]);
-          C[2][0] = df_det2(F[0][1], F[1][2], F[0][2], F[1][1]);
-          C[2][1] = df_det2(F[0][2], F[1][0], F[0][0], F[1][2]);
-          C[2][2] = df_det2(F[0][0], F[1][1], F[0][1], F[1][0]);
-        }
-      } else {
-        C[0][0] = F[1][1];
-        C[0][1] = df_neg(F[1][0]);
-        C[1][0] = df_neg(F[0][1]);
-        C[1][1] = F[0][0];
-        det = df_det2(F[0][0], F[1][1], F[0][1], F[1][0]);
-      }
-      const bool ebad = !(det.hi > 0.f);
-      const df delta = df_add_f(det, -1.0f);
-      if (ENERGY || DENS) {
-        // W = C1 (I1 - dim - 2 log det F) + D1 (det F - 1)^2, with I1 - dim = 2 tr H + |H|^2
-        df tr = H[0][0];
-#pragma unroll
-        for (int j = 1; j < DIM; ++j) tr = df_add(tr, H[j][j]);
-        const df hsq = df_sumsq<D * DIM>(&H[0][0]);
-        const df lg = df_log(ebad ? df{1.f, 0.f} : det, tab);
-        const df br = df_add(df_add(df_scale(tr, 2.f), hsq), df_scale(lg, -2.f));
-        W = df_dot2(md.C1, br, md.D1, df_sqr(delta));
-        if (ebad) W = {CUDART_INF_F, 0.f};
-      }
-      if (GRAD) {
-        // dW/dF = 2 C1 F + (2 D1 (det F - 1) - 2 C1 / det F) cof F, times |T|
-        const df rJ = df_rcp(det);
-        const df a = df_mul(md.twoC1, vT);
-        const df c = df_mul(vT, df_dot2(md.twoD1, delta, md.negTwoC1, rJ));
-#pragma unroll
-        for (int j = 0; j < D; ++j)
-#pragma unroll
-          for (int m = 0; m < DIM; ++m) P[j][m] = df_dot2(a, F[j][m], c, C[j][m]);
-      }
-      bad |= ebad;
-    } else {
-      const df s = df_sumsq<DIM>(&H[0][0]);
-      df coef = {1.f, 0.f};
-      if (md.pcase == 2) {
-        W = df_scale(s, 0.5f);
-      } else if (md.pcase == 3) {
-        coef = df_sqrt(s);
-        W = df_mul(df_mul(s, coef), df{0x1.555556p-2f, -0x1.555556p-27f});
-      } else if (md.pcase == 4) {
-        coef = s;
-        W = df_scale(df_sqr(s), 0.25f);
-      } else if (md.pcase == 15) {
-        const df q = df_sqrt(s), qq = df_sqrt(q);                // s^(1/2), s^(1/4)
-        W = df_mul(df_mul(q, qq), df{0x1.555556p-1f, -0x1.555556p-26f});   // s^(3/4) / 1.5
-        coef = (qq.hi > 0.f) ? df_rcp(qq) : df{0.f, 0.f};        // s^(-1/4)
-      } else {
-        double Wd, cd;
-        plap_general_f64(df_to_double(s), md.p, &Wd, &cd);
-        W = df_from_double(Wd);
-        coef = df_from_double(cd);
-      }
-      if (GRAD) {
-        const df c = df_mul(vT, coef);
-#pragma unroll
-        for (int m = 0; m < DIM; ++m) P[0][m] = df_mul(c, H[0][m]);
-      }
-    }
-    if (ENERGY) acc = df_fma(vT, W, acc);
     if (DENS) dens[eperm ? (int64_t)eperm[e] : e] = df_to_double(W);
-    if (GRAD) {
-      df r0[D];
-#pragma unroll
-      for (int j = 0; j < D; ++j) r0[j] = {0.f, 0.f};
-#pragma unroll
-      for (int l = 1; l <= DIM; ++l) {
-        const int64_t q = __ldg(slot + (int64_t)l * ne + e);
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-          const df s = (DIM == 3) ? df_dot3(P[j][0], g[l - 1][0], P[j][1], g[l - 1][1], P[j][DIM - 1], g[l - 1][DIM - 1])
-                                  : df_dot2(P[j][0], g[l - 1][0], P[j][DIM - 1], g[l - 1][DIM - 1]);
-          r[q * D + j] = make_float2(s.hi, s.lo);
-          r0[j] = df_sub(r0[j], s);
-        }
-      }
-      const int64_t q0 = __ldg(slot + e);
-#pragma unroll
-      for (int j = 0; j < D; ++j) r[q0 * D + j] = make_float2(r0[j].hi, r0[j].lo);
-    }
   }
   if (bad) atomicOr(status, kStatusDomain);
   if (ENERGY) {
-    const double t = block_sum(df_to_double(acc), sh);
+    const double t = block_sum(inf_seen ? CUDART_INF : df_to_double(acc), sh);
     finish_energy(t, partials, gridDim.x, node_partials, n_node_blocks, counter, J, sh);
   }
 }

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kTile, 20) k_elem_f32(
       if (t < ntiles) tile_issue(A, L, smem + k * L.stage_bytes, &bars[k], t, ne);
     }
   FPair acc;
-  bool bad = false;
+  bool bad = false, inf_seen = false;
   const float C1 = (float)mp.C1, D1 = (float)mp.D1;
   int it = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -380,7 +380,10 @@ __global__ void __launch_bounds__(kTile, 20) k_elem_f32(
         for (int m = 0; m < DIM; ++m) P[0][m] = cf * H[0][m];
       }
     }
-    if (ENERGY) acc.add(vT * W);
+    if (ENERGY) {
+      if (isinf(W)) inf_seen = true;   // +Inf would become NaN inside TwoSum
+      else acc.add(vT * W);
+    }
     if (DENS) dens[eperm ? (int64_t)eperm[e] : e] = (double)W;
     if (GRAD) {
       float r0[D];
@@ -409,7 +412,7 @@ __global__ void __launch_bounds__(kTile, 20) k_elem_f32(
   }
   if (bad) atomicOr(status, kStatusDomain);
   if (ENERGY) {
-    const double t = block_sum_nt<kTile>(acc.value(), sh);
+    const double t = block_sum_nt<kTile>(inf_seen ? CUDART_INF : acc.value(), sh);
     finish_energy_nt<kTile>(t, partials, gridDim.x, node_partials, n_node_blocks, counter, J, sh);
   }
 }

@@ -65,6 +65,12 @@ _SIGNATURES = {
     "fe_profile_enable": [_vp, _int],
     "fe_profile_read": [_vp, _vp, _vp, _int],
     "fe_diag_df64_log": [_vp, _vp, _vp, _i64],
+    "fe_batch_work_bytes": [_vp, _vp],
+    "fe_batch_create": [_vp, _int, _vp],
+    "fe_batch_destroy": [_vp],
+    "fe_batch_energy_gradient": [_vp, _vp, _int],
+    "fe_batch_sync_status": [_vp],
+    "fe_batch_launch_count": [_vp, _vp],
     "fe_energy_noalloc": [_int, _vp, _int, _int, _int, _dbl, _dbl, _dbl, _i64, _vp, _i64, _vp, _vp,
                           _vp, _vp, _vp, _vp],
 }
@@ -136,6 +142,70 @@ fe_profile_enable = _checked("fe_profile_enable")
 fe_profile_read = _checked("fe_profile_read")
 fe_energy_noalloc = _checked("fe_energy_noalloc")
 fe_diag_df64_log = _checked("fe_diag_df64_log")
+fe_batch_work_bytes = _checked("fe_batch_work_bytes")
+fe_batch_create = _checked("fe_batch_create")
+fe_batch_destroy = _checked("fe_batch_destroy")
+fe_batch_energy_gradient = _checked("fe_batch_energy_gradient")
+fe_batch_launch_count = _checked("fe_batch_launch_count")
+
+
+def fe_batch_sync_status(batch) -> int:
+    """Returns FE_OK or FE_EDOMAIN; raises on other errors."""
+    st = load_library().fe_batch_sync_status(batch)
+    if st not in (FE_OK, FE_EDOMAIN):
+        raise FEError(st, "fe_batch_sync_status", fe_last_error())
+    return st
+
+
+class BatchItem(ctypes.Structure):
+    """ctypes mirror of fe_batch_item."""
+    _fields_ = [("mesh", _vp), ("v", _vp), ("J", _vp), ("g", _vp), ("work", _vp)]
+
+
+class Batch:
+    """Batched executor (fe_batch) on one device and stream: `run(items)` enqueues one
+    energy + gradient evaluation of every (mesh, v, J, g, work) item in three launches."""
+
+    def __init__(self, device=0):
+        self.device = torch.device("cuda", device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream(self.device).cuda_stream
+            fe_batch_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream))
+        self.handle = h
+
+    @staticmethod
+    def work_bytes(mesh) -> int:
+        n = ctypes.c_size_t(0)
+        fe_batch_work_bytes(mesh.ctx, ctypes.byref(n))
+        return n.value
+
+    def run(self, items):
+        """items: list of (FEMesh, v, J, g, work) with device tensors; work is a uint8 tensor
+        of at least work_bytes(mesh) bytes whose data pointer is 256-byte aligned."""
+        arr = (BatchItem * max(len(items), 1))()
+        for k, (mesh, v, J, g, work) in enumerate(items):
+            arr[k] = BatchItem(mesh.ctx.value, v.data_ptr(), J.data_ptr(), g.data_ptr(), work.data_ptr())
+        fe_batch_energy_gradient(self.handle, arr, len(items))
+
+    def sync_status(self) -> int:
+        return fe_batch_sync_status(self.handle)
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int64(0)
+        fe_batch_launch_count(self.handle, ctypes.byref(n))
+        return n.value
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            fe_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 FE_PROFILE_STAGES = 5
 PROFILE_STAGE_NAMES = ("node_prep", "element", "gather", "fd_element", "fd_gather")

@@ -230,13 +230,14 @@ def test_no_elements_and_all_dirichlet():
     check_energy(J.item(), om.energy(w.v)[0], energy_scale(om, w.v))
 
 
-def test_inverted_element_reports_domain_error():
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["f64", "f32", "df64"])
+def test_inverted_element_reports_domain_error(precision):
     fem = _fem()
     w = mg.neohooke_cube3d(3)
     v = w.coords.ravel().copy()
     v[3 * 21] += 2.0
     w.v = v
-    gm = _gpu(w)
+    gm = _gpu(w, precisions=(precision,))
     J = gm.energy(_v(w))
     assert gm.sync_status() == fem.FE_EDOMAIN
     assert J.item() == math.inf
