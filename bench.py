@@ -52,6 +52,38 @@ F64_FLOPS_PER_TET = 250.0
 F64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+# DRAM traffic of the element kernels per launch, from an ncu capture (profiles/): valid only
+# while the kernel's sources hash to the value recorded with the capture.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+KERNEL_SOURCES = {
+    "f64": ["fe_eval_f64.cu", "fe_internal.cuh", "phi_table_f64.h"],
+    "df64": ["fe_eval_df64.cu", "elem_df.cuh", "df64.cuh", "fe_internal.cuh"],
+    "f32": ["fe_eval_f32.cu", "tile_stream.cuh", "async_copy.cuh", "df64.cuh", "fe_internal.cuh"],
+}
+
+
+def sources_sha256(prec):
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[prec]:
+        with open(os.path.join(ROOT, "paper_2109_01158_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(prec, dim, ne):
+    """DRAM bytes per launch of the element kernel scaled to ne elements, or None when there is
+    no capture for this kernel or its sources changed since."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh)[prec]
+    except Exception:
+        return None
+    if rec.get("dim") != dim or rec.get("sources_sha256") != sources_sha256(prec):
+        return None
+    return float(rec["bytes_per_element"]) * ne
+
+
 def load_peaks():
     try:
         with open(MEASURED_PEAKS) as fh:
@@ -289,6 +321,7 @@ def run_ours(args, rank, world, local):
     else:
         roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": hbm_achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind}
+    roof["traffic"] = recorded_traffic(prec, w.dim, w.ne)
     roof["kernel"] = "k_elem_%s (energy+gradient)" % prec
     roof["kernel_ms"] = elem_ms
     roof["algorithmic_bytes_per_launch"] = elem_bytes
@@ -338,6 +371,8 @@ def run_ours(args, rank, world, local):
     }
     if rank == 0 and not args.no_serve:
         line["serving"] = run_serving(args, local)
+    if rank == 0 and args.minimize:
+        line["minimize"] = run_minimize(args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ws = oracle_sample(w, args.sample_fraction)
         ts = time_oracle(ws, 2)
@@ -380,6 +415,60 @@ def run_serving(args, device):
     return out
 
 
+def run_minimize(args, device):
+    """End-to-end minimisation: 3D Neo-Hookean 64^3 x 6 tetrahedra (1,572,864), face x = 0
+    clamped, gravity f = (0, 0, -1e-2), E = 1e4, nu = 0.3, from v = X; L-BFGS (m = 10) on the
+    displacement u = v - X (FE_INPUT_DISPLACEMENT) until
+    ||g||_inf <= 1e-6 ||g_0||_inf, driven by the exact-gradient kernels (double-float, FP64,
+    FP32) and by the FP64 central-difference gradient (eps = 1e-6), and eight instances (load scaled by
+    1 + k/8, 32^3 x 6 each) in lockstep through the batched kernels."""
+    import numpy as np
+    import torch
+    from paper_2109_01158_gb300 import fem
+    from paper_2109_01158_gb300 import meshgen as mg
+    from paper_2109_01158_gb300.minimize import batch_evaluator, lbfgs, lbfgs_batched, mesh_evaluator
+    n = args.minimize_n
+    dev = torch.device("cuda", device)
+
+    def problem(scale=1.0, size=n):
+        w = mg.neohooke_cube3d(size)
+        w.f = np.tile([0.0, 0.0, -1e-2 * scale], w.nn)
+        w.v = w.coords.ravel().copy()
+        return w
+
+    w = problem()
+    gm = fem.FEMesh.from_workload(w, device=device, precisions=(fem.FE_DF64, fem.FE_F64, fem.FE_F32_COMP))
+    gm.set_input(fem.FE_INPUT_DISPLACEMENT)
+    v0 = torch.zeros(w.ndof, dtype=torch.float64, device=dev)     # u = 0, i.e. v = X
+    out = {"workload": f"neohooke3d_{n}^3x6 gravity (0,0,-1e-2), {w.ne} tets, {w.ndof} dofs",
+           "criterion": "||g||_inf <= 1e-6 ||g_0||_inf", "unknown": "displacement u = v - X",
+           "runs": {}}
+    for name, prec, grad in (("df64_exact", fem.FE_DF64, "exact"), ("f64_exact", fem.FE_F64, "exact"),
+                             ("f32_exact", fem.FE_F32_COMP, "exact"), ("f64_fd", fem.FE_F64, "fd")):
+        gm.set_precision(prec)
+        r = lbfgs(mesh_evaluator(gm, grad, eps=1e-6), v0, gtol=1e-6, relative=True, max_iter=args.minimize_iters)
+        out["runs"][name] = {"J": r.J, "iters": r.iters, "evals": r.evals, "converged": r.converged,
+                             "seconds": r.seconds, "gnorm": r.gnorm, "g0": r.history[0][1]}
+    ref = out["runs"]["df64_exact"]["J"]
+    for rec in out["runs"].values():
+        rec["J_rel_diff_vs_df64"] = abs(rec["J"] - ref) / abs(ref)
+    # eight instances of the problem on 32^3 x 6 (load scaled by 1 + k/8) in lockstep: one
+    # batched launch per line-search round evaluates every active instance's trial point
+    nl = max(n // 2, 4)
+    ws = [problem(1.0 + k / 8.0, nl) for k in range(8)]
+    meshes = [fem.FEMesh.from_workload(wk, device=device, precisions=(fem.FE_DF64,)) for wk in ws]
+    for m in meshes:
+        m.set_input(fem.FE_INPUT_DISPLACEMENT)
+    batch = fem.Batch(device)
+    rs = lbfgs_batched(batch_evaluator(batch, meshes, device),
+                       [torch.zeros(wk.ndof, dtype=torch.float64, device=dev) for wk in ws],
+                       gtol=1e-6, relative=True, max_iter=args.minimize_iters)
+    out[f"lockstep_8x{nl}^3x6"] = {"seconds": rs[0].seconds, "iters": [r.iters for r in rs],
+                                   "evals": [r.evals for r in rs],
+                                   "converged": all(r.converged for r in rs), "J": [r.J for r in rs]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,6 +483,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-budget-gb", type=int, default=8)
+    ap.add_argument("--minimize", action="store_true", help="also run the L-BFGS minimisation (64^3 x 6)")
+    ap.add_argument("--minimize-n", type=int, default=64)
+    ap.add_argument("--minimize-iters", type=int, default=20000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -64,6 +64,13 @@ typedef enum { FE_F64 = 0, FE_F32_COMP = 1, FE_DF64 = 2 } fe_precision;
 /* Internal node/element numbering used for the device layout (invisible to callers). */
 typedef enum { FE_ORDER_NONE = 0, FE_ORDER_MORTON = 1 } fe_order;
 
+/* Meaning of the vector v passed to the evaluation calls.  FE_INPUT_DEFORMATION: v is the
+ * deformation (the paper's unknown, Sec. 3), v = X + u for the Neo-Hookean model.
+ * FE_INPUT_DISPLACEMENT: v is the displacement u itself (Neo-Hookean only; the p-Laplacian
+ * ignores it) -- same J and gradient, but small displacements keep their full relative
+ * precision instead of being rounded to the spacing of doubles near X. */
+typedef enum { FE_INPUT_DEFORMATION = 0, FE_INPUT_DISPLACEMENT = 1 } fe_input;
+
 /* Library version (major*10000 + minor*100 + patch). */
 int fe_version(void);
 
@@ -117,6 +124,13 @@ fe_status fe_precompute(fe_ctx* ctx, unsigned precisions);
 
 /* Choose the arithmetic of later evaluation calls (must have been precomputed). */
 fe_status fe_set_precision(fe_ctx* ctx, int precision);
+
+/* Choose what the v argument of later evaluation calls (fe_energy ... fe_gradient_fd,
+ * fe_energy_gradient_host and the batched calls on this mesh) means: FE_INPUT_DEFORMATION
+ * (default) or FE_INPUT_DISPLACEMENT.  With displacements the energy is still
+ * J = sum |T| W(I + grad u) - b.(X + u), with b.X formed once per load (Neumaier sum) and
+ * b.u summed per call.  Any time after fe_create; FE_EINVAL for another value. */
+fe_status fe_set_input(fe_ctx* ctx, int input);
 
 /* Device bytes held by the context (mesh, precompute and work buffers). */
 fe_status fe_footprint(const fe_ctx* ctx, size_t* bytes);

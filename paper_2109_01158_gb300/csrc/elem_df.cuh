@@ -62,6 +62,24 @@ static __device__ __noinline__ void plap_general_f64(double s, double p, double*
   *coef = s > 0.0 ? pow(s, 0.5 * (p - 2.0)) : 0.0;
 }
 
+// phi(x) = x - log(1 + x) for x > -1.  For |x| <= 1/16 by the series of 2 atanh without any
+// cancellation: with s = x / (2 + x), phi = s x - 2 s^3 (1/3 + s^2/5 + s^4/7 + s^6/9 + s^8/11)
+// (|s| < 1/31, truncation below 2^-50 relative); otherwise x - log(1 + x) with the
+// table-driven logarithm (the difference then keeps about 2^-40 of phi).
+__device__ __forceinline__ df df_phi(df x, const LogEntry* tab) {
+  if (fabsf(x.hi) <= 0.0625f) {
+    const df s = df_mul(x, df_rcp(df_add_f(x, 2.0f)));
+    const df s2 = df_sqr(s);
+    const float t1 = fmaf(s2.hi, 1.0f / 11.0f, 1.0f / 9.0f);
+    df t = df_add(df{0x1.24924ap-3f, -0x1.b6db6ep-28f}, df_mul_f(s2, t1));         // 1/7 + s^2 t1
+    t = df_fma(s2, t, df{0x1.99999ap-3f, -0x1.99999ap-29f});                      // 1/5 + s^2 t
+    t = df_fma(s2, t, df{0x1.555556p-2f, -0x1.555556p-27f});                      // 1/3 + s^2 t
+    const df s3 = df_mul(s2, s);
+    return df_sub(df_mul(s, x), df_scale(df_mul(s3, t), 2.0f));
+  }
+  return df_sub(x, df_log(df_add_f(x, 1.0f), tab));
+}
+
 // One element: gathers the nodal values, forms H = grad u (eq. Dv) and returns W(F) when
 // WANT_W (eq. neoHook or eq. pLaplacian); when GRAD, also writes the local forces
 // r_{T,l} = |T| dW/dF grad(phi_l) (Sec. 6.2) to the CSR slots.  vT receives |T|; `bad` is set
@@ -97,16 +115,28 @@ __device__ __forceinline__ df elem_df_one(int64_t e, int64_t ne, const int32_t* 
     df W = {0.f, 0.f};
     df P[D][DIM];
     if (MODEL == FE_NEOHOOKE) {
-      df F[DIM][DIM], C[DIM][DIM], det;
+      // Displacement form of eq. neoHook with F = I + H (the same value, no cancellation of
+      // O(1) terms):  delta = det F - 1 = tr H + q with q = i2(H) + det H, and
+      //   I1 - dim - 2 log det F = |H|^2 - 2 q + 2 phi(delta),   phi(x) = x - log(1 + x).
+      df F[DIM][DIM], C[DIM][DIM];
 #pragma unroll
       for (int j = 0; j < DIM; ++j)
 #pragma unroll
         for (int m = 0; m < DIM; ++m) F[j][m] = (j == m) ? df_add_f(H[j][m], 1.0f) : H[j][m];
+      df tr = H[0][0];
+#pragma unroll
+      for (int j = 1; j < DIM; ++j) tr = df_add(tr, H[j][j]);
+      df q, X0 = {0.f, 0.f};
       if (DIM == 3) {
-        C[0][0] = df_det2(F[1][1], F[2][2], F[1][2], F[2][1]);
+        // C00 = 1 + X with X = H11 + H22 + M00 (M00 the minor of H); then
+        // q = M00 + H00 X + H01 C01 + H02 C02 exactly in real arithmetic
+        const df M00 = df_det2(H[1][1], H[DIM - 1][DIM - 1], H[1][DIM - 1], H[DIM - 1][1]);
+        const df X = df_add(df_add(H[1][1], H[DIM - 1][DIM - 1]), M00);
+        X0 = X;
+        C[0][0] = df_add_f(X, 1.0f);
         C[0][1] = df_det2(F[1][2], F[2][0], F[1][0], F[2][2]);
         C[0][2] = df_det2(F[1][0], F[2][1], F[1][1], F[2][0]);
-        det = df_dot3(F[0][0], C[0][0], F[0][1], C[0][1], F[0][DIM - 1], C[0][DIM - 1]);
+        q = df_add(M00, df_dot3(H[0][0], X, H[0][1], C[0][1], H[0][DIM - 1], C[0][DIM - 1]));
         if (GRAD) {
           C[1][0] = df_det2(F[0][2], F[2][1], F[0][1], F[2][2]);
           C[1][1] = df_det2(F[0][0], F[2][2], F[0][2], F[2][0]);
@@ -120,30 +150,53 @@ __device__ __forceinline__ df elem_df_one(int64_t e, int64_t ne, const int32_t* 
         C[0][1] = df_neg(F[1][0]);
         C[1][0] = df_neg(F[0][1]);
         C[1][1] = F[0][0];
-        det = df_det2(F[0][0], F[1][1], F[0][1], F[1][0]);
+        q = df_det2(H[0][0], H[1][1], H[0][1], H[1][0]);   // det H
       }
+      const df delta = df_add(tr, q);
+      const df det = df_add_f(delta, 1.0f);
       const bool ebad = !(det.hi > 0.f);
-      const df delta = df_add_f(det, -1.0f);
       if (WANT_W) {
-        // W = C1 (I1 - dim - 2 log det F) + D1 (det F - 1)^2, with I1 - dim = 2 tr H + |H|^2
-        df tr = H[0][0];
-#pragma unroll
-        for (int j = 1; j < DIM; ++j) tr = df_add(tr, H[j][j]);
         const df hsq = df_sumsq<D * DIM>(&H[0][0]);
-        const df lg = df_log(ebad ? df{1.f, 0.f} : det, tab);
-        const df br = df_add(df_add(df_scale(tr, 2.f), hsq), df_scale(lg, -2.f));
+        const df phi = ebad ? df{0.f, 0.f} : df_phi(delta, tab);
+        const df br = df_add(df_add(hsq, df_scale(q, -2.f)), df_scale(phi, 2.f));
         W = df_dot2(md.C1, br, md.D1, df_sqr(delta));
         if (ebad) W = {CUDART_INF_F, 0.f};
       }
       if (GRAD) {
-        // dW/dF = 2 C1 F + (2 D1 (det F - 1) - 2 C1 / det F) cof F, times |T|
+        // dW/dF = 2 C1 F + (2 D1 (det F - 1) - 2 C1 / det F) cof F, times |T|.  Near F = I the
+        // two terms cancel to O(|H|); a warp with any |H|^2 < 1e-4 uses the same value as
+        //   2 C1 (H - L) + 2 delta (D1 + C1 / det F) cof F,   L = cof F - I,
+        // with the diagonal L_jj formed from H without the 1 (no O(1) term left).
         const df rJ = df_rcp(det);
         const df a = df_mul(md.twoC1, vT);
-        const df c = df_mul(vT, df_dot2(md.twoD1, delta, md.negTwoC1, rJ));
+        float hs = 0.f;
 #pragma unroll
         for (int j = 0; j < D; ++j)
 #pragma unroll
-          for (int m = 0; m < DIM; ++m) P[j][m] = df_dot2(a, F[j][m], c, C[j][m]);
+          for (int m = 0; m < DIM; ++m) hs = fmaf(H[j][m].hi, H[j][m].hi, hs);
+        if (__any_sync(__activemask(), hs < 1e-4f)) {
+          df Ld[DIM];
+          if constexpr (DIM == 3) {
+            Ld[0] = X0;
+            Ld[1] = df_add(df_add(H[0][0], H[2][2]), df_det2(H[0][0], H[2][2], H[0][2], H[2][0]));
+            Ld[2] = df_add(df_add(H[0][0], H[1][1]), df_det2(H[0][0], H[1][1], H[0][1], H[1][0]));
+          } else {
+            Ld[0] = H[1][1];
+            Ld[1] = H[0][0];
+          }
+          const df cp = df_mul(vT, df_scale(df_mul(delta, df_add(md.D1, df_mul(md.C1, rJ))), 2.f));
+#pragma unroll
+          for (int j = 0; j < D; ++j)
+#pragma unroll
+            for (int m = 0; m < DIM; ++m)
+              P[j][m] = df_dot2(a, df_sub(H[j][m], j == m ? Ld[j] : C[j][m]), cp, C[j][m]);
+        } else {
+          const df c = df_mul(vT, df_dot2(md.twoD1, delta, md.negTwoC1, rJ));
+#pragma unroll
+          for (int j = 0; j < D; ++j)
+#pragma unroll
+            for (int m = 0; m < DIM; ++m) P[j][m] = df_dot2(a, F[j][m], c, C[j][m]);
+        }
       }
       bad |= ebad;
     } else {

@@ -440,6 +440,13 @@ fe_status fe_set_precision(fe_ctx* c, int precision) {
   return FE_OK;
 }
 
+fe_status fe_set_input(fe_ctx* c, int input) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  if (input != FE_INPUT_DEFORMATION && input != FE_INPUT_DISPLACEMENT) return set_error(FE_EINVAL, "bad input kind");
+  c->input = input;
+  return FE_OK;
+}
+
 fe_status fe_footprint(const fe_ctx* c, size_t* bytes) {
   if (!c || !bytes) return set_error(FE_EINVAL, "null argument");
   *bytes = c->bytes;

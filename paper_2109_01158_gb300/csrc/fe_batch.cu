@@ -3,7 +3,8 @@
 // One call evaluates J and grad J (Sec. 5 and 6.2, double-float arithmetic as FE_DF64) for a
 // list of independent requests, each on its own precomputed mesh, with three launches in
 // total whatever the number of requests:
-//   k_batch_prep     one block per 256-node tile of any request: u = v - X as double-floats
+//   k_batch_prep     one block per 256-node tile of any request: u = v - X (or u = v when the
+//                    mesh takes displacements) as double-floats
 //                    into the request's scratch, per-tile partial sums of b.v
 //   k_batch_elem     one block per 256-element tile of any request: W and the local forces
 //                    (elem_df_one, the same code as the single-mesh kernels), per-tile partial
@@ -35,7 +36,8 @@ struct BItem {
   const uint8_t* dir;
   const int32_t* perm;
   int64_t nn, ne;
-  int dim, d, model, pad;
+  int dim, d, model, disp;   // disp: v is the Neo-Hookean displacement u = v - X
+  double shift;             // b.X, added to the b.u partial of tile 0 when disp
   ModelDF md;
   const double* v;
   double* J;
@@ -87,7 +89,7 @@ __device__ __forceinline__ double prep_node(const BItem& it, int64_t i) {
   for (int j = 0; j < D; ++j) {
     const double vj = it.v[src * D + j];
     dot += it.b[i * D + j] * vj;
-    w[j] = df_from_double(NH ? vj - it.X[i * DIM + j] : vj);
+    w[j] = df_from_double((NH && !it.disp) ? vj - it.X[i * DIM + j] : vj);
   }
   if (DP == 4) w[3] = {0.f, 0.f};
   if (DP == 1) {
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(kBT) k_batch_prep(const BItem* __restrict__ it
     else dot = (it.dim == 3) ? prep_node<1, false, 3>(it, i) : prep_node<1, false, 2>(it, i);
   }
   dot = bblock_sum(dot, sh);
-  if (threadIdx.x == 0) it.npart[t] = dot;
+  if (threadIdx.x == 0) it.npart[t] = (t == 0 && it.disp) ? dot + it.shift : dot;
 }
 
 __global__ void __launch_bounds__(kBT) k_batch_elem(const BItem* __restrict__ items, int n,
@@ -333,7 +335,8 @@ fe_status fe_batch_energy_gradient(fe_batch* b, const fe_batch_item* items, int 
     it.dim = m->dim;
     it.d = m->d;
     it.model = m->model;
-    it.pad = 0;
+    it.disp = input_is_disp(m) ? 1 : 0;
+    it.shift = it.disp ? m->bX : 0.0;
     it.md = model_df_of(m);
     it.v = q.v;
     it.J = q.J;

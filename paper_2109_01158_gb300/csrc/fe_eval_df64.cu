@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(kThreads) k_node_prep_df(int64_t nn, const dou
                                                            const int32_t* __restrict__ perm,
                                                            const double* __restrict__ b,
                                                            float2* __restrict__ u,
-                                                           double* __restrict__ node_partials) {
+                                                           double* __restrict__ node_partials, bool disp,
+    double shift) {
   __shared__ double sh[kThreads / 32];
   constexpr int DP = D == 3 ? 4 : D;
   double dot = 0.0;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) k_node_prep_df(int64_t nn, const dou
     for (int j = 0; j < D; ++j) {
       const double vj = v[src * D + j];
       dot += b[i * D + j] * vj;
-      w[j] = df_from_double(NH ? vj - X[i * DIM + j] : vj);
+      w[j] = df_from_double((NH && !disp) ? vj - X[i * DIM + j] : vj);
     }
     if (DP == 4) w[3] = {0.f, 0.f};
     if (DP == 1) {
@@ -91,7 +92,8 @@ __global__ void __launch_bounds__(kThreads) k_node_prep_df(int64_t nn, const dou
     }
   }
   dot = block_sum(dot, sh);
-  if (threadIdx.x == 0) node_partials[blockIdx.x] = dot;
+  // block 0 adds b.X when v is a displacement (then dot sums b.u)
+  if (threadIdx.x == 0) node_partials[blockIdx.x] = (blockIdx.x == 0 && disp) ? dot + shift : dot;
 }
 
 template <int DIM, int D, int MODEL, bool ENERGY, bool GRAD, bool DENS>
@@ -179,7 +181,8 @@ fe_status evaldf_t(fe_ctx* c, const double* v, double* J, double* dens, double* 
   double* node_partials = c->partials + kMaxElemBlocks;
   prof_begin(c, kStagePrep);
   k_node_prep_df<D, MODEL == FE_NEOHOOKE, DIM><<<nb_node, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b,
-                                                                            c->u_df, node_partials);
+                                                                            c->u_df, node_partials, input_is_disp(c),
+                                                                            input_is_disp(c) ? c->bX : 0.0);
   prof_end(c, kStagePrep);
   c->launches++;
   const bool E = want_energy, G = want_grad, Dn = dens != nullptr;

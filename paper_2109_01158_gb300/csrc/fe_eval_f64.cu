@@ -67,32 +67,79 @@ __device__ __forceinline__ void finish_energy(double block_total, double* partia
 
 // ---- densities --------------------------------------------------------------------------
 
-// Compressible Neo-Hookean (eq. neoHook) for F = I + H in 3D, with its derivative
-// dW/dF = 2 C1 F + (2 D1 (det F - 1) - 2 C1 / det F) cof F, where cof F_jm = d det/dF_jm
-// = (-1)^(j+m) det(F^sub_jm) (Sec. 6.2).
-struct NH3 {
-  double F[3][3], C[3][3], det;
-  __device__ __forceinline__ void setup(const double H[3][3]) {
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int m = 0; m < 3; ++m) F[j][m] = (j == m) ? 1.0 + H[j][m] : H[j][m];
-    C[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
-    C[0][1] = F[1][2] * F[2][0] - F[1][0] * F[2][2];
-    C[0][2] = F[1][0] * F[2][1] - F[1][1] * F[2][0];
-    C[1][0] = F[0][2] * F[2][1] - F[0][1] * F[2][2];
-    C[1][1] = F[0][0] * F[2][2] - F[0][2] * F[2][0];
-    C[1][2] = F[0][1] * F[2][0] - F[0][0] * F[2][1];
-    C[2][0] = F[0][1] * F[1][2] - F[0][2] * F[1][1];
-    C[2][1] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
-    C[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
-    det = F[0][0] * C[0][0] + F[0][1] * C[0][1] + F[0][2] * C[0][2];
-  }
-};
+// ---- phi(x) = x - log(1 + x), x > -1 --------------------------------------------------------
+//
+// Breakpoints c_j = (j - FE_PHI_J0) / 256 with F_j = 1 + c_j; inside
+// [-76.5/256, 108.5/256) the nearest breakpoint gives x = c_j + f with |f| <= 1/512 (exact:
+// c_j is a multiple of 2^-8 within a factor 2 of x, Sterbenz' lemma), and with r = f / F_j
+//   phi(x) = (c_j - ln F_j) + f (1 - 1/F_j) + (r - log1p(r)),
+//   r - log1p(r) = r^2 (1/2 - r/3 + r^2/4 - r^3/5 + r^4/6 - r^5/7 + r^6/8) + O(r^10),
+// |r| < 2.8e-3, so the truncation is below 2^-53 of the last term.  The three terms never
+// cancel by more than about a factor 4, the table holds c_j - ln F_j to twice double
+// precision (hi + lo), and there is no division.  Outside the interval: x - log1p(x).
+#include "phi_table_f64.h"
 
-__device__ __forceinline__ double nh_density(double I1, double det, int dim, const ModelParams& mp) {
-  const double dm1 = det - 1.0;
-  return mp.C1 * (I1 - (double)dim - 2.0 * log(det)) + mp.D1 * dm1 * dm1;
+struct __align__(32) PhiRow {
+  double a_hi, a_lo, b, r;   // c_j - ln F_j (hi + lo), 1 - 1/F_j, 1/F_j
+};
+__device__ const PhiRow kPhiTab[FE_PHI_N] = {FE_PHI_TABLE_ROWS};
+
+__device__ __noinline__ double phi_f64_wide(double x) { return x - log1p(x); }
+
+__device__ __forceinline__ double phi_f64(double x) {
+  constexpr double kLo = -(FE_PHI_J0 + 0.5) / FE_PHI_SCALE;
+  constexpr double kHi = (FE_PHI_N - FE_PHI_J0 - 0.5) / FE_PHI_SCALE;
+  if (!(x >= kLo && x < kHi)) return phi_f64_wide(x);
+  // round(256 x) by the 1.5 * 2^52 shift: t = 1.5 * 2^52 + round(256 x) exactly
+  const double t = fma(x, (double)FE_PHI_SCALE, 0x1.8p52);
+  const double c = (t - 0x1.8p52) * (1.0 / FE_PHI_SCALE);
+  int j = __double2loint(t) + FE_PHI_J0;
+  j = min(max(j, 0), FE_PHI_N - 1);
+  const double2* row = reinterpret_cast<const double2*>(kPhiTab + j);
+  const double2 A = __ldg(row), BR = __ldg(row + 1);
+  const double f = x - c;
+  const double r = f * BR.y;
+  double p = 1.0 / 8.0;
+  p = fma(p, r, -1.0 / 7.0);
+  p = fma(p, r, 1.0 / 6.0);
+  p = fma(p, r, -1.0 / 5.0);
+  p = fma(p, r, 1.0 / 4.0);
+  p = fma(p, r, -1.0 / 3.0);
+  p = fma(p, r, 1.0 / 2.0);
+  const double psi = (r * r) * p;
+  return A.x + (A.y + fma(f, BR.x, psi));
+}
+
+// Compressible Neo-Hookean density (eq. neoHook) at F = I + H in displacement form:
+// delta = det F - 1 = tr H + q with q = i2(H) + det H (3D: q = M00 + H00 X + H01 C01 + H02 C02,
+// the row-0 cofactor expansion of det(I + H) minus its O(1) and trace terms), and
+//   W = C1 (|H|^2 - 2 q + 2 phi(delta)) + D1 delta^2,
+// the same value as C1 (I1 - dim - 2 log det F) + D1 (det F - 1)^2 with rounding relative to
+// the size of W instead of C1 dim.  +Inf (and bad) when det F <= 0.
+template <int DIM>
+__device__ __forceinline__ double nh_density_disp(const double H[DIM][DIM], const ModelParams& mp, bool& bad) {
+  double tr = 0.0, hsq = 0.0, q;
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) {
+    tr += H[j][j];
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) hsq = fma(H[j][m], H[j][m], hsq);
+  }
+  if constexpr (DIM == 3) {
+    const double M00 = H[1][1] * H[2][2] - H[1][2] * H[2][1];
+    const double X = H[1][1] + H[2][2] + M00;
+    const double C01 = H[1][2] * H[2][0] - H[1][0] * (1.0 + H[2][2]);
+    const double C02 = H[1][0] * H[2][1] - (1.0 + H[1][1]) * H[2][0];
+    q = M00 + H[0][0] * X + H[0][1] * C01 + H[0][2] * C02;
+  } else {
+    q = H[0][0] * H[1][1] - H[0][1] * H[1][0];
+  }
+  const double delta = tr + q;
+  if (!(1.0 + delta > 0.0)) {
+    bad = true;
+    return CUDART_INF;
+  }
+  return mp.C1 * (hsq - 2.0 * q + 2.0 * phi_f64(delta)) + mp.D1 * delta * delta;
 }
 
 __device__ __forceinline__ double plap_density(double s, const ModelParams& mp) {
@@ -133,7 +180,8 @@ __global__ void __launch_bounds__(kThreads) k_node_prep(int64_t nn, const double
                                                         const int32_t* __restrict__ perm,
                                                         const double* __restrict__ b,
                                                         double* __restrict__ u,
-                                                        double* __restrict__ node_partials) {
+                                                        double* __restrict__ node_partials, bool disp,
+    double shift) {
   __shared__ double sh[kThreads / 32];
   constexpr int DP = D == 3 ? 4 : D;
   double dot = 0.0;
@@ -145,7 +193,7 @@ __global__ void __launch_bounds__(kThreads) k_node_prep(int64_t nn, const double
     for (int j = 0; j < D; ++j) {
       const double vj = v[src * D + j];
       dot += b[i * D + j] * vj;
-      w[j] = NH ? vj - X[i * DIM + j] : vj;
+      w[j] = (NH && !disp) ? vj - X[i * DIM + j] : vj;
     }
     if (DP == 4) w[3] = 0.0;
     if (DP == 1) {
@@ -157,7 +205,8 @@ __global__ void __launch_bounds__(kThreads) k_node_prep(int64_t nn, const double
     }
   }
   dot = block_sum(dot, sh);
-  if (threadIdx.x == 0) node_partials[blockIdx.x] = dot;
+  // block 0 adds b.X when v is a displacement (then dot sums b.u)
+  if (threadIdx.x == 0) node_partials[blockIdx.x] = (blockIdx.x == 0 && disp) ? dot + shift : dot;
 }
 
 // Element kernel: energy partials, densities, and/or local forces.
@@ -201,51 +250,77 @@ __global__ void __launch_bounds__(kThreads) k_elem_f64(
     double W = 0.0;
     double P[D][DIM];
     if (MODEL == FE_NEOHOOKE) {
-      double det, I1 = 0.0, Fm[DIM][DIM], Cm[DIM][DIM];
+      // Displacement form of eq. neoHook with F = I + H (same value, no cancellation of O(1)
+      // terms): delta = det F - 1 = tr H + q, q = i2(H) + det H, and
+      //   I1 - dim - 2 log det F = |H|^2 - 2 q + 2 phi(delta),  phi(x) = x - log(1 + x).
+      double Fm[DIM][DIM], Cm[DIM][DIM], q, tr = 0.0, hsq = 0.0, X0 = 0.0;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        tr += H[j][j];
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) {
+          Fm[j][m] = (j == m) ? 1.0 + H[j][m] : H[j][m];
+          hsq = fma(H[j][m], H[j][m], hsq);
+        }
+      }
       if (DIM == 3) {
-        NH3 nh;
-        double H3[3][3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-          for (int m = 0; m < 3; ++m) H3[j][m] = H[j][m];
-        nh.setup(H3);
-        det = nh.det;
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            Fm[j][m] = nh.F[j][m];
-            Cm[j][m] = nh.C[j][m];
-          }
+        const double M00 = H[1][1] * H[DIM - 1][DIM - 1] - H[1][DIM - 1] * H[DIM - 1][1];
+        const double X = H[1][1] + H[DIM - 1][DIM - 1] + M00;
+        X0 = X;
+        Cm[0][0] = 1.0 + X;
+        Cm[0][1] = Fm[1][2] * Fm[2][0] - Fm[1][0] * Fm[2][2];
+        Cm[0][2] = Fm[1][0] * Fm[2][1] - Fm[1][1] * Fm[2][0];
+        Cm[1][0] = Fm[0][2] * Fm[2][1] - Fm[0][1] * Fm[2][2];
+        Cm[1][1] = Fm[0][0] * Fm[2][2] - Fm[0][2] * Fm[2][0];
+        Cm[1][2] = Fm[0][1] * Fm[2][0] - Fm[0][0] * Fm[2][1];
+        Cm[2][0] = Fm[0][1] * Fm[1][2] - Fm[0][2] * Fm[1][1];
+        Cm[2][1] = Fm[0][2] * Fm[1][0] - Fm[0][0] * Fm[1][2];
+        Cm[2][2] = Fm[0][0] * Fm[1][1] - Fm[0][1] * Fm[1][0];
+        q = M00 + H[0][0] * X + H[0][1] * Cm[0][1] + H[0][DIM - 1] * Cm[0][DIM - 1];
       } else {
-        Fm[0][0] = 1.0 + H[0][0];
-        Fm[0][1] = H[0][1];
-        Fm[1][0] = H[1][0];
-        Fm[1][1] = 1.0 + H[1][1];
         Cm[0][0] = Fm[1][1];
         Cm[0][1] = -Fm[1][0];
         Cm[1][0] = -Fm[0][1];
         Cm[1][1] = Fm[0][0];
-        det = Fm[0][0] * Fm[1][1] - Fm[0][1] * Fm[1][0];
+        q = H[0][0] * H[1][1] - H[0][1] * H[1][0];
       }
-#pragma unroll
-      for (int j = 0; j < DIM; ++j)
-#pragma unroll
-        for (int m = 0; m < DIM; ++m) I1 = fma(Fm[j][m], Fm[j][m], I1);
+      const double delta = tr + q;
+      const double det = 1.0 + delta;
       if (!(det > 0.0)) {
         bad = true;
         W = CUDART_INF;
       } else if (ENERGY || DENS) {
-        W = nh_density(I1, det, DIM, mp);
+        W = mp.C1 * (hsq - 2.0 * q + 2.0 * phi_f64(delta)) + mp.D1 * delta * delta;
       }
       if (GRAD) {
+        // dW/dF = 2 C1 F + (2 D1 delta - 2 C1 / det F) cof F.  Near F = I its two terms cancel
+        // to O(|H|), leaving a relative error of about u / |H|; a warp with any |H|^2 < 1e-4
+        // uses instead the same value as
+        //   2 C1 (H - L) + 2 delta (D1 + C1 / det F) cof F,   L = cof F - I,
+        // whose diagonal L_jj is formed from H without the 1 (no O(1) term left).
         const double a = 2.0 * mp.C1 * vT;
-        const double c = vT * (2.0 * mp.D1 * (det - 1.0) - 2.0 * mp.C1 / det);
+        if (__any_sync(__activemask(), hsq < 1e-4)) {
+          double Ld[DIM];
+          if constexpr (DIM == 3) {
+            Ld[0] = X0;
+            Ld[1] = H[0][0] + H[2][2] + (H[0][0] * H[2][2] - H[0][2] * H[2][0]);
+            Ld[2] = H[0][0] + H[1][1] + (H[0][0] * H[1][1] - H[0][1] * H[1][0]);
+          } else {
+            Ld[0] = H[1][1];
+            Ld[1] = H[0][0];
+          }
+          const double cp = 2.0 * vT * delta * (mp.D1 + mp.C1 / det);
 #pragma unroll
-        for (int j = 0; j < D; ++j)
+          for (int j = 0; j < D; ++j)
 #pragma unroll
-          for (int m = 0; m < DIM; ++m) P[j][m] = fma(a, Fm[j][m], c * Cm[j][m]);
+            for (int m = 0; m < DIM; ++m) P[j][m] = fma(a, H[j][m] - (j == m ? Ld[j] : Cm[j][m]), cp * Cm[j][m]);
+        } else {
+          const double c = vT * (2.0 * mp.D1 * delta - 2.0 * mp.C1 / det);
+#pragma unroll
+          for (int j = 0; j < D; ++j)
+#pragma unroll
+            for (int m = 0; m < DIM; ++m) P[j][m] = fma(a, Fm[j][m], c * Cm[j][m]);
+        }
       }
     } else {
       double s = 0.0;
@@ -335,32 +410,13 @@ __device__ __forceinline__ double fd_density(double ul[DIM + 1][D], const double
     for (int l = 1; l < DIM; ++l) s = fma(a[l], g[l][m], s);
     row[m] = s;
   }
-  if (MODEL == FE_NEOHOOKE) {
-    double F[DIM][DIM];
+  if constexpr (MODEL == FE_NEOHOOKE) {
+    double Hx[DIM][DIM];
 #pragma unroll
     for (int jj = 0; jj < DIM; ++jj)
 #pragma unroll
-      for (int m = 0; m < DIM; ++m) {
-        const double h = (jj == j) ? row[m] : H[jj][m];
-        F[jj][m] = (jj == m) ? 1.0 + h : h;
-      }
-    double det, I1 = 0.0;
-    if (DIM == 3) {
-      det = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) +
-            F[0][1] * (F[1][2] * F[2][0] - F[1][0] * F[2][2]) +
-            F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
-    } else {
-      det = F[0][0] * F[1][1] - F[0][1] * F[1][0];
-    }
-#pragma unroll
-    for (int jj = 0; jj < DIM; ++jj)
-#pragma unroll
-      for (int m = 0; m < DIM; ++m) I1 = fma(F[jj][m], F[jj][m], I1);
-    if (!(det > 0.0)) {
-      bad = true;
-      return CUDART_INF;
-    }
-    return nh_density(I1, det, DIM, mp);
+      for (int m = 0; m < DIM; ++m) Hx[jj][m] = (jj == j) ? row[m] : H[jj][m];
+    return nh_density_disp<DIM>(Hx, mp, bad);
   } else {
     double s = 0.0;
 #pragma unroll
@@ -536,7 +592,8 @@ fe_status eval_t(fe_ctx* c, const double* v, double* J, double* dens, double* g,
   double* node_partials = c->partials + kMaxElemBlocks;
   prof_begin(c, kStagePrep);
   k_node_prep<D, MODEL == FE_NEOHOOKE, DIM><<<nb_node, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b,
-                                                                         c->u, node_partials);
+                                                                         c->u, node_partials, input_is_disp(c),
+                                                                         input_is_disp(c) ? c->bX : 0.0);
   prof_end(c, kStagePrep);
   c->launches++;
   const bool E = want_energy, G = want_grad, Dn = dens != nullptr;
@@ -575,7 +632,8 @@ fe_status fd_t(fe_ctx* c, const double* v, double eps, double* g, const int64_t*
   const int nb_node = grid_for(c->nn, kMaxNodeBlocks);
   prof_begin(c, kStagePrep);
   k_node_prep<D, MODEL == FE_NEOHOOKE, DIM><<<nb_node, kThreads, 0, s>>>(
-      c->nn, v, c->X, c->perm, c->b, c->u, c->partials + kMaxElemBlocks);
+      c->nn, v, c->X, c->perm, c->b, c->u, c->partials + kMaxElemBlocks, input_is_disp(c),
+      input_is_disp(c) ? c->bX : 0.0);
   prof_end(c, kStagePrep);
   c->launches++;
   if (dofs) {

@@ -57,6 +57,8 @@ struct fe_ctx {
   int model = FE_NEOHOOKE;
   double p = 2.0, C1 = 0.0, D1 = 0.0;
   bool model_set = false;
+  int input = FE_INPUT_DEFORMATION;  // meaning of the v argument of the evaluation calls
+  double bX = 0.0;              // b.X (Neo-Hookean), added to b.u when v is a displacement
   std::vector<double> f_host;   // load in the caller's dof order (empty = 0)
   std::vector<int32_t> perm_h;  // device node -> caller node (empty = identity)
   std::vector<int32_t> eperm_h; // device element -> caller element (empty = identity)
@@ -102,6 +104,12 @@ struct fe_ctx {
   std::vector<cudaEvent_t> prof_ev[FE_PROFILE_STAGES];
   int prof_n[FE_PROFILE_STAGES] = {0};
 };
+
+// True when the v argument of an evaluation is the Neo-Hookean displacement u = v - X.
+inline bool input_is_disp(const fe_ctx* c) {
+  return c->model == FE_NEOHOOKE && c->input == FE_INPUT_DISPLACEMENT;
+}
+
 
 namespace fe {
 

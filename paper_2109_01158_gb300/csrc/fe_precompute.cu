@@ -4,6 +4,9 @@
 // The floating-point steps use the _rn intrinsics so that no multiply-add is contracted:
 // every value is produced by the same sequence of correctly rounded operations as the
 // plain definition, which makes this one-off step reproducible bit for bit.
+#include <cmath>
+#include <vector>
+
 #include "fe_internal.cuh"
 
 namespace fe {
@@ -313,8 +316,32 @@ fe_status launch_precompute(fe_ctx* c) {
   return c->dim == 2 ? precompute_dim<2>(c) : precompute_dim<3>(c);
 }
 
+// b.X for vector problems (d = dim): the constant part of b.v when the caller passes the
+// Neo-Hookean displacement u = v - X.  Neumaier sum in device node order on the host.
+static fe_status compute_bX(fe_ctx* c) {
+  c->bX = 0.0;
+  if (c->d != c->dim || c->nn == 0) return FE_OK;
+  const size_t n = (size_t)c->nn * c->d;
+  std::vector<double> bh(n), xh((size_t)c->nn * c->dim);
+  cudaMemcpyAsync(bh.data(), c->b, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(xh.data(), c->X, sizeof(double) * xh.size(), cudaMemcpyDeviceToHost, c->stream);
+  fe_status st = cuda_check(cudaStreamSynchronize(c->stream), "b.X read back");
+  if (st) return st;
+  double s = 0.0, comp = 0.0;
+  for (int64_t i = 0; i < c->nn; ++i)
+    for (int j = 0; j < c->d; ++j) {
+      const double t = bh[(size_t)i * c->d + j] * xh[(size_t)i * c->dim + j];
+      const double y = s + t;
+      comp += (std::fabs(s) >= std::fabs(t)) ? (s - y) + t : (t - y) + s;
+      s = y;
+    }
+  c->bX = s + comp;
+  return FE_OK;
+}
+
 fe_status launch_load_vector(fe_ctx* c) {
-  return c->dim == 2 ? load_vector_dim<2>(c) : load_vector_dim<3>(c);
+  const fe_status st = c->dim == 2 ? load_vector_dim<2>(c) : load_vector_dim<3>(c);
+  return st ? st : compute_bX(c);
 }
 
 }  // namespace fe

@@ -21,6 +21,7 @@ FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_EDOMAIN, FE_ETIMEOUT, FE_EBUSY = range
 FE_PLAPLACE, FE_NEOHOOKE = 0, 1
 FE_F64, FE_F32_COMP, FE_DF64 = 0, 1, 2
 FE_ORDER_NONE, FE_ORDER_MORTON = 0, 1
+FE_INPUT_DEFORMATION, FE_INPUT_DISPLACEMENT = 0, 1
 
 _STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "FE_EDOMAIN",
                  5: "FE_ETIMEOUT", 6: "FE_EBUSY"}
@@ -51,6 +52,7 @@ _SIGNATURES = {
     "fe_set_load": [_vp, _vp],
     "fe_precompute": [_vp, ctypes.c_uint],
     "fe_set_precision": [_vp, _int],
+    "fe_set_input": [_vp, _int],
     "fe_footprint": [_vp, _vp],
     "fe_energy": [_vp, _vp, _vp, _vp],
     "fe_gradient_exact": [_vp, _vp, _vp],
@@ -128,6 +130,7 @@ fe_set_model = _checked("fe_set_model")
 fe_set_load = _checked("fe_set_load")
 fe_precompute = _checked("fe_precompute")
 fe_set_precision = _checked("fe_set_precision")
+fe_set_input = _checked("fe_set_input")
 fe_footprint = _checked("fe_footprint")
 fe_energy = _checked("fe_energy")
 fe_gradient_exact = _checked("fe_gradient_exact")
@@ -263,6 +266,7 @@ class FEMesh:
         fe_precompute(self.ctx, mask)
         fe_set_precision(self.ctx, int(precisions[0]))
         self.precision = int(precisions[0])
+        self.input = FE_INPUT_DEFORMATION
 
     @classmethod
     def from_workload(cls, w, **kw):
@@ -286,6 +290,11 @@ class FEMesh:
     def set_precision(self, prec):
         fe_set_precision(self.ctx, int(prec))
         self.precision = int(prec)
+
+    def set_input(self, kind):
+        """FE_INPUT_DEFORMATION (v = X + u, default) or FE_INPUT_DISPLACEMENT (v = u)."""
+        fe_set_input(self.ctx, int(kind))
+        self.input = int(kind)
 
     # -- evaluation ----------------------------------------------------------------------
     def energy(self, v, densities=False):

@@ -1,0 +1,281 @@
+"""L-BFGS minimisation of J(v) driven by the energy + gradient kernels.
+
+The paper minimises with MATLAB's trust-region method (Sec. 7); this module replaces it by
+limited-memory BFGS (Nocedal & Wright, Numerical Optimization, Alg. 7.4 two-loop recursion)
+with a bracketing line search.  A step is accepted when it satisfies the weak Wolfe
+conditions or -- once energy differences reach the rounding level of J -- the approximate
+Wolfe conditions of Hager & Zhang (SIAM J. Optim. 16, 2005): J does not rise above
+J + eps_f |J| and the directional derivative satisfies sigma g.d <= g_new.d <= (2 c1 - 1) g.d.
+Iterates stay on the device; Dirichlet dofs never move because the gradient is 0 there.  A
+trial point with det F <= 0 has J = +Inf and is rejected like any point without decrease.
+
+`lbfgs` runs one minimisation through an evaluator `ev(v) -> (J, g)`; `lbfgs_batched` runs
+many instances in lockstep, evaluating every active instance's trial point in one batched
+launch (fe_batch_energy_gradient) per line-search round.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import torch
+
+
+@dataclass
+class LBFGSResult:
+    v: torch.Tensor
+    J: float
+    gnorm: float
+    iters: int
+    evals: int
+    converged: bool
+    seconds: float
+    history: list = field(default_factory=list)   # (J, ||g||_inf) per iteration
+
+
+def _gnorm(g):
+    return float(g.abs().max().item()) if g.numel() else 0.0
+
+
+class _LineSearch:
+    """Bracketing search for a step t > 0 along a descent direction d (phi(t) = J(v + t d)).
+
+    Accepts t when phi satisfies the weak Wolfe conditions -- sufficient decrease
+    phi(t) <= phi(0) + c1 t phi'(0) and curvature phi'(t) >= sigma phi'(0) -- or, once energy
+    differences are at the rounding level of J, the approximate Wolfe conditions of Hager &
+    Zhang: phi(t) <= phi(0) + eps_f |phi(0)| and sigma phi'(0) <= phi'(t) <= (2 c1 - 1) phi'(0).
+    A step that fails the decrease test (or gives J = +Inf) becomes the upper end of the
+    bracket; a step that passes it but is too short becomes the lower end.  Without an upper
+    end the step doubles; inside a bracket the next step is the secant root of phi' when both
+    ends carry derivatives of opposite sign (kept at least 10% of the bracket from each end),
+    else the midpoint."""
+
+    def __init__(self, J, gd, c1, sigma, eps_f, t0=1.0):
+        self.J, self.gd = J, gd
+        self.c1, self.sigma, self.eps_f = c1, sigma, eps_f
+        self.lo, self.d_lo = 0.0, gd
+        self.hi, self.d_hi = math.inf, None
+        self.t = t0
+
+    def update(self, J_new, gd_new):
+        """Feed phi(t), phi'(t) of the current trial; True when t is accepted."""
+        t = self.t
+        if not (math.isfinite(J_new) and math.isfinite(gd_new)):
+            self.hi, self.d_hi = t, None
+        else:
+            armijo = J_new <= self.J + self.c1 * t * self.gd
+            approx = (J_new <= self.J + self.eps_f * abs(self.J)
+                      and gd_new <= (2.0 * self.c1 - 1.0) * self.gd)
+            if not (armijo or approx):
+                self.hi, self.d_hi = t, gd_new
+            elif gd_new >= self.sigma * self.gd:
+                return True
+            else:
+                self.lo, self.d_lo = t, gd_new
+        if math.isinf(self.hi):
+            self.t = 2.0 * t
+            return False
+        lo, hi, w = self.lo, self.hi, self.hi - self.lo
+        nt = 0.5 * (lo + hi)
+        if self.d_hi is not None and self.d_lo < 0.0 < self.d_hi:
+            nt = lo - self.d_lo * w / (self.d_hi - self.d_lo)
+            nt = min(max(nt, lo + 0.1 * w), hi - 0.1 * w)
+        self.t = nt
+        return False
+
+
+class _State:
+    """L-BFGS state of one instance (m most recent pairs on the device)."""
+
+    def __init__(self, v, J, g, m):
+        self.v, self.J, self.g = v, J, g
+        self.S, self.Y, self.R = [], [], []
+        self.m = m
+        self.iters = 0
+        self.evals = 1
+        self.done = False
+        self.history = []
+
+    def direction(self):
+        """Two-loop recursion; the initial Hessian scaling is s.y / y.y of the newest pair, and
+        the very first step has unit length.  Falls back to -g (memory cleared) when the
+        result is not a descent direction."""
+        q = -self.g
+        alphas = []
+        for s, y, rho in zip(reversed(self.S), reversed(self.Y), reversed(self.R)):
+            a = rho * torch.dot(s, q)
+            alphas.append(a)
+            q = q - a * y
+        if self.S:
+            s, y = self.S[-1], self.Y[-1]
+            q = q * (torch.dot(s, y) / torch.dot(y, y))
+        else:
+            gn = torch.linalg.vector_norm(self.g)
+            q = q / torch.clamp(gn, min=1e-300)
+        for (s, y, rho), a in zip(zip(self.S, self.Y, self.R), reversed(alphas)):
+            b = rho * torch.dot(y, q)
+            q = q + s * (a - b)
+        gd = float(torch.dot(self.g, q).item())
+        if not gd < 0.0 and self.S:
+            self.S.clear(), self.Y.clear(), self.R.clear()
+            return self.direction()
+        return q, gd
+
+    def accept(self, v_new, J_new, g_new):
+        s = v_new - self.v
+        y = g_new - self.g
+        sy = float(torch.dot(s, y).item())
+        if sy > 0.0:          # weak Wolfe guarantees s.y > 0 unless the step is rounding-level
+            self.S.append(s)
+            self.Y.append(y)
+            self.R.append(1.0 / sy)
+            if len(self.S) > self.m:
+                self.S.pop(0), self.Y.pop(0), self.R.pop(0)
+        self.v, self.J, self.g = v_new, J_new, g_new
+        self.iters += 1
+
+
+def _noise(ev, eps_f):
+    """Relative rounding level of J: the caller's, else the evaluator's `eps_f`, else 1e-10."""
+    return eps_f if eps_f is not None else getattr(ev, "eps_f", 1e-10)
+
+
+def lbfgs(ev, v0: torch.Tensor, *, m: int = 10, gtol: float = 1e-6, relative: bool = False,
+          max_iter: int = 20000, c1: float = 1e-4, sigma: float = 0.9, eps_f: float | None = None,
+          max_evals_per_iter: int = 60) -> LBFGSResult:
+    """Minimise J from v0.  Stops when ||g||_inf <= gtol (times ||g0||_inf if relative), or when
+    a line search finds no acceptable step (converged is then False).  eps_f is the relative
+    rounding level of the evaluated J used by the approximate Wolfe test."""
+    t0 = time.perf_counter()
+    eps_f = _noise(ev, eps_f)
+    J, g = ev(v0)
+    st = _State(v0.clone(), float(J), g, m)
+    tol = gtol * (_gnorm(g) if relative else 1.0)
+    gn = _gnorm(g)
+    st.history.append((st.J, gn))
+    while gn > tol and st.iters < max_iter:
+        d, gd = st.direction()
+        if not gd < 0.0:
+            break
+        ls = _LineSearch(st.J, gd, c1, sigma, eps_f)
+        for _ in range(max_evals_per_iter):
+            v_new = st.v + ls.t * d
+            J_new, g_new = ev(v_new)
+            st.evals += 1
+            J_new = float(J_new)
+            if ls.update(J_new, float(torch.dot(g_new, d).item())):
+                break
+        else:
+            break
+        st.accept(v_new, J_new, g_new)
+        gn = _gnorm(st.g)
+        st.history.append((st.J, gn))
+    return LBFGSResult(st.v, st.J, gn, st.iters, st.evals, gn <= tol, time.perf_counter() - t0, st.history)
+
+
+def lbfgs_batched(batch_eval, v0s, *, m: int = 10, gtol: float = 1e-6, relative: bool = False,
+                  max_iter: int = 20000, c1: float = 1e-4, sigma: float = 0.9, eps_f: float | None = None,
+                  max_evals_per_iter: int = 60):
+    """Lockstep L-BFGS over several instances.  batch_eval(list of (k, v)) -> list of (J, g)
+    evaluates the trial points of the listed instances in one batched launch; each instance
+    follows exactly the iterates `lbfgs` would produce for it alone."""
+    t0 = time.perf_counter()
+    eps_f = _noise(batch_eval, eps_f)
+    first = batch_eval(list(enumerate(v0s)))
+    states = [_State(v.clone(), float(J), g, m) for v, (J, g) in zip(v0s, first)]
+    tols = []
+    for s in states:
+        gn = _gnorm(s.g)
+        tols.append(gtol * (gn if relative else 1.0))
+        s.history.append((s.J, gn))
+        s.done = gn <= tols[-1]
+    while True:
+        active = [k for k, s in enumerate(states) if not s.done and s.iters < max_iter]
+        if not active:
+            break
+        dirs, searches = {}, {}
+        for k in active:
+            s = states[k]
+            d, gd = s.direction()
+            if not gd < 0.0:
+                s.done = True
+                continue
+            dirs[k], searches[k] = d, _LineSearch(s.J, gd, c1, sigma, eps_f)
+        searching = list(searches)
+        for _ in range(max_evals_per_iter):
+            if not searching:
+                break
+            trial = [(k, states[k].v + searches[k].t * dirs[k]) for k in searching]
+            res = batch_eval(trial)
+            still = []
+            for (k, v_new), (J_new, g_new) in zip(trial, res):
+                s = states[k]
+                s.evals += 1
+                J_new = float(J_new)
+                if searches[k].update(J_new, float(torch.dot(g_new, dirs[k]).item())):
+                    s.accept(v_new, J_new, g_new)
+                    gn = _gnorm(s.g)
+                    s.history.append((s.J, gn))
+                    s.done = gn <= tols[k]
+                else:
+                    still.append(k)
+            searching = still
+        for k in searching:                # no acceptable step: stop that instance
+            states[k].done = True
+    secs = time.perf_counter() - t0
+    return [LBFGSResult(s.v, s.J, _gnorm(s.g), s.iters, s.evals, _gnorm(s.g) <= tols[k], secs, s.history)
+            for k, s in enumerate(states)]
+
+
+# ----------------------------------------------------------------------------------------
+# Evaluators over the CUDA library
+# ----------------------------------------------------------------------------------------
+
+# Relative rounding level of J per element precision: FP64 and double-float sums are accurate
+# to about 1e-14 of the energy scale; the FP32 element path to about 1e-7 of it.
+EPS_F = {0: 1e-10, 1: 1e-6, 2: 1e-10}
+
+
+def mesh_evaluator(mesh, gradient: str = "exact", eps: float = 1e-6):
+    """ev(v) -> (J, g) with the library's kernels: exact gradient or patch central
+    differences (the energy comes from the same call in the exact case).  ev.eps_f is the
+    rounding level of J at the mesh's active precision when the evaluator is made."""
+    if gradient == "exact":
+        def ev(v):
+            J, g = mesh.energy_gradient(v)
+            return J.item(), g
+    elif gradient == "fd":
+        def ev(v):
+            J = mesh.energy(v)
+            g = mesh.gradient_fd(v, eps)
+            return J.item(), g
+    else:
+        raise ValueError(gradient)
+    ev.eps_f = EPS_F.get(mesh.precision, 1e-10)
+    return ev
+
+
+def batch_evaluator(batch, meshes, device=0):
+    """batch_eval(list of (k, v)) -> list of (J, g) through one fe_batch call."""
+    from . import fem
+    dev = torch.device("cuda", device)
+    works = []
+    for mesh in meshes:
+        wb = fem.Batch.work_bytes(mesh)
+        buf = torch.empty(wb + 256, dtype=torch.uint8, device=dev)
+        off = (-buf.data_ptr()) % 256
+        works.append(buf[off: off + wb])
+
+    def batch_eval(trials):
+        items, outs = [], []
+        for k, v in trials:
+            J = torch.empty((), dtype=torch.float64, device=dev)
+            g = torch.empty(meshes[k].ndof, dtype=torch.float64, device=dev)
+            items.append((meshes[k], v.contiguous(), J, g, works[k]))
+            outs.append((J, g))
+        batch.run(items)
+        batch.sync_status()
+        return [(J.item(), g) for J, g in outs]
+
+    return batch_eval

@@ -3,10 +3,16 @@
 Energy (FP64 path): |J - J*| <= 1e-12 * (sum_T |T| |W_T| + sum_n |b_n v_n|), the condition
 number of the sum times the 1e-12 relative bar (a plain relative error is meaningless when
 J_grad and b.v nearly cancel).  Gradient: ||g - g*||_inf <= 1e-10 ||g*||_inf.
-Central differences amplify the rounding of W by 1/(2 eps), so the FD comparison adds
-64 u max_n (sum_{T in patch(n)} |T| |W_T|) / eps to the gradient bar.
+Central differences amplify the rounding of the patch energies by 1/(2 eps).  The oracle
+evaluates eq. neoHook as written, C1 (I1 - dim - 2 log det F) + D1 (det F - 1)^2, whose
+rounding is relative to the size of its terms S_T = C1 (I1 + dim + 2 |log det F|) +
+D1 (det F - 1)^2 rather than to W_T (near F = I the terms cancel to a W_T orders of magnitude
+smaller); for the p-Laplacian S_T = |W_T|.  The FD comparison therefore adds
+64 u max_n (sum_{T in patch(n)} |T| S_T) / eps to the gradient bar.
 """
 import numpy as np
+
+from paper_2109_01158_gb300 import meshgen as mg
 
 U = np.finfo(np.float64).eps / 2
 
@@ -19,9 +25,24 @@ def energy_scale(om, v):
     return float(np.abs(om.vol * dens).sum() + np.abs(om.b * v).sum())
 
 
-def patch_energy_max(om, v):
+def density_term_scale(om, v):
+    """S_T per element: the magnitude of the terms the oracle's density is evaluated from."""
     _, _, dens = om.energy(v, densities=True)
-    ew = np.abs(om.vol * dens)
+    if om.model != mg.MODEL_NEOHOOKE:
+        return np.abs(dens)
+    k = om.dim + 1
+    dphi = om.dphi.reshape(om.ne, k, om.dim)
+    vv = np.asarray(v, dtype=np.float64).reshape(om.nn, om.d)
+    F = np.einsum("elj,elm->ejm", vv[om.elems], dphi)
+    I1 = (F * F).sum(axis=(1, 2))
+    det = np.linalg.det(F)
+    with np.errstate(divide="ignore"):
+        logdet = np.abs(np.log(np.abs(det)))
+    return om.C1 * (I1 + om.dim + 2.0 * logdet) + om.D1 * (det - 1.0) ** 2
+
+
+def patch_energy_max(om, v):
+    ew = np.abs(om.vol * density_term_scale(om, v))
     k = om.dim + 1
     per_entry = ew[om.ent[: om.ne * k] // k]
     sums = np.add.reduceat(per_entry, om.row_ptr[:-1]) if om.ne else np.zeros(om.nn)

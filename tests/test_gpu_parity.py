@@ -160,6 +160,63 @@ def test_c3_neohooke_3d_full(precision):
     print(f"C3 precision {precision}: energy err/condition {e1:.2e}, gradient rel {e2:.2e}")
 
 
+def _w_homogeneous_decimal(A, C1, D1):
+    """W(A) of eq. neoHook for a 3x3 matrix A in 50-digit decimal arithmetic."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 50
+    a = [[Decimal(repr(float(x))) for x in row] for row in A]
+    det = (a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0])
+           + a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]))
+    I1 = sum(x * x for row in a for x in row)
+    W = Decimal(repr(C1)) * (I1 - 3 - 2 * det.ln()) + Decimal(repr(D1)) * (det - 1) ** 2
+    return float(W)
+
+
+@pytest.mark.parametrize("precision", [0, 2], ids=["f64", "df64"])
+@pytest.mark.parametrize("eps", [1e-3, 1e-5])
+def test_small_strain_homogeneous_energy(precision, eps):
+    """Small strains: v = (I + eps B) X on the unit cube gives J = W(I + eps B) exactly.  The
+    kernels evaluate eq. neoHook in displacement form and keep full relative accuracy even
+    where I1 - 3 - 2 log det F cancels down to O(eps^2) (the formula as written loses about
+    1e-16 / eps^2 relative); reference in 50-digit decimals.  The tolerance adds the rounding
+    of the input itself: v = X + u is stored in FP64 with |v| ~ 1, so u carries a relative
+    error of about 1e-16 / eps and W ~ u^2 twice that."""
+    fem = _fem()
+    w = mg.neohooke_cube3d(6)
+    w.dirichlet[:] = 0
+    w.f = None
+    B = np.array([[0.3, -0.2, 0.1], [0.05, -0.4, 0.2], [-0.1, 0.25, 0.15]])
+    A = np.eye(3) + eps * B
+    w.v = (w.coords @ A.T).ravel()
+    ref = _w_homogeneous_decimal(A, w.C1, w.D1)
+    gm = _gpu(w, precisions=(precision,))
+    J = gm.energy(_v(w)).item()
+    assert abs(J - ref) <= (1e-12 + 4.4e-16 / eps) * abs(ref), (J, ref)
+
+
+@pytest.mark.parametrize("precision", [0, 2], ids=["f64", "df64"])
+@pytest.mark.parametrize("delta", [-0.25, -0.1, -0.0021, 0.0019, 0.003, 0.05, 0.3, 0.42, 0.6])
+def test_homogeneous_stretch_energy_over_the_log_range(precision, delta):
+    """v = A X with A = (1 + delta)^(1/3) (I + 0.02 S) (det A - 1 = delta up to O(0.02^2)):
+    J = W(A) on the unit cube.  The values of det F - 1 cover the breakpoint table of
+    phi(x) = x - log(1 + x) of the FP64 kernels on both sides of zero, next to the +-1/512 row
+    boundaries, and beyond it (0.6: the log1p branch); reference in 50-digit decimals."""
+    fem = _fem()
+    w = mg.neohooke_cube3d(6)
+    w.dirichlet[:] = 0
+    w.f = None
+    S = np.array([[0.0, 0.3, -0.1], [0.2, 0.0, 0.25], [-0.15, 0.1, 0.0]])
+    A = (1.0 + delta) ** (1.0 / 3.0) * (np.eye(3) + 0.02 * S)
+    w.v = (w.coords @ A.T).ravel()
+    ref = _w_homogeneous_decimal(A, w.C1, w.D1)
+    gm = _gpu(w, precisions=(precision,))
+    J = gm.energy(_v(w)).item()
+    # input rounding of v = A X (~1e-16 of |v|, averaging over the elements) enters W
+    # through dW/dF ~ C1 |F| + D1
+    tol = 1e-12 * abs(ref) + 1e-16 * (w.C1 + w.D1)
+    assert abs(J - ref) <= tol, (J, ref, abs(J - ref) / abs(ref))
+
+
 def test_twisted_bar_df64_levels():
     """Double-float energies of Benchmark 2 (E = 2e8, volumes down to 1e-10) against the
     oracle at the FP64 tolerance, levels 1-4."""
@@ -310,6 +367,23 @@ def test_c3_fd_subset_10k():
     check_grad(g, gref, extra_abs=extra)
     gex = gm.gradient_exact(v).cpu().numpy()[dofs]
     check_grad(g, gex, rtol=1e-6, extra_abs=extra)
+
+
+def test_fd_small_strain_matches_exact_gradient():
+    """Near F = I (displacements of 1e-6, eps = 1e-7) the patch energies are evaluated in
+    displacement form, so their rounding is relative to W, not to the O(1) terms of the
+    formula as written: the central differences then agree with the exact gradient to their
+    O(eps^2) truncation (~1e-9 relative here), where differences of the formula as written
+    would carry ~u C1 dim |T| / eps ~ 5e-6 relative of rounding."""
+    w = mg.neohooke_cube3d(8)
+    w.v = w.coords.ravel() + mg.uniform(11, np.arange(w.ndof), -1e-6, 1e-6) * (w.dirichlet == 0)
+    gm = _gpu(w)
+    v = _v(w)
+    g = gm.gradient_exact(v).cpu().numpy()
+    gfd = gm.gradient_fd(v, 1e-7).cpu().numpy()
+    check_grad(gfd, g, rtol=1e-8)
+    dofs = np.flatnonzero(w.dirichlet == 0)[::7].astype(np.int64)
+    check_grad(gm.gradient_fd(v, 1e-7, dofs).cpu().numpy(), g[dofs], rtol=1e-8)
 
 
 # ----------------------------------------------------------------------------------------
