@@ -357,6 +357,22 @@ def run_ours(args, rank, world, local):
                            "element_hbm_frac": (w.ne * ob + w.nn * on) / (o_elem / 1e3) / 1e9 / hbm_peak}
     gm.set_precision(code[prec])
 
+    # Hessian-vector products (FP64) on the same mesh and state, for context
+    x = torch.from_numpy(mg.uniform(80, np.arange(w.ndof), -1.0, 1.0)).to(dev)
+    Hx = torch.empty(w.ndof, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        gm.hessian_vector(v, x, out=Hx)
+    nh = max(5, args.steps // 4)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nh):
+        gm.hessian_vector(v, x, out=Hx)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    hms = e0.elapsed_time(e1) / nh
+    variants["f64_hessian_vector"] = {"value": w.ne / (hms / 1e3) / 1e9, "unit": "Gelem/s", "ms_per_call": hms}
+
     line = {
         "metric": "energy+grad throughput", "value": value, "unit": "Gelem/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -397,7 +413,9 @@ def run_serving(args, device):
     reqs = serve.make_requests(args.serve_requests, seed=3, rate=1.0, catalogue=cat)
     setup_s = time.perf_counter() - t0
     server = serve.Server(cat, hbm_budget=args.serve_budget_gb << 30)
-    serve.serial_capacity(server, reqs[:32])                 # warm-up
+    warm = [serve.Request(r.rid, r.key, 0.0, r.v, ne=r.ne) for r in reqs[:64]]
+    server.run(warm, mode="serial", keep_results=False)     # warm-up of both native servers
+    server.run(warm, mode="batched", keep_results=False)
     cap = serve.serial_capacity(server, reqs)
     out = {"requests": len(reqs), "precision": "df64", "catalogue_meshes": len(cat.meshes),
            "resident_bytes": cat.bytes(), "setup_s": setup_s, "serial_capacity_req_s": cap,
@@ -412,6 +430,7 @@ def run_serving(args, device):
             rec[mode] = {k: st.as_dict()[k] for k in ("p50_ms", "p99_ms", "mean_ms", "req_per_s",
                                                        "gelem_per_s", "max_batch", "steps", "wall_s")}
         out["loads"].append(rec)
+    server.close()
     return out
 
 
@@ -426,7 +445,8 @@ def run_minimize(args, device):
     import torch
     from paper_2109_01158_gb300 import fem
     from paper_2109_01158_gb300 import meshgen as mg
-    from paper_2109_01158_gb300.minimize import batch_evaluator, lbfgs, lbfgs_batched, mesh_evaluator
+    from paper_2109_01158_gb300.minimize import (batch_evaluator, lbfgs, lbfgs_batched, mesh_evaluator, mesh_hvp,
+                                                 newton_cg)
     n = args.minimize_n
     dev = torch.device("cuda", device)
 
@@ -449,6 +469,12 @@ def run_minimize(args, device):
         r = lbfgs(mesh_evaluator(gm, grad, eps=1e-6), v0, gtol=1e-6, relative=True, max_iter=args.minimize_iters)
         out["runs"][name] = {"J": r.J, "iters": r.iters, "evals": r.evals, "converged": r.converged,
                              "seconds": r.seconds, "gnorm": r.gnorm, "g0": r.history[0][1]}
+    # trust-region Newton-CG on the FP64 Hessian-vector products
+    gm.set_precision(fem.FE_F64)
+    r = newton_cg(mesh_evaluator(gm), mesh_hvp(gm), v0, gtol=1e-6, relative=True)
+    out["runs"]["f64_newton_cg"] = {"J": r.J, "iters": r.iters, "evals": r.evals, "hessian_vector_products": r.hvps,
+                                    "converged": r.converged, "seconds": r.seconds, "gnorm": r.gnorm,
+                                    "g0": r.history[0][1]}
     ref = out["runs"]["df64_exact"]["J"]
     for rec in out["runs"].values():
         rec["J_rel_diff_vs_df64"] = abs(rec["J"] - ref) / abs(ref)

@@ -150,6 +150,17 @@ fe_status fe_gradient_exact(fe_ctx* ctx, const double* v_dev, double* g_dev);
 /* Energy and exact gradient in one pass over the elements (J_dev as in fe_energy). */
 fe_status fe_energy_gradient(fe_ctx* ctx, const double* v_dev, double* J_dev, double* g_dev);
 
+/* Hessian-vector product (not in the paper, whose trust-region solver uses the Hessian's
+ * sparsity pattern only): Hw_dev = d/dt grad J(v + t w) at t = 0, the second derivative of
+ * J_grad = sum_k |T_k| W(F_k) along w, gathered over the nodal patches like the exact
+ * gradient (Sec. 6.2); b.v contributes nothing.  Entries of w_dev on Dirichlet dofs are
+ * taken as 0 and the Dirichlet rows of Hw_dev are 0 (the Hessian on the free dofs).  v_dev,
+ * w_dev, Hw_dev: n_nodes*d doubles (device, caller's dof order; v as set by fe_set_input).
+ * p-Laplacian with p < 2: 0 where grad v = 0 (the Hessian is unbounded there).  Always
+ * evaluated in FP64 (needs the FP64 precompute).  Neo-Hookean with some det F <= 0:
+ * fe_sync_status returns FE_EDOMAIN. */
+fe_status fe_hessian_vector(fe_ctx* ctx, const double* v_dev, const double* w_dev, double* Hw_dev);
+
 /* Central-difference gradient over nodal patches (Sec. 6.1, eqs. CD, CDS, jgradpm,
  * sumpatch): for dof n of node i, component j,
  *   g_n = ( sum_{T in T^i} |T| W(F_T^+) - sum_{T in T^i} |T| W(F_T^-) ) / (2 eps) - b_n,
@@ -233,6 +244,50 @@ fe_status fe_batch_energy_gradient(fe_batch* b, const fe_batch_item* items, int 
 /* Synchronise the batch stream; FE_EDOMAIN if an item had det F <= 0 since the last call. */
 fe_status fe_batch_sync_status(fe_batch* b);
 fe_status fe_batch_launch_count(const fe_batch* b, int64_t* count);
+
+/* ---- Continuous-batching server over resident meshes -------------------------------
+ * Not in the paper: a native request loop around the batched kernels.  Callers submit
+ * energy + gradient requests (host vectors in, host results out); a worker thread admits
+ * the requests that have arrived, in FIFO order, while their device bytes fit in the HBM
+ * budget (a ring arena allocated at creation), stages their vectors through pinned memory
+ * (one host-to-device copy per batch), launches the three batch kernels on the server's own
+ * stream, and copies the results back (one device-to-host copy per batch).  Batch k + 1 is
+ * prepared and enqueued while batch k runs; a completion thread copies the results into the
+ * callers' buffers in launch order, stamps the completion time and frees the arena.  With
+ * max_batch = 1 it serves one request at a time with the same kernels.  Results are bitwise
+ * those of fe_batch_energy_gradient on the same request (alone or in any mix).
+ * Page-locked caller buffers (cudaMallocHost, cudaHostRegister) are copied to and from by
+ * DMA directly; pageable ones go through the server's pinned staging (one extra host copy).
+ * Times are seconds on a steady clock since fe_server_create. */
+typedef struct fe_server fe_server;
+
+/* hbm_budget: bytes of device memory for the in-flight requests (vectors + scratch);
+ * max_batch >= 1: most requests per batch.  Creates its own non-blocking stream on `device`
+ * and allocates everything it serves with up front: the arena, and per batch slot pinned
+ * staging of min(max(hbm_budget/16, 1 MB), 256 MB) bytes for each direction (a batch is also
+ * bounded by it; a single larger request grows it). */
+fe_status fe_server_create(fe_server** out, int device, size_t hbm_budget, int max_batch);
+/* Serve every submitted request, then stop the threads and free everything. */
+fe_status fe_server_destroy(fe_server* s);
+/* Queue one request.  mesh: precomputed with FE_DF64 and given a model (only read; it must
+ * outlive the request).  v_host: n_nodes*d doubles, read when the request is admitted (keep
+ * it unchanged until then).  J_host (one double) and g_host (n_nodes*d doubles) receive the
+ * results at completion.  t_arrival: when the request arrives (server clock; < 0 = now);
+ * arrivals must be submitted in non-decreasing order.  *ticket identifies it.  FE_EINVAL if
+ * its device bytes exceed the whole budget. */
+fe_status fe_server_submit(fe_server* s, const fe_ctx* mesh, const double* v_host, double* J_host,
+                           double* g_host, double t_arrival, int64_t* ticket);
+/* Block until request `ticket` completed; returns its status (FE_OK, or FE_EDOMAIN when some
+ * det F <= 0 and J = +Inf) and its arrival, start (batch enqueued) and completion times (any
+ * pointer may be NULL).  Each ticket can be waited for once. */
+fe_status fe_server_wait(fe_server* s, int64_t ticket, double* t_arrival, double* t_start, double* t_done);
+/* Seconds since fe_server_create on the server clock. */
+fe_status fe_server_now(const fe_server* s, double* t);
+/* Counters since creation: batches launched, largest batch, kernel launches, requests done. */
+fe_status fe_server_stats(const fe_server* s, int64_t* batches, int64_t* max_batch, int64_t* launches,
+                          int64_t* completed);
+/* Zero those counters (e.g. between measurement runs). */
+fe_status fe_server_reset_stats(fe_server* s);
 
 /* Energy without any allocation (the paper has no counterpart: this is an interface for
  * callers that cannot let this library allocate device memory -- a host program whose GPU

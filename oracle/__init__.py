@@ -63,6 +63,8 @@ def _load():
             lib.or_gradient_fd.argtypes = [_int, _dbl, _dbl, _dbl, _int, _int, _i64, _D, _i64,
                                            _I32, _D, _D, _D, _U8, _I64, _I64, _D, _dbl, _I64,
                                            _i64, _D]
+            lib.or_hessian_vector.argtypes = [_int, _dbl, _dbl, _dbl, _int, _int, _i64, _D, _i64,
+                                              _I32, _D, _D, _U8, _I64, _I64, _D, _D, _D]
             _lib = lib
     return _lib
 
@@ -134,6 +136,17 @@ class OracleMesh:
                                    _p(self.row_ptr, _I64), _p(self.ent, _I64), _p(v, _D),
                                    _p(g, _D))
         return g, st
+
+    def hessian_vector(self, v, w):
+        """Hw = d/dt grad J(v + t w) at t = 0 on the free dofs (w on Dirichlet dofs taken as 0,
+        Dirichlet rows 0); returns (Hw, status)."""
+        lib = _load()
+        v, w = _f64(v), _f64(w)
+        Hw = np.zeros(self.nn * self.d)
+        c = self._common()
+        st = lib.or_hessian_vector(*c[:-1], _p(self.dirichlet, _U8), _p(self.row_ptr, _I64),
+                                   _p(self.ent, _I64), _p(v, _D), _p(w, _D), _p(Hw, _D))
+        return Hw, st
 
     def gradient_fd(self, v, eps, dofs=None):
         """Patch-local central differences; all dofs (dofs=None) or a subset."""

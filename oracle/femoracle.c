@@ -381,3 +381,116 @@ int or_gradient_fd(int model, double p, double C1, double D1, int dim, int d, in
     }
     return dom_err ? OR_EDOMAIN : OR_OK;
 }
+
+/* ------------------------------------------------------------------------------ */
+/* Hessian-vector product: Hw = d/dt grad J(v + t w) at t = 0 on the free dofs, i.e.  */
+/* for every element the directional derivative of dW/dF along dF = sum_l w_l        */
+/* grad(phi_l)^T, contracted with grad(phi_l) and gathered over the patches like the */
+/* exact gradient (Sec. 6.2).  The linear term b.v has no second derivative.  Entries */
+/* of w on Dirichlet dofs are taken as 0 and Dirichlet rows of Hw are 0 (the Hessian  */
+/* of J restricted to the free dofs).                                                 */
+/* ------------------------------------------------------------------------------ */
+
+/* dP = (d/dt) dW/dF(F + t dF) at t = 0.
+ * Neo-Hookean, from dW/dF = C1 (2F - (2/det) cof) + 2 D1 (det - 1) cof with cof_jm =
+ * ddet/dF_jm: d(det) = sum cof_jm dF_jm, d(cof_jm) = derivative of the same signed minor,
+ *   dP = C1 (2 dF + (2/det^2) d(det) cof - (2/det) d(cof)) + 2 D1 (d(det) cof + (det - 1) d(cof)).
+ * p-Laplacian, from dW/dF = s^((p-2)/2) F with s = |F|^2:
+ *   dP = s^((p-2)/2) dF + (p - 2) s^((p-4)/2) (F . dF) F,
+ * with dP = dF for p = 2 and dP = 0 at F = 0 otherwise (the Hessian of |F|^p / p is 0 there
+ * for p > 2 and unbounded for p < 2). */
+static void or_d2W(const or_mesh* M, double F[3][3], double dF[3][3], double dP[3][3], int* dom_err) {
+    const int dim = M->dim;
+    if (M->model == OR_NEOHOOKE) {
+        double det = or_det(dim, F);
+        if (!(det > 0.0)) *dom_err = 1;
+        double cof[3][3], dcof[3][3], ddet = 0.0;
+        for (int j = 0; j < dim; ++j)
+            for (int m = 0; m < dim; ++m) {
+                double minor, dminor;
+                if (dim == 2) {
+                    minor = F[1 - j][1 - m];
+                    dminor = dF[1 - j][1 - m];
+                } else {
+                    int r[2], c[2], nr = 0, nc = 0;
+                    for (int a = 0; a < 3; ++a) if (a != j) r[nr++] = a;
+                    for (int a = 0; a < 3; ++a) if (a != m) c[nc++] = a;
+                    minor = F[r[0]][c[0]] * F[r[1]][c[1]] - F[r[0]][c[1]] * F[r[1]][c[0]];
+                    dminor = dF[r[0]][c[0]] * F[r[1]][c[1]] + F[r[0]][c[0]] * dF[r[1]][c[1]]
+                           - dF[r[0]][c[1]] * F[r[1]][c[0]] - F[r[0]][c[1]] * dF[r[1]][c[0]];
+                }
+                int sgn = ((j + m) % 2 == 0) ? 1 : -1;
+                cof[j][m] = sgn * minor;
+                dcof[j][m] = sgn * dminor;
+                ddet += cof[j][m] * dF[j][m];
+            }
+        for (int j = 0; j < dim; ++j)
+            for (int m = 0; m < dim; ++m)
+                dP[j][m] = M->C1 * (2.0 * dF[j][m] + (2.0 / (det * det)) * ddet * cof[j][m]
+                                    - (2.0 / det) * dcof[j][m])
+                         + 2.0 * M->D1 * (ddet * cof[j][m] + (det - 1.0) * dcof[j][m]);
+        return;
+    }
+    double s = 0.0, fd = 0.0;
+    for (int m = 0; m < dim; ++m) {
+        s += F[0][m] * F[0][m];
+        fd += F[0][m] * dF[0][m];
+    }
+    double c1, c2;
+    if (M->p == 2.0) {
+        c1 = 1.0;
+        c2 = 0.0;
+    } else if (s > 0.0) {
+        c1 = pow(s, (M->p - 2.0) / 2.0);
+        c2 = (M->p - 2.0) * pow(s, (M->p - 4.0) / 2.0);
+    } else {
+        c1 = c2 = 0.0;
+    }
+    for (int m = 0; m < dim; ++m) dP[0][m] = c1 * dF[0][m] + c2 * fd * F[0][m];
+}
+
+int or_hessian_vector(int model, double p, double C1, double D1, int dim, int d, int64_t nn,
+                      const double* coords, int64_t ne, const int32_t* elems,
+                      const double* dphi, const double* vol, const uint8_t* dirichlet,
+                      const int64_t* row_ptr, const int64_t* ent, const double* v,
+                      const double* w, double* Hw) {
+    if (!or_check_model(model, dim, d)) return OR_EINVAL;
+    or_mesh M = {model, dim, d, p, C1, D1, coords, elems, dphi, vol};
+    const int k = dim + 1;
+    double* r = (double*)malloc(sizeof(double) * (size_t)(ne > 0 ? ne * k * d : 1));
+    if (!r) return OR_ENOMEM;
+    int dom_err = 0;
+    for (int64_t e = 0; e < ne; ++e) {
+        double uloc[4][3], F[3][3], dF[3][3], dP[3][3];
+        or_local_values(&M, e, v, uloc);
+        or_element_F(&M, e, uloc, F);
+        const int32_t* en = elems + e * k;
+        const double* de = dphi + e * k * dim;
+        for (int j = 0; j < d; ++j)
+            for (int m = 0; m < dim; ++m) {
+                double s = 0.0;
+                for (int l = 0; l < k; ++l) {
+                    int64_t n = (int64_t)en[l] * d + j;
+                    double wl = (dirichlet && dirichlet[n]) ? 0.0 : w[n];
+                    s += wl * de[l * dim + m];
+                }
+                dF[j][m] = s;
+            }
+        or_d2W(&M, F, dF, dP, &dom_err);
+        for (int l = 0; l < k; ++l)
+            for (int j = 0; j < d; ++j) {
+                double s = 0.0;
+                for (int m = 0; m < dim; ++m) s += dP[j][m] * de[l * dim + m];
+                r[(e * k + l) * d + j] = vol[e] * s;
+            }
+    }
+    for (int64_t i = 0; i < nn; ++i)
+        for (int j = 0; j < d; ++j) {
+            double s = 0.0;
+            for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) s += r[ent[q] * d + j];
+            int64_t n = i * d + j;
+            Hw[n] = (dirichlet && dirichlet[n]) ? 0.0 : s;
+        }
+    free(r);
+    return dom_err ? OR_EDOMAIN : OR_OK;
+}

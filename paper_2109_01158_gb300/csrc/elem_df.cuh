@@ -80,6 +80,35 @@ __device__ __forceinline__ df df_phi(df x, const LogEntry* tab) {
   return df_sub(x, df_log(df_add_f(x, 1.0f), tab));
 }
 
+template <int DIM>
+struct MatDF {
+  df m[DIM][DIM];
+};
+
+// |T| dW/dF near F = I without O(1) terms: 2 C1 (H - L) + 2 delta (D1 + C1 / det F) cof F with
+// L = cof F - I, whose diagonal L_jj is formed from H (X0 = L_00 from the caller).  Out of
+// line: the common path keeps the registers and code of the plain form.
+template <int DIM>
+static __device__ __noinline__ MatDF<DIM> nh_stress_small_df(MatDF<DIM> H, MatDF<DIM> C, df X0, df delta, df rJ,
+                                                             df a, df vT, df C1, df D1) {
+  df Ld[DIM];
+  if constexpr (DIM == 3) {
+    Ld[0] = X0;
+    Ld[1] = df_add(df_add(H.m[0][0], H.m[2][2]), df_det2(H.m[0][0], H.m[2][2], H.m[0][2], H.m[2][0]));
+    Ld[2] = df_add(df_add(H.m[0][0], H.m[1][1]), df_det2(H.m[0][0], H.m[1][1], H.m[0][1], H.m[1][0]));
+  } else {
+    Ld[0] = H.m[1][1];
+    Ld[1] = H.m[0][0];
+  }
+  const df cp = df_mul(vT, df_scale(df_mul(delta, df_add(D1, df_mul(C1, rJ))), 2.f));
+  MatDF<DIM> P;
+#pragma unroll
+  for (int j = 0; j < DIM; ++j)
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) P.m[j][m] = df_dot2(a, df_sub(H.m[j][m], j == m ? Ld[j] : C.m[j][m]), cp, C.m[j][m]);
+  return P;
+}
+
 // One element: gathers the nodal values, forms H = grad u (eq. Dv) and returns W(F) when
 // WANT_W (eq. neoHook or eq. pLaplacian); when GRAD, also writes the local forces
 // r_{T,l} = |T| dW/dF grad(phi_l) (Sec. 6.2) to the CSR slots.  vT receives |T|; `bad` is set
@@ -175,21 +204,19 @@ __device__ __forceinline__ df elem_df_one(int64_t e, int64_t ne, const int32_t* 
 #pragma unroll
           for (int m = 0; m < DIM; ++m) hs = fmaf(H[j][m].hi, H[j][m].hi, hs);
         if (__any_sync(__activemask(), hs < 1e-4f)) {
-          df Ld[DIM];
-          if constexpr (DIM == 3) {
-            Ld[0] = X0;
-            Ld[1] = df_add(df_add(H[0][0], H[2][2]), df_det2(H[0][0], H[2][2], H[0][2], H[2][0]));
-            Ld[2] = df_add(df_add(H[0][0], H[1][1]), df_det2(H[0][0], H[1][1], H[0][1], H[1][0]));
-          } else {
-            Ld[0] = H[1][1];
-            Ld[1] = H[0][0];
-          }
-          const df cp = df_mul(vT, df_scale(df_mul(delta, df_add(md.D1, df_mul(md.C1, rJ))), 2.f));
+          MatDF<DIM> h, cf;
 #pragma unroll
-          for (int j = 0; j < D; ++j)
+          for (int j = 0; j < DIM; ++j)
 #pragma unroll
-            for (int m = 0; m < DIM; ++m)
-              P[j][m] = df_dot2(a, df_sub(H[j][m], j == m ? Ld[j] : C[j][m]), cp, C[j][m]);
+            for (int m = 0; m < DIM; ++m) {
+              h.m[j][m] = H[j][m];
+              cf.m[j][m] = C[j][m];
+            }
+          const MatDF<DIM> p = nh_stress_small_df<DIM>(h, cf, X0, delta, rJ, a, vT, md.C1, md.D1);
+#pragma unroll
+          for (int j = 0; j < DIM; ++j)
+#pragma unroll
+            for (int m = 0; m < DIM; ++m) P[j][m] = p.m[j][m];
         } else {
           const df c = df_mul(vT, df_dot2(md.twoD1, delta, md.negTwoC1, rJ));
 #pragma unroll

@@ -102,6 +102,7 @@ void free_precompute(fe_ctx* c) {
   dev_free(c, &c->u_df, nn * padded_d(c->d));
   dev_free(c, &c->r_df, ne * k * c->d);
   dev_free(c, &c->u, nn * padded_d(c->d));
+  dev_free(c, &c->w_hvp, nn * padded_d(c->d));
   dev_free(c, &c->r, ne * k * c->d);
   dev_free(c, &c->r32, ne * k * c->d);
   dev_free(c, &c->stage_v, nn * c->d);
@@ -475,6 +476,17 @@ fe_status fe_energy_gradient(fe_ctx* c, const double* v, double* J, double* gout
   if (!v || !J || !gout) return set_error(FE_EINVAL, "null v, J or g");
   DeviceGuard g(c->device);
   return eval(c, v, J, nullptr, gout, true, true);
+}
+
+fe_status fe_hessian_vector(fe_ctx* c, const double* v, const double* w, double* Hw) {
+  fe_status st = check_ready(c);
+  if (st) return st;
+  if (!v || !w || !Hw) return set_error(FE_EINVAL, "null v, w or Hw");
+  if (!(c->pre_mask & (1u << FE_F64)))
+    return set_error(FE_EINVAL, "the Hessian-vector product needs the FP64 precompute");
+  DeviceGuard g(c->device);
+  if (!c->w_hvp && (st = dev_alloc(c, &c->w_hvp, (size_t)c->nn * padded_d(c->d)))) return st;
+  return launch_hvp_f64(c, v, w, Hw);
 }
 
 fe_status fe_gradient_fd(fe_ctx* c, const double* v, double eps, double* gout, const int64_t* dofs,

@@ -223,6 +223,67 @@ ModelDF model_df_of(const fe_ctx* c) {
 }
 
 }  // namespace
+
+size_t batch_item_bytes() { return sizeof(BItem); }
+
+size_t batch_work_bytes(const fe_ctx* m) { return work_layout(m).total; }
+
+fe_status batch_enqueue(cudaStream_t s, const fe_batch_item* items, int n, void* host_stage, void* dev_stage,
+                        int* status) {
+  BItem* host = static_cast<BItem*>(host_stage);
+  BItem* dev = static_cast<BItem*>(dev_stage);
+  const LogEntry* tab = nullptr;
+  int64_t et = 0, nt = 0;
+  for (int k = 0; k < n; ++k) {
+    const fe_batch_item& q = items[k];
+    const fe_ctx* m = q.mesh;
+    if (!m || !m->have_pre || !m->model_set || !(m->pre_mask & (1u << FE_DF64)))
+      return set_error(FE_EINVAL, "batch item: mesh must be precomputed with FE_DF64 and have a model");
+    if (!q.v || !q.J || !q.g || !q.work) return set_error(FE_EINVAL, "batch item: null v, J, g or work");
+    if (reinterpret_cast<uintptr_t>(q.work) & 255u) return set_error(FE_EINVAL, "batch item: work not 256-byte aligned");
+    const WorkLayout L = work_layout(m);
+    unsigned char* w = static_cast<unsigned char*>(q.work);
+    BItem& it = host[k];
+    it.elems = m->elems;
+    it.dphi = m->dphi_df;
+    it.vol = m->vol_df;
+    it.slot = m->slot;
+    it.row_ptr = m->row_ptr;
+    it.X = m->X;
+    it.b = m->b;
+    it.dir = m->dir;
+    it.perm = m->perm;
+    it.nn = m->nn;
+    it.ne = m->ne;
+    it.dim = m->dim;
+    it.d = m->d;
+    it.model = m->model;
+    it.disp = input_is_disp(m) ? 1 : 0;
+    it.shift = it.disp ? m->bX : 0.0;
+    it.md = model_df_of(m);
+    it.v = q.v;
+    it.J = q.J;
+    it.g = q.g;
+    it.u = reinterpret_cast<float2*>(w + L.u);
+    it.r = reinterpret_cast<float2*>(w + L.r);
+    it.epart = reinterpret_cast<double*>(w + L.ep);
+    it.npart = reinterpret_cast<double*>(w + L.np);
+    it.netiles = std::max<int64_t>((m->ne + kBT - 1) / kBT, 1);
+    it.nntiles = std::max<int64_t>((m->nn + kBT - 1) / kBT, 1);
+    it.etile0 = et;
+    it.ntile0 = nt;
+    et += it.netiles;
+    nt += it.nntiles;
+    tab = m->log_tab;
+  }
+  if (et >= (1ll << 31) || nt >= (1ll << 31)) return set_error(FE_EINVAL, "batch too large");
+  cudaMemcpyAsync(dev, host, sizeof(BItem) * n, cudaMemcpyHostToDevice, s);
+  k_batch_prep<<<(unsigned)nt, kBT, 0, s>>>(dev, n);
+  k_batch_elem<<<(unsigned)et, kBT, 0, s>>>(dev, n, tab, status);
+  k_batch_gather<<<(unsigned)nt, kBT, 0, s>>>(dev, n);
+  return cuda_check(cudaGetLastError(), "batch launch");
+}
+
 }  // namespace fe
 
 struct fe_batch {
@@ -308,58 +369,11 @@ fe_status fe_batch_energy_gradient(fe_batch* b, const fe_batch_item* items, int 
   }
   // the staging buffer may still be read by the previous call's copy
   if ((st = cuda_check(cudaStreamSynchronize(b->stream), "batch sync"))) return st;
-  const LogEntry* tab = nullptr;
-  int64_t et = 0, nt = 0;
-  for (int k = 0; k < n; ++k) {
-    const fe_batch_item& q = items[k];
-    const fe_ctx* m = q.mesh;
-    if (!m || !m->have_pre || !m->model_set || !(m->pre_mask & (1u << FE_DF64)))
-      return set_error(FE_EINVAL, "batch item: mesh must be precomputed with FE_DF64 and have a model");
-    if (m->device != b->device) return set_error(FE_EINVAL, "batch item on another device");
-    if (!q.v || !q.J || !q.g || !q.work) return set_error(FE_EINVAL, "batch item: null v, J, g or work");
-    if (reinterpret_cast<uintptr_t>(q.work) & 255u) return set_error(FE_EINVAL, "batch item: work not 256-byte aligned");
-    const WorkLayout L = work_layout(m);
-    unsigned char* w = static_cast<unsigned char*>(q.work);
-    BItem& it = b->host[k];
-    it.elems = m->elems;
-    it.dphi = m->dphi_df;
-    it.vol = m->vol_df;
-    it.slot = m->slot;
-    it.row_ptr = m->row_ptr;
-    it.X = m->X;
-    it.b = m->b;
-    it.dir = m->dir;
-    it.perm = m->perm;
-    it.nn = m->nn;
-    it.ne = m->ne;
-    it.dim = m->dim;
-    it.d = m->d;
-    it.model = m->model;
-    it.disp = input_is_disp(m) ? 1 : 0;
-    it.shift = it.disp ? m->bX : 0.0;
-    it.md = model_df_of(m);
-    it.v = q.v;
-    it.J = q.J;
-    it.g = q.g;
-    it.u = reinterpret_cast<float2*>(w + L.u);
-    it.r = reinterpret_cast<float2*>(w + L.r);
-    it.epart = reinterpret_cast<double*>(w + L.ep);
-    it.npart = reinterpret_cast<double*>(w + L.np);
-    it.netiles = std::max<int64_t>((m->ne + kBT - 1) / kBT, 1);
-    it.nntiles = std::max<int64_t>((m->nn + kBT - 1) / kBT, 1);
-    it.etile0 = et;
-    it.ntile0 = nt;
-    et += it.netiles;
-    nt += it.nntiles;
-    tab = m->log_tab;
-  }
-  if (et >= (1ll << 31) || nt >= (1ll << 31)) return set_error(FE_EINVAL, "batch too large");
-  cudaMemcpyAsync(b->dev, b->host, sizeof(BItem) * n, cudaMemcpyHostToDevice, b->stream);
-  k_batch_prep<<<(unsigned)nt, kBT, 0, b->stream>>>(b->dev, n);
-  k_batch_elem<<<(unsigned)et, kBT, 0, b->stream>>>(b->dev, n, tab, b->status);
-  k_batch_gather<<<(unsigned)nt, kBT, 0, b->stream>>>(b->dev, n);
+  for (int k = 0; k < n; ++k)
+    if (items[k].mesh && items[k].mesh->device != b->device) return set_error(FE_EINVAL, "batch item on another device");
+  if ((st = batch_enqueue(b->stream, items, n, b->host, b->dev, b->status))) return st;
   b->launches += 3;
-  return cuda_check(cudaGetLastError(), "batch launch");
+  return FE_OK;
 }
 
 fe_status fe_batch_sync_status(fe_batch* b) {

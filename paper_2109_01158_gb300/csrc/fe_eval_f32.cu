@@ -277,9 +277,14 @@ __global__ void __launch_bounds__(kTile, 20) k_elem_f32(
     float H[D][DIM];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
+      // u_l - u_0 to float accuracy from the pairs: the hi difference is exact when the two
+      // values are within a factor 2 (Sterbenz' lemma), otherwise within half an ulp of a
+      // result of the same size; adding the (tiny) lo difference and rounding once leaves at
+      // most about one float ulp of the difference
       float a[DIM];
 #pragma unroll
-      for (int l = 0; l < DIM; ++l) a[l] = df_sub(ul[l + 1][j], ul[0][j]).hi;
+      for (int l = 0; l < DIM; ++l)
+        a[l] = fadd(fsub(ul[l + 1][j].hi, ul[0][j].hi), fsub(ul[l + 1][j].lo, ul[0][j].lo));
 #pragma unroll
       for (int m = 0; m < DIM; ++m) {
         float s = a[0] * g[0][m];

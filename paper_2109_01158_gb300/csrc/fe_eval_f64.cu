@@ -3,18 +3,20 @@
 //
 // Pipeline of one call (all on the context stream):
 //   k_node_prep   v (caller order) -> u (device order): u = v - X for Neo-Hookean
-//                 (displacement form of F = grad v), u = v for the p-Laplacian; also the
-//                 block partials of b.v.
+//                 (displacement form of F = grad v; u = v when the caller passes
+//                 displacements), u = v for the p-Laplacian; also the block partials of b.v.
 //   k_elem_f64    one thread per element (grid-stride, fixed grid): gathers u at the
 //                 dim+1 vertices, forms F = I + sum_{l>=1} (u_l - u_0) grad(phi_l)^T (the
 //                 same matrix as eq. Dv because sum_l grad(phi_l) = 0 and
 //                 sum_l X_l grad(phi_l)^T = I), evaluates W (and dW/dF), accumulates
 //                 |T| W, and writes the local forces r_{T,l} = |T| dW/dF grad(phi_l) to the
 //                 CSR position of (T, l); the last block to finish reduces the partials.
-//   k_gather      one thread per node: g_i = sum of its CSR segment - b_i (0 on Dirichlet
-//                 dofs), written in the caller's dof order.
+//   k_gather_bulk one lane per node, 32-node patch blocks staged in shared memory by bulk
+//                 copies: g_i = sum of its CSR segment - b_i (0 on Dirichlet dofs), written
+//                 in the caller's dof order.
 // Every reduction has a fixed order, so results are bitwise reproducible.
 #include "fe_internal.cuh"
+#include "gather_bulk.cuh"
 
 namespace fe {
 namespace {
@@ -172,6 +174,36 @@ __device__ __forceinline__ void load_u(const double* __restrict__ u, int32_t n, 
   }
 }
 
+template <int DIM>
+struct Mat64 {
+  double m[DIM][DIM];
+};
+
+// |T| dW/dF near F = I without O(1) terms: 2 C1 (H - L) + 2 delta (D1 + C1 / det F) cof F with
+// L = cof F - I, whose diagonal L_jj is formed from H (X0 = L_00 from the caller).  Out of
+// line: the common path keeps the registers and code of the plain form.
+template <int DIM>
+static __device__ __noinline__ Mat64<DIM> nh_stress_small_f64(Mat64<DIM> H, Mat64<DIM> C, double X0, double delta,
+                                                               double det, double a, double vT, double C1,
+                                                               double D1) {
+  double Ld[DIM];
+  if constexpr (DIM == 3) {
+    Ld[0] = X0;
+    Ld[1] = H.m[0][0] + H.m[2][2] + (H.m[0][0] * H.m[2][2] - H.m[0][2] * H.m[2][0]);
+    Ld[2] = H.m[0][0] + H.m[1][1] + (H.m[0][0] * H.m[1][1] - H.m[0][1] * H.m[1][0]);
+  } else {
+    Ld[0] = H.m[1][1];
+    Ld[1] = H.m[0][0];
+  }
+  const double cp = 2.0 * vT * delta * (D1 + C1 / det);
+  Mat64<DIM> P;
+#pragma unroll
+  for (int j = 0; j < DIM; ++j)
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) P.m[j][m] = fma(a, H.m[j][m] - (j == m ? Ld[j] : C.m[j][m]), cp * C.m[j][m]);
+  return P;
+}
+
 // ---- kernels ------------------------------------------------------------------------------
 
 template <int D, bool NH, int DIM>
@@ -300,20 +332,19 @@ __global__ void __launch_bounds__(kThreads) k_elem_f64(
         // whose diagonal L_jj is formed from H without the 1 (no O(1) term left).
         const double a = 2.0 * mp.C1 * vT;
         if (__any_sync(__activemask(), hsq < 1e-4)) {
-          double Ld[DIM];
-          if constexpr (DIM == 3) {
-            Ld[0] = X0;
-            Ld[1] = H[0][0] + H[2][2] + (H[0][0] * H[2][2] - H[0][2] * H[2][0]);
-            Ld[2] = H[0][0] + H[1][1] + (H[0][0] * H[1][1] - H[0][1] * H[1][0]);
-          } else {
-            Ld[0] = H[1][1];
-            Ld[1] = H[0][0];
-          }
-          const double cp = 2.0 * vT * delta * (mp.D1 + mp.C1 / det);
+          Mat64<DIM> h, cf;
 #pragma unroll
-          for (int j = 0; j < D; ++j)
+          for (int j = 0; j < DIM; ++j)
 #pragma unroll
-            for (int m = 0; m < DIM; ++m) P[j][m] = fma(a, H[j][m] - (j == m ? Ld[j] : Cm[j][m]), cp * Cm[j][m]);
+            for (int m = 0; m < DIM; ++m) {
+              h.m[j][m] = H[j][m];
+              cf.m[j][m] = Cm[j][m];
+            }
+          const Mat64<DIM> p = nh_stress_small_f64<DIM>(h, cf, X0, delta, det, a, vT, mp.C1, mp.D1);
+#pragma unroll
+          for (int j = 0; j < DIM; ++j)
+#pragma unroll
+            for (int m = 0; m < DIM; ++m) P[j][m] = p.m[j][m];
         } else {
           const double c = vT * (2.0 * mp.D1 * delta - 2.0 * mp.C1 / det);
 #pragma unroll
@@ -361,32 +392,6 @@ __global__ void __launch_bounds__(kThreads) k_elem_f64(
   if (ENERGY) {
     acc = block_sum(acc, sh);
     finish_energy(acc, partials, gridDim.x, node_partials, n_node_blocks, counter, J, sh);
-  }
-}
-
-// g_i = sum of the CSR segment of node i - b_i, 0 on Dirichlet dofs, caller's order.
-template <int D>
-__global__ void __launch_bounds__(kThreads) k_gather(int64_t nn, const int32_t* __restrict__ row_ptr,
-                                                     const double* __restrict__ r,
-                                                     const double* __restrict__ b,
-                                                     const uint8_t* __restrict__ dir,
-                                                     const int32_t* __restrict__ perm,
-                                                     double* __restrict__ g) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
-    double s[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) s[j] = 0.0;
-    const int32_t q1 = __ldg(row_ptr + i + 1);
-    for (int32_t q = __ldg(row_ptr + i); q < q1; ++q)
-#pragma unroll
-      for (int j = 0; j < D; ++j) s[j] += __ldg(r + (int64_t)q * D + j);
-    const int64_t dst = perm ? (int64_t)__ldg(perm + i) : i;
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      const double val = s[j] - b[i * D + j];
-      g[dst * D + j] = dir[i * D + j] ? 0.0 : val;
-    }
   }
 }
 
@@ -616,9 +621,9 @@ fe_status eval_t(fe_ctx* c, const double* v, double* J, double* dens, double* g,
 #undef FE_ELEM
   if (G) {
     prof_begin(c, kStageGather);
-    k_gather<D><<<grid_for(c->nn, 4 * kMaxNodeBlocks), kThreads, 0, s>>>(c->nn, c->row_ptr, c->r, c->b,
-                                                                         c->dir, c->perm, g);
+    const fe_status gs = launch_gather_bulk<D, AccF64>(c, c->r, g);
     prof_end(c, kStageGather);
+    if (gs) return gs;
     c->launches++;
   }
   return cuda_check(cudaGetLastError(), "eval f64 launch");
@@ -682,6 +687,25 @@ fe_status launch_eval_f64(fe_ctx* c, const double* v, double* J, double* dens, d
   }
   if (c->dim == 2) return eval_t<2, 1, FE_PLAPLACE>(c, v, J, dens, g, want_energy, want_grad);
   return eval_t<3, 1, FE_PLAPLACE>(c, v, J, dens, g, want_energy, want_grad);
+}
+
+// v (caller order) -> u (device order) and the b.v partials, as the first step of an
+// FP64 evaluation (used by the Hessian-vector product).
+fe_status launch_node_prep_f64(fe_ctx* c, const double* v) {
+  const int nb = grid_for(c->nn, kMaxNodeBlocks);
+  double* np = c->partials + kMaxElemBlocks;
+  const bool disp = input_is_disp(c);
+  const double sh = disp ? c->bX : 0.0;
+  cudaStream_t s = c->stream;
+  if (c->model == FE_NEOHOOKE) {
+    if (c->dim == 2) k_node_prep<2, true, 2><<<nb, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b, c->u, np, disp, sh);
+    else k_node_prep<3, true, 3><<<nb, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b, c->u, np, disp, sh);
+  } else {
+    if (c->dim == 2) k_node_prep<1, false, 2><<<nb, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b, c->u, np, false, 0.0);
+    else k_node_prep<1, false, 3><<<nb, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b, c->u, np, false, 0.0);
+  }
+  c->launches++;
+  return cuda_check(cudaGetLastError(), "node preparation");
 }
 
 fe_status launch_fd_f64(fe_ctx* c, const double* v, double eps, double* g, const int64_t* dofs,

@@ -1,0 +1,226 @@
+// fe_hessian.cu -- Hessian-vector products of the discrete energy (FP64):
+//   Hw = d/dt grad J(v + t w) at t = 0 on the free dofs,
+// the second derivative of J_grad = sum |T| W(F_T) (Sec. 1) along w, gathered over the nodal
+// patches like the exact gradient (Sec. 6.2); b.v has no second derivative.  Entries of w on
+// Dirichlet dofs are taken as 0 and Dirichlet rows of Hw are 0.
+//
+// Pipeline (context stream):
+//   k_node_prep   v -> u (the same kernel as the gradient)
+//   k_w_prep      w (caller order) -> device order, Dirichlet entries zeroed
+//   k_hvp_f64     one thread per element: H and dF = sum_{l>=1} (w_l - w_0) grad(phi_l)^T,
+//                 the directional derivative dP of dW/dF along dF, local contributions
+//                 |T| dP grad(phi_l) to the CSR slots
+//   k_gather_bulk per-node patch sums (no load term)
+// Neo-Hookean: with cof = cof F and d(cof) its derivative along dF,
+//   dP = 2 C1 dF + (2 C1 / det^2 + 2 D1) (cof : dF) cof + (2 D1 (det - 1) - 2 C1 / det) d(cof);
+// every term is O(|dF|), so no O(1) terms cancel near F = I.  p-Laplacian, s = |grad v|^2:
+//   dP = s^((p-2)/2) dF + (p - 2) s^((p-4)/2) (grad v . dF) grad v,  dP = dF for p = 2 and
+//   0 at grad v = 0 otherwise.
+#include "fe_internal.cuh"
+#include "gather_bulk.cuh"
+
+namespace fe {
+namespace {
+
+template <int D>
+__device__ __forceinline__ void load_vec(const double* __restrict__ u, int32_t n, double* out) {
+  if (D == 1) {
+    out[0] = __ldg(u + n);
+  } else if (D == 2) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(u) + n);
+    out[0] = a.x;
+    out[1] = a.y;
+  } else {
+    const double2* p = reinterpret_cast<const double2*>(u) + 2 * (int64_t)n;
+    const double2 a = __ldg(p), b = __ldg(p + 1);
+    out[0] = a.x;
+    out[1] = a.y;
+    out[2] = b.x;
+  }
+}
+
+// w (caller dof order) -> device order in the padded node layout of u, 0 on Dirichlet dofs.
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_w_prep(int64_t nn, const double* __restrict__ w,
+                                                     const int32_t* __restrict__ perm,
+                                                     const uint8_t* __restrict__ dir, double* __restrict__ wd) {
+  constexpr int DP = D == 3 ? 4 : D;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
+    const int64_t src = perm ? (int64_t)perm[i] : i;
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+      double x = 0.0;
+      if (j < D && !dir[i * D + j]) x = w[src * D + j];
+      wd[i * DP + j] = x;
+    }
+  }
+}
+
+template <int DIM, int D, int MODEL>
+__global__ void __launch_bounds__(kThreads) k_hvp_f64(int64_t ne, const int32_t* __restrict__ elems,
+                                                      const double* __restrict__ dphi, const double* __restrict__ vol,
+                                                      const double* __restrict__ u, const double* __restrict__ wd,
+                                                      const int32_t* __restrict__ slot, ModelParams mp,
+                                                      double* __restrict__ r, int* status) {
+  constexpr int K = DIM + 1;
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
+    double ul[K][D], wl[K][D];
+#pragma unroll
+    for (int l = 0; l < K; ++l) {
+      const int32_t n = __ldg(elems + (int64_t)l * ne + e);
+      load_vec<D>(u, n, ul[l]);
+      load_vec<D>(wd, n, wl[l]);
+    }
+    double g[DIM][DIM];
+#pragma unroll
+    for (int l = 0; l < DIM; ++l)
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) g[l][m] = __ldg(dphi + ((int64_t)l * DIM + m) * ne + e);
+    const double vT = __ldg(vol + e);
+    double H[D][DIM], dF[D][DIM];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double a[DIM], b[DIM];
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) {
+        a[l] = ul[l + 1][j] - ul[0][j];
+        b[l] = wl[l + 1][j] - wl[0][j];
+      }
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) {
+        double s = a[0] * g[0][m], t = b[0] * g[0][m];
+#pragma unroll
+        for (int l = 1; l < DIM; ++l) {
+          s = fma(a[l], g[l][m], s);
+          t = fma(b[l], g[l][m], t);
+        }
+        H[j][m] = s;
+        dF[j][m] = t;
+      }
+    }
+    double dP[D][DIM];
+    if constexpr (MODEL == FE_NEOHOOKE) {
+      double F[DIM][DIM], C[DIM][DIM], dC[DIM][DIM];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) F[j][m] = (j == m) ? 1.0 + H[j][m] : H[j][m];
+      double delta;
+      if constexpr (DIM == 3) {
+        // cofactors and their derivatives along dF: signed 2x2 minors of the other rows/columns
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            const int r0 = j == 0 ? 1 : 0, r1 = j == 2 ? 1 : 2;
+            const int c0 = m == 0 ? 1 : 0, c1 = m == 2 ? 1 : 2;
+            const double mn = F[r0][c0] * F[r1][c1] - F[r0][c1] * F[r1][c0];
+            const double dmn = dF[r0][c0] * F[r1][c1] + F[r0][c0] * dF[r1][c1] - dF[r0][c1] * F[r1][c0] -
+                               F[r0][c1] * dF[r1][c0];
+            const double sg = ((j + m) & 1) ? -1.0 : 1.0;
+            C[j][m] = sg * mn;
+            dC[j][m] = sg * dmn;
+          }
+        // det F - 1 without the O(1) cancellation: tr H + i2(H) + det H via the row-0 expansion
+        const double M00 = H[1][1] * H[2][2] - H[1][2] * H[2][1];
+        const double X = H[1][1] + H[2][2] + M00;
+        delta = H[0][0] + X + H[0][0] * X + H[0][1] * C[0][1] + H[0][2] * C[0][2];
+      } else {
+        C[0][0] = F[1][1];
+        C[0][1] = -F[1][0];
+        C[1][0] = -F[0][1];
+        C[1][1] = F[0][0];
+        dC[0][0] = dF[1][1];
+        dC[0][1] = -dF[1][0];
+        dC[1][0] = -dF[0][1];
+        dC[1][1] = dF[0][0];
+        delta = H[0][0] + H[1][1] + (H[0][0] * H[1][1] - H[0][1] * H[1][0]);
+      }
+      const double det = 1.0 + delta;
+      if (!(det > 0.0)) bad = true;
+      double cdf = 0.0;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) cdf = fma(C[j][m], dF[j][m], cdf);
+      const double rdet = 1.0 / det;
+      const double a = 2.0 * mp.C1 * vT;
+      const double bcoef = vT * (2.0 * mp.C1 * rdet * rdet + 2.0 * mp.D1) * cdf;
+      const double ccoef = vT * (2.0 * mp.D1 * delta - 2.0 * mp.C1 * rdet);
+#pragma unroll
+      for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) dP[j][m] = fma(a, dF[j][m], fma(bcoef, C[j][m], ccoef * dC[j][m]));
+    } else {
+      double s = 0.0, hd = 0.0;
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) {
+        s = fma(H[0][m], H[0][m], s);
+        hd = fma(H[0][m], dF[0][m], hd);
+      }
+      double c1, c2;
+      if (mp.pcase == 2) {
+        c1 = 1.0;
+        c2 = 0.0;
+      } else if (s > 0.0) {
+        c1 = (mp.pcase == 3) ? sqrt(s) : pow(s, 0.5 * (mp.p - 2.0));
+        c2 = (mp.p - 2.0) * c1 / s;
+      } else {
+        c1 = c2 = 0.0;
+      }
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) dP[0][m] = vT * fma(c1, dF[0][m], c2 * hd * H[0][m]);
+    }
+    // local contributions dP grad(phi_l) (l >= 1); l = 0 gets minus their sum
+    double r0[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) r0[j] = 0.0;
+#pragma unroll
+    for (int l = 1; l <= DIM; ++l) {
+      const int64_t q = __ldg(slot + (int64_t)l * ne + e);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        double s = dP[j][0] * g[l - 1][0];
+#pragma unroll
+        for (int m = 1; m < DIM; ++m) s = fma(dP[j][m], g[l - 1][m], s);
+        r[q * D + j] = s;
+        r0[j] -= s;
+      }
+    }
+    const int64_t q0 = __ldg(slot + e);
+#pragma unroll
+    for (int j = 0; j < D; ++j) r[q0 * D + j] = r0[j];
+  }
+  if (bad) atomicOr(status, kStatusDomain);
+}
+
+template <int DIM, int D, int MODEL>
+fe_status hvp_t(fe_ctx* c, const double* v, const double* w, double* Hw) {
+  cudaStream_t s = c->stream;
+  const ModelParams mp = model_params(c);
+  fe_status st = launch_node_prep_f64(c, v);
+  if (st) return st;
+  const int nb_node = grid_for(c->nn, kMaxNodeBlocks);
+  k_w_prep<D><<<nb_node, kThreads, 0, s>>>(c->nn, w, c->perm, c->dir, c->w_hvp);
+  c->launches++;
+  if (c->ne > 0) {
+    k_hvp_f64<DIM, D, MODEL><<<grid_for(c->ne, kMaxElemBlocks), kThreads, 0, s>>>(
+        c->ne, c->elems, c->dphi, c->vol, c->u, c->w_hvp, c->slot, mp, c->r, c->status);
+    c->launches++;
+  }
+  if ((st = launch_gather_bulk<D, AccF64>(c, c->r, Hw, nullptr))) return st;
+  c->launches++;
+  return cuda_check(cudaGetLastError(), "hessian-vector launch");
+}
+
+}  // namespace
+
+fe_status launch_hvp_f64(fe_ctx* c, const double* v, const double* w, double* Hw) {
+  if (c->model == FE_NEOHOOKE) return c->dim == 2 ? hvp_t<2, 2, FE_NEOHOOKE>(c, v, w, Hw) : hvp_t<3, 3, FE_NEOHOOKE>(c, v, w, Hw);
+  return c->dim == 2 ? hvp_t<2, 1, FE_PLAPLACE>(c, v, w, Hw) : hvp_t<3, 1, FE_PLAPLACE>(c, v, w, Hw);
+}
+
+}  // namespace fe

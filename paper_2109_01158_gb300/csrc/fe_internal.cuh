@@ -85,6 +85,7 @@ struct fe_ctx {
 
   // device: work buffers
   double* u = nullptr;         // nn*padded_d(d): displacement (Neo-Hookean) or v
+  double* w_hvp = nullptr;     // nn*padded_d(d): direction of a Hessian-vector product
   double* r = nullptr;         // ne*(dim+1)*d slot-ordered local forces (x2 for FD)
   float* r32 = nullptr;        // ne*(dim+1)*d, FP32 local forces
   float2* u_df = nullptr;      // nn*padded_d(d) double-float displacement (FE_DF64, FE_F32_COMP)
@@ -118,6 +119,18 @@ fe_status set_error(fe_status st, const std::string& msg);
 fe_status cuda_check(cudaError_t e, const char* what);
 
 // fe_precompute.cu
+// fe_batch.cu: descriptors and launches of the batched kernels (FE_DF64 meshes).  host_stage
+// (pinned) and dev_stage hold n descriptors of batch_item_bytes() each; work buffers hold
+// batch_work_bytes(mesh) bytes, 256-byte aligned.
+size_t batch_item_bytes();
+size_t batch_work_bytes(const fe_ctx* m);
+fe_status batch_enqueue(cudaStream_t s, const fe_batch_item* items, int n, void* host_stage, void* dev_stage,
+                        int* status);
+
+// fe_eval_f64.cu / fe_hessian.cu
+fe_status launch_node_prep_f64(fe_ctx* c, const double* v);
+fe_status launch_hvp_f64(fe_ctx* c, const double* v, const double* w, double* Hw);
+
 fe_status launch_precompute(fe_ctx* c);
 fe_status launch_load_vector(fe_ctx* c);
 

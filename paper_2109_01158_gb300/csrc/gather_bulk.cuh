@@ -1,8 +1,8 @@
 // gather_bulk.cuh -- warp-cooperative patch gather with bulk (TMA) copies.
 //
 // g_i = sum over the CSR segment of node i of the local forces r_{T,l} (written by the
-// element kernel to the CSR positions), minus b_i, and 0 on Dirichlet dofs (Sec. 6.2,
-// Remark 1).  Each warp owns 32 consecutive nodes; their segments form one contiguous range
+// element kernel to the CSR positions), minus b_i (when a load is given), and 0 on Dirichlet
+// dofs (Sec. 6.2, Remark 1).  Each warp owns 32 consecutive nodes; their segments form one contiguous range
 // of r, which lane 0 copies into the warp's shared-memory buffer with one cp.async.bulk
 // completing on an mbarrier.  Each lane then sums its node's segment in a fixed rotated order
 // (below), so results do not depend on the launch shape.  A range larger than the buffer is
@@ -17,6 +17,14 @@ namespace fe {
 constexpr int kGatherWarps = 8;
 constexpr int kGatherCap = 20480;   // bytes of shared memory per warp
 constexpr int kGatherSmem = kGatherWarps * kGatherCap;
+
+// Double slots, FP64 sums (the FP64 path).
+struct AccF64 {
+  using T = double;
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
 
 // Double-float slots (float2 per component), double-float sums.
 struct AccDF {
@@ -37,6 +45,11 @@ struct AccF32 {
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
+
+// The kernel and its launcher have internal linkage: every translation unit that uses them
+// compiles its own copy of the kernel, and the launcher's once-per-device attribute flag must
+// belong to that copy.
+namespace {
 
 template <int D, class Acc>
 __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
@@ -106,7 +119,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
       const int64_t dst = perm ? (int64_t)__ldg(perm + i) : i;
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        const double val = acc[j].value() - b[i * D + j];
+        const double val = b ? acc[j].value() - b[i * D + j] : acc[j].value();
         g[dst * D + j] = dir[i * D + j] ? 0.0 : val;
       }
     }
@@ -115,8 +128,9 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
 }
 
 // Launch on the context stream: one block of 8 warps per SM (160 KB of shared memory each).
+// b: the load vector subtracted from the sums (the context's b unless given; nullptr = 0).
 template <int D, class Acc>
-inline fe_status launch_gather_bulk(fe_ctx* c, const typename Acc::T* r, double* g) {
+inline fe_status launch_gather_bulk(fe_ctx* c, const typename Acc::T* r, double* g, const double* b) {
   static bool configured[64] = {false};
   if (c->device < 0 || c->device >= 64 || !configured[c->device]) {
     cudaError_t e = cudaFuncSetAttribute(k_gather_bulk<D, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -131,8 +145,15 @@ inline fe_status launch_gather_bulk(fe_ctx* c, const typename Acc::T* r, double*
   if (blocks > sms) blocks = sms;
   if (blocks < 1) blocks = 1;
   k_gather_bulk<D, Acc><<<(unsigned)blocks, kGatherWarps * 32, kGatherSmem, c->stream>>>(
-      c->nn, c->row_ptr, r, c->b, c->dir, c->perm, g, c->status);
+      c->nn, c->row_ptr, r, b, c->dir, c->perm, g, c->status);
   return cuda_check(cudaGetLastError(), "gather launch");
 }
+
+template <int D, class Acc>
+inline fe_status launch_gather_bulk(fe_ctx* c, const typename Acc::T* r, double* g) {
+  return launch_gather_bulk<D, Acc>(c, r, g, c->b);
+}
+
+}  // namespace
 
 }  // namespace fe

@@ -58,6 +58,7 @@ _SIGNATURES = {
     "fe_gradient_exact": [_vp, _vp, _vp],
     "fe_energy_gradient": [_vp, _vp, _vp, _vp],
     "fe_gradient_fd": [_vp, _vp, _dbl, _vp, _vp, _i64],
+    "fe_hessian_vector": [_vp, _vp, _vp, _vp],
     "fe_energy_gradient_host": [_vp, _vp, _vp, _vp],
     "fe_sync_status": [_vp],
     "fe_get_shape_gradients": [_vp, _vp, _vp],
@@ -73,6 +74,13 @@ _SIGNATURES = {
     "fe_batch_energy_gradient": [_vp, _vp, _int],
     "fe_batch_sync_status": [_vp],
     "fe_batch_launch_count": [_vp, _vp],
+    "fe_server_create": [_vp, _int, ctypes.c_size_t, _int],
+    "fe_server_destroy": [_vp],
+    "fe_server_submit": [_vp, _vp, _vp, _vp, _vp, _dbl, _vp],
+    "fe_server_wait": [_vp, _i64, _vp, _vp, _vp],
+    "fe_server_now": [_vp, _vp],
+    "fe_server_stats": [_vp, _vp, _vp, _vp, _vp],
+    "fe_server_reset_stats": [_vp],
     "fe_energy_noalloc": [_int, _vp, _int, _int, _int, _dbl, _dbl, _dbl, _i64, _vp, _i64, _vp, _vp,
                           _vp, _vp, _vp, _vp],
 }
@@ -136,6 +144,7 @@ fe_energy = _checked("fe_energy")
 fe_gradient_exact = _checked("fe_gradient_exact")
 fe_energy_gradient = _checked("fe_energy_gradient")
 fe_gradient_fd = _checked("fe_gradient_fd")
+fe_hessian_vector = _checked("fe_hessian_vector")
 fe_energy_gradient_host = _checked("fe_energy_gradient_host")
 fe_get_shape_gradients = _checked("fe_get_shape_gradients")
 fe_get_patches = _checked("fe_get_patches")
@@ -209,6 +218,80 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+fe_server_create = _checked("fe_server_create")
+fe_server_destroy = _checked("fe_server_destroy")
+fe_server_submit = _checked("fe_server_submit")
+fe_server_now = _checked("fe_server_now")
+fe_server_stats = _checked("fe_server_stats")
+fe_server_reset_stats = _checked("fe_server_reset_stats")
+
+
+def fe_server_wait(server, ticket, t_arrival, t_start, t_done) -> int:
+    """Returns FE_OK or FE_EDOMAIN (the request's status); raises on other errors."""
+    st = load_library().fe_server_wait(server, ticket, t_arrival, t_start, t_done)
+    if st not in (FE_OK, FE_EDOMAIN):
+        raise FEError(st, "fe_server_wait", fe_last_error())
+    return st
+
+
+class NativeServer:
+    """Continuous-batching server (fe_server): energy + gradient requests on resident
+    FE_DF64 meshes, host vectors in and host results out, served by the library's own worker
+    and completion threads.  `submit` keeps references to the arrays until `wait`."""
+
+    def __init__(self, device=0, hbm_budget=8 << 30, max_batch=256):
+        h = ctypes.c_void_p()
+        fe_server_create(ctypes.byref(h), int(device), int(hbm_budget), int(max_batch))
+        self.handle = h
+        self._keep = {}
+
+    def now(self) -> float:
+        t = ctypes.c_double()
+        fe_server_now(self.handle, ctypes.byref(t))
+        return t.value
+
+    def submit(self, mesh, v, J, g, t_arrival=-1.0) -> int:
+        """v, g: float64 numpy arrays of mesh.ndof entries (C order); J: float64 array of one
+        entry.  t_arrival: arrival time on the server clock (< 0 = now)."""
+        for a, n in ((v, mesh.ndof), (g, mesh.ndof), (J, 1)):
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size == n):
+                raise TypeError("v, g and J must be C-contiguous float64 numpy arrays of the mesh's sizes")
+        t = ctypes.c_int64()
+        fe_server_submit(self.handle, mesh.ctx, v.ctypes.data, J.ctypes.data, g.ctypes.data, float(t_arrival),
+                         ctypes.byref(t))
+        self._keep[t.value] = (mesh, v, J, g)
+        return t.value
+
+    def wait(self, ticket):
+        """(status, t_arrival, t_start, t_done); status FE_OK or FE_EDOMAIN, raises otherwise."""
+        ta, ts, td = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        try:
+            st = fe_server_wait(self.handle, int(ticket), ctypes.byref(ta), ctypes.byref(ts), ctypes.byref(td))
+        finally:
+            self._keep.pop(ticket, None)
+        return st, ta.value, ts.value, td.value
+
+    def reset_stats(self):
+        fe_server_reset_stats(self.handle)
+
+    def stats(self) -> dict:
+        v = [ctypes.c_int64() for _ in range(4)]
+        fe_server_stats(self.handle, *[ctypes.byref(x) for x in v])
+        return dict(zip(("batches", "max_batch", "launches", "completed"), (x.value for x in v)))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            fe_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 FE_PROFILE_STAGES = 5
 PROFILE_STAGE_NAMES = ("node_prep", "element", "gather", "fd_element", "fd_gather")
@@ -331,6 +414,14 @@ class FEMesh:
             g = torch.empty(dofs.numel(), dtype=torch.float64, device=self.device)
             fe_gradient_fd(self.ctx, _ptr(v), float(eps), _ptr(g), _ptr(dofs), dofs.numel())
         return g
+
+    def hessian_vector(self, v, w, out=None):
+        """Hw = d/dt grad J(v + t w) at t = 0 on the free dofs (FP64)."""
+        v, w = self._vec(v), self._vec(w)
+        self._sync_stream()
+        Hw = out if out is not None else torch.empty(self.ndof, dtype=torch.float64, device=self.device)
+        fe_hessian_vector(self.ctx, _ptr(v), _ptr(w), _ptr(Hw))
+        return Hw
 
     def energy_gradient_host(self, v_host, g_host=None):
         """End-to-end call on host buffers (numpy float64; pinned memory is fastest)."""

@@ -11,7 +11,8 @@ trial point with det F <= 0 has J = +Inf and is rejected like any point without 
 
 `lbfgs` runs one minimisation through an evaluator `ev(v) -> (J, g)`; `lbfgs_batched` runs
 many instances in lockstep, evaluating every active instance's trial point in one batched
-launch (fe_batch_energy_gradient) per line-search round.
+launch (fe_batch_energy_gradient) per line-search round.  `newton_cg` is a trust-region
+Newton-CG method on the kernels' Hessian-vector products (fe_hessian_vector).
 """
 from __future__ import annotations
 
@@ -226,6 +227,128 @@ def lbfgs_batched(batch_eval, v0s, *, m: int = 10, gtol: float = 1e-6, relative:
     secs = time.perf_counter() - t0
     return [LBFGSResult(s.v, s.J, _gnorm(s.g), s.iters, s.evals, _gnorm(s.g) <= tols[k], secs, s.history)
             for k, s in enumerate(states)]
+
+
+@dataclass
+class NewtonResult:
+    v: torch.Tensor
+    J: float
+    gnorm: float
+    iters: int
+    evals: int
+    hvps: int
+    converged: bool
+    seconds: float
+    history: list = field(default_factory=list)   # (J, ||g||_inf, CG iterations) per iteration
+
+
+def _to_boundary(z, d, radius):
+    """tau >= 0 with ||z + tau d|| = radius."""
+    dd = float(torch.dot(d, d).item())
+    zd = float(torch.dot(z, d).item())
+    zz = float(torch.dot(z, z).item())
+    disc = max(zd * zd + dd * (radius * radius - zz), 0.0)
+    return (-zd + math.sqrt(disc)) / max(dd, 1e-300)
+
+
+def _cg_steihaug(g, hv, radius, tol, max_cg):
+    """Steihaug's truncated CG (Nocedal & Wright, Alg. 7.2) for min g.z + z.Hz/2 within
+    ||z|| <= radius.  Returns (z, Hz, iterations, hit_boundary)."""
+    z = torch.zeros_like(g)
+    Hz = torch.zeros_like(g)
+    r = g.clone()
+    d = -r
+    rr = float(torch.dot(r, r).item())
+    if math.sqrt(rr) <= tol:
+        return z, Hz, 0, False
+    for k in range(1, max_cg + 1):
+        Hd = hv(d)
+        dHd = float(torch.dot(d, Hd).item())
+        if not dHd > 0.0:
+            tau = _to_boundary(z, d, radius)
+            return z + tau * d, Hz + tau * Hd, k, True
+        alpha = rr / dHd
+        z_new = z + alpha * d
+        if float(torch.linalg.vector_norm(z_new).item()) >= radius:
+            tau = _to_boundary(z, d, radius)
+            return z + tau * d, Hz + tau * Hd, k, True
+        z, Hz = z_new, Hz + alpha * Hd
+        r = r + alpha * Hd
+        rr_new = float(torch.dot(r, r).item())
+        if math.sqrt(rr_new) <= tol:
+            return z, Hz, k, False
+        d = -r + (rr_new / rr) * d
+        rr = rr_new
+    return z, Hz, max_cg, False
+
+
+def newton_cg(ev, hvp, v0: torch.Tensor, *, gtol: float = 1e-6, relative: bool = False,
+              max_iter: int = 1000, max_cg: int = 5000, eta_max: float = 0.5,
+              eps_f: float | None = None, radius_max: float = 1e30) -> NewtonResult:
+    """Trust-region Newton-CG (Nocedal & Wright, Alg. 4.1 with Steihaug's CG), the analogue
+    of the trust-region method the paper minimises with (Sec. 7), driven by the kernels'
+    Hessian-vector products hvp(v, w) -> Hw.  The inner CG stops at ||r|| <= eta ||g||,
+    eta = min(eta_max, sqrt(||g|| / ||g_0||)), at the trust-region boundary, or at a direction
+    of non-positive curvature (the p-Laplacian's Hessian vanishes where grad v = 0).  The
+    first radius is the length of the Cauchy step.  A step is accepted when the ratio of
+    actual to predicted decrease exceeds 1e-4, or -- at the rounding level of J -- when J
+    does not rise above it and ||g|| decreases."""
+    t0 = time.perf_counter()
+    eps_f = _noise(ev, eps_f)
+    J, g = ev(v0)
+    J = float(J)
+    v = v0.clone()
+    gn = _gnorm(g)
+    tol = gtol * (gn if relative else 1.0)
+    g2 = float(torch.linalg.vector_norm(g).item())
+    g0_2 = g2
+    hist = [(J, gn, 0)]
+    evals, hvps, it = 1, 0, 0
+    Hg = hvp(v, g)
+    hvps += 1
+    gHg = float(torch.dot(g, Hg).item())
+    radius = g2 ** 3 / gHg if gHg > 0.0 else g2
+    rejected = 0
+    while gn > tol and it < max_iter and rejected < 60:
+        eta = min(eta_max, math.sqrt(g2 / max(g0_2, 1e-300)))
+        cnt = [0]
+
+        def hv(w):
+            cnt[0] += 1
+            return hvp(v, w)
+
+        z, Hz, k, boundary = _cg_steihaug(g, hv, radius, eta * g2, max_cg)
+        hvps += cnt[0]
+        pred = -(float(torch.dot(g, z).item()) + 0.5 * float(torch.dot(z, Hz).item()))
+        v_new = v + z
+        J_new, g_new = ev(v_new)
+        evals += 1
+        J_new = float(J_new)
+        zn = float(torch.linalg.vector_norm(z).item())
+        rho = (J - J_new) / pred if pred > 0.0 and math.isfinite(J_new) else -1.0
+        noise_ok = (math.isfinite(J_new) and J_new <= J + eps_f * abs(J)
+                    and _gnorm(g_new) < gn and pred > 0.0 and abs(J - J_new) <= 2 * eps_f * abs(J))
+        if rho < 0.25 and not noise_ok:
+            radius = 0.25 * zn
+        elif rho > 0.75 and boundary:
+            radius = min(2.0 * radius, radius_max)
+        if rho > 1e-4 or noise_ok:
+            v, J, g = v_new, J_new, g_new
+            g2 = float(torch.linalg.vector_norm(g).item())
+            gn = _gnorm(g)
+            it += 1
+            rejected = 0
+            hist.append((J, gn, k))
+        else:
+            rejected += 1
+    return NewtonResult(v, J, gn, it, evals, hvps, gn <= tol, time.perf_counter() - t0, hist)
+
+
+def mesh_hvp(mesh):
+    """hvp(v, w) -> Hw with the library's FP64 Hessian-vector kernel."""
+    def hvp(v, w):
+        return mesh.hessian_vector(v, w)
+    return hvp
 
 
 # ----------------------------------------------------------------------------------------

@@ -1,12 +1,13 @@
 """Serving: continuous batching of energy + gradient requests over resident meshes.
 
 A request asks for J(v) and grad J(v) on one mesh.  Meshes are precomputed once and stay
-resident on the device (a catalogue keyed by model and size).  The server runs in real time:
-requests arrive (Poisson process), wait in a FIFO, and are admitted while their device bytes
-(the scratch of the batched kernels plus v and g) fit in the HBM budget.  Each server step
-evaluates every admitted request in one fe_batch_energy_gradient call (three launches for the
-whole batch); requests that arrive while a step runs join the next step.  The one-at-a-time
-baseline runs the same kernels with batches of one request, in arrival order.
+resident on the device (a catalogue keyed by model and size).  The server runs in real time
+in the library (fe_server): requests arrive (Poisson process), wait in a FIFO, and are
+admitted while their device bytes (the scratch of the batched kernels plus v and g) fit in
+the HBM budget.  Each batch is evaluated in three launches whatever its size; requests that
+arrive while a batch runs join the next one, which is prepared and enqueued while the GPU
+is still busy.  The one-at-a-time baseline runs the same kernels with batches of one
+request, in arrival order.
 
 Latency of a request = completion time - arrival time; the report gives p50/p99 latency,
 requests/s and elements/s for both modes at the same offered load.
@@ -15,7 +16,6 @@ from __future__ import annotations
 
 import math
 import time
-from collections import deque
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -124,17 +124,6 @@ class Catalogue:
 # ----------------------------------------------------------------------------------------
 
 @dataclass
-class Slot:
-    req: Request
-    mesh: fem.FEMesh
-    v: torch.Tensor
-    J: torch.Tensor
-    g: torch.Tensor
-    work: torch.Tensor
-    nbytes: int
-
-
-@dataclass
 class ServeStats:
     mode: str
     n: int
@@ -157,84 +146,79 @@ class ServeStats:
 
 
 class Server:
-    """Real-time server over a catalogue of resident meshes."""
+    """Real-time server over a catalogue of resident meshes.  The stream of requests is
+    handed to the library's native server (fe_server) with each request's arrival time; its
+    worker thread admits the arrived requests FIFO within the HBM budget and batches them
+    (mode 'batched', up to max_batch per launch) or serves them one at a time ('serial'),
+    with the same kernels either way."""
 
     def __init__(self, catalogue: Catalogue, hbm_budget: int = 8 << 30, max_batch: int = 256):
         self.cat = catalogue
         self.budget = int(hbm_budget)
         self.max_batch = max_batch
-        self.dev = torch.device("cuda", catalogue.device)
-        self.batch = fem.Batch(catalogue.device)
+        self._servers = {}      # mode -> fe_server, created on first use and kept
+        self._pinned = {}       # id(request vector) -> page-locked (v, g) buffers
 
-    def _admit(self, r: Request) -> Slot:
-        mesh = self.cat.get(r.key)
-        wb = fem.Batch.work_bytes(mesh)
-        work = torch.empty(wb + 256, dtype=torch.uint8, device=self.dev)
-        off = (-work.data_ptr()) % 256
-        work = work[off: off + wb]
-        v = torch.from_numpy(r.v).to(self.dev, non_blocking=True)
-        J = torch.empty((), dtype=torch.float64, device=self.dev)
-        g = torch.empty(mesh.ndof, dtype=torch.float64, device=self.dev)
-        return Slot(r, mesh, v, J, g, work, wb + 16 * mesh.ndof)
+    def _buffers(self, r, mesh):
+        """Page-locked copies of the request's vector and a page-locked result buffer (the
+        server copies those by DMA directly), made once per request vector."""
+        key = id(r.v)
+        if key not in self._pinned:
+            vt = torch.empty(mesh.ndof, dtype=torch.float64).pin_memory()
+            gt = torch.zeros(mesh.ndof, dtype=torch.float64).pin_memory()
+            vt.numpy()[:] = r.v
+            self._pinned[key] = (r.v, vt, gt)
+        _, vt, gt = self._pinned[key]
+        return vt.numpy(), gt.numpy()
 
-    def need_bytes(self, r: Request) -> int:
-        mesh = self.cat.get(r.key)
-        return fem.Batch.work_bytes(mesh) + 16 * mesh.ndof
+    def _server(self, mode):
+        if mode not in self._servers:
+            cap = self.max_batch if mode == "batched" else 1
+            self._servers[mode] = fem.NativeServer(self.cat.device, self.budget, cap)
+        return self._servers[mode]
 
-    def run(self, requests: list, mode: str = "batched", keep_results: bool = True) -> ServeStats:
-        """Serve `requests` (sorted by arrival) in real time; mode 'batched' or 'serial'."""
+    def close(self):
+        for srv in self._servers.values():
+            srv.close()
+        self._servers.clear()
+        self._pinned.clear()
+
+    def run(self, requests: list, mode: str = "batched", keep_results: bool = True,
+            lead_s: float = 0.05) -> ServeStats:
+        """Serve `requests` (sorted by arrival, seconds from the start of the stream) in real
+        time.  The stream starts lead_s after the server is created, so that every request is
+        submitted before it arrives; latency = completion - arrival on the server clock."""
         assert mode in ("batched", "serial")
-        cap = self.max_batch if mode == "batched" else 1
         for r in requests:           # meshes are resident before the stream starts
             self.cat.get(r.key)
-        torch.cuda.synchronize(self.dev)
-        l0 = self.batch.launch_count()
-        pending: deque = deque()
-        nxt, done, steps, max_b = 0, 0, 0, 0
-        t0 = time.perf_counter()
-        while done < len(requests):
-            now = time.perf_counter() - t0
-            while nxt < len(requests) and requests[nxt].arrival <= now:
-                pending.append(requests[nxt])
-                nxt += 1
-            if not pending:
-                wait = requests[nxt].arrival - now
-                if wait > 2e-4:
-                    time.sleep(wait - 1e-4)
-                continue
-            # admission: FIFO while the request's device bytes fit in the budget
-            slots, used = [], 0
-            while pending and len(slots) < cap:
-                need = self.need_bytes(pending[0])
-                if slots and used + need > self.budget:
-                    break
-                r = pending.popleft()
-                slots.append(self._admit(r))
-                used += need
-            t_start = time.perf_counter() - t0
-            self.batch.run([(s.mesh, s.v, s.J, s.g, s.work) for s in slots])
-            st = self.batch.sync_status()
-            t_done = time.perf_counter() - t0
-            steps += 1
-            max_b = max(max_b, len(slots))
-            for s in slots:
-                s.req.t_start = t_start
-                s.req.t_done = t_done
-                if keep_results:
-                    s.req.J = s.J.item()
-                    s.req.g = s.g.cpu().numpy()
-                done += 1
-            del slots
-            if st not in (fem.FE_OK, fem.FE_EDOMAIN):
-                raise RuntimeError(f"batch status {st}")
-        wall = time.perf_counter() - t0
+        torch.cuda.synchronize(torch.device("cuda", self.cat.device))
+        srv = self._server(mode)
+        srv.reset_stats()
+        # the callers' request and result buffers exist (page-locked) before the stream starts
+        bufs = []
+        for r in requests:
+            mesh = self.cat.get(r.key)
+            v, g = self._buffers(r, mesh)
+            bufs.append((mesh, v, np.zeros(1), g))
+        t0 = srv.now() + lead_s + 2e-5 * len(requests)
+        sub = []
+        for r, (mesh, v, J, g) in zip(requests, bufs):
+            sub.append((r, srv.submit(mesh, v, J, g, t0 + r.arrival), J, g))
+        for r, ticket, J, g in sub:
+            st, ta, ts, td = srv.wait(ticket)
+            r.t_start, r.t_done = ts - t0, td - t0
+            if keep_results:
+                r.J = float(J[0])
+                r.g = g.copy()
+        stats = srv.stats()
+        wall = max(r.t_done for r in requests) if requests else 0.0
         lat = np.array([r.latency for r in requests]) * 1e3
         elems = sum(self.cat.get(r.key).ne for r in requests)
         rate = len(requests) / max(requests[-1].arrival, 1e-9)
         return ServeStats(mode, len(requests), rate, wall, float(np.percentile(lat, 50)),
-                          float(np.percentile(lat, 99)), float(lat.mean()), max_b, steps,
-                          len(requests) / wall, elems / wall / 1e9,
-                          self.batch.launch_count() - l0, lat.tolist())
+                          float(np.percentile(lat, 99)), float(lat.mean()), stats["max_batch"],
+                          stats["batches"], len(requests) / wall, elems / wall / 1e9,
+                          stats["launches"], lat.tolist())
 
 
 def make_requests(n: int = 512, seed: int = 3, rate: float = 1000.0, catalogue: Catalogue | None = None):

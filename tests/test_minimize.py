@@ -12,7 +12,7 @@ import oracle
 from paper_2109_01158_gb300 import meshgen as mg
 
 torch = pytest.importorskip("torch")
-from paper_2109_01158_gb300.minimize import lbfgs, lbfgs_batched  # noqa: E402
+from paper_2109_01158_gb300.minimize import lbfgs, lbfgs_batched, newton_cg  # noqa: E402
 
 
 def _oracle_ev(om):
@@ -71,6 +71,39 @@ def test_lbfgs_rejects_inverted_trial_points():
     res = lbfgs(_oracle_ev(om), torch.from_numpy(w.v), gtol=1e-6, relative=True, max_iter=400)
     assert res.converged and math.isfinite(res.J)
     assert oracle.OracleMesh(w).energy(res.v.numpy())[1] == oracle.OK
+
+
+def _oracle_hvp(om):
+    def hvp(v, x):
+        H, _ = om.hessian_vector(v.cpu().numpy(), x.cpu().numpy())
+        return torch.from_numpy(H).to(v.device)
+    return hvp
+
+
+def test_newton_cg_p2_converges_in_one_step():
+    """p = 2 is a quadratic: the first Newton step (CG to 1e-12) lands on the solution of
+    the five-point system, the same minimiser as L-BFGS."""
+    w = mg.plaplace_square(16, p=2.0)
+    om = oracle.OracleMesh(w)
+    res = newton_cg(_oracle_ev(om), _oracle_hvp(om), torch.zeros(w.nn, dtype=torch.float64),
+                    gtol=1e-11, eta_max=1e-12)
+    ref = lbfgs(_oracle_ev(om), torch.zeros(w.nn, dtype=torch.float64), gtol=1e-12)
+    assert res.converged and res.iters <= 3
+    np.testing.assert_allclose(res.v.numpy(), ref.v.numpy(), atol=1e-9 * np.abs(ref.v.numpy()).max())
+
+
+@pytest.mark.parametrize("p", [3.0, 4.5])
+def test_newton_cg_lshape_matches_lbfgs(p):
+    """The degenerate p-Laplacian (p > 2: the Hessian vanishes where grad v = 0, as at the
+    start v = 0) on the L-shape: trust-region Newton-CG reaches the same minimum as L-BFGS,
+    in far fewer iterations, and satisfies the Euler identity J = (1/p - 1) b.u."""
+    w = _lshape(3, p)
+    om = oracle.OracleMesh(w)
+    res = newton_cg(_oracle_ev(om), _oracle_hvp(om), torch.zeros(w.nn, dtype=torch.float64), gtol=1e-10)
+    ref = lbfgs(_oracle_ev(om), torch.zeros(w.nn, dtype=torch.float64), gtol=1e-10)
+    assert res.converged and res.iters < ref.iters / 3
+    assert abs(res.J - ref.J) <= 1e-11 * abs(ref.J)
+    assert abs(res.J - (1.0 / p - 1.0) * float(om.b @ res.v.numpy())) <= 1e-8 * abs(res.J)
 
 
 # ---------------------------------------------------------------------------------------
@@ -139,3 +172,28 @@ def test_gpu_lockstep_instances_match_individual_runs():
         single = lbfgs(minimize.mesh_evaluator(mesh), v, gtol=1e-8, relative=True)
         assert r.converged and single.converged
         assert abs(r.J - single.J) <= 1e-9 * max(abs(single.J), 1e-30) + 1e-14
+
+
+@pytest.mark.gpu
+def test_gpu_newton_cg_matches_oracle_driven_and_lbfgs():
+    """Trust-region Newton-CG on the kernels' Hessian-vector products: the L-shape (p = 3,
+    level 4) against the oracle-driven run, and the 3D gravity problem (16^3 x 6, displacement
+    input) against L-BFGS on the kernels."""
+    fem, minimize = _gpu()
+    w = _lshape(4)
+    om = oracle.OracleMesh(w)
+    ref = newton_cg(_oracle_ev(om), _oracle_hvp(om), torch.zeros(w.nn, dtype=torch.float64), gtol=1e-10)
+    gm = fem.FEMesh.from_workload(w)
+    z = torch.zeros(w.nn, dtype=torch.float64, device="cuda")
+    res = newton_cg(minimize.mesh_evaluator(gm), minimize.mesh_hvp(gm), z, gtol=1e-10)
+    assert res.converged and ref.converged
+    assert abs(res.J - ref.J) <= 1e-11 * abs(ref.J)
+    w3 = mg.neohooke_cube3d(16)
+    w3.f = np.tile([0.0, 0.0, -1e-2], w3.nn)
+    g3 = fem.FEMesh.from_workload(w3)
+    g3.set_input(fem.FE_INPUT_DISPLACEMENT)
+    u0 = torch.zeros(w3.ndof, dtype=torch.float64, device="cuda")
+    nt = newton_cg(minimize.mesh_evaluator(g3), minimize.mesh_hvp(g3), u0, gtol=1e-8, relative=True)
+    lb = lbfgs(minimize.mesh_evaluator(g3), u0, gtol=1e-8, relative=True)
+    assert nt.converged and lb.converged and nt.iters < lb.iters / 10
+    assert abs(nt.J - lb.J) <= 1e-13 * abs(lb.J)

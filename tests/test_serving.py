@@ -117,3 +117,80 @@ def test_server_stream_results(mode):
         batch.sync_status()
         assert it[2].item() == r.J
         np.testing.assert_array_equal(it[3].cpu().numpy(), r.g)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("pinned", [False, True], ids=["pageable", "pinned"])
+@pytest.mark.parametrize("max_batch", [256, 1], ids=["batched", "serial"])
+def test_native_server_results_equal_the_batch_call(max_batch, pinned):
+    """fe_server (host vectors in, host results out; staged through its pinned buffers, or
+    copied by DMA straight from page-locked caller buffers) returns bitwise the J and g of the
+    batch call on each request alone, whatever the batching; every request completes after
+    it arrives and after it started."""
+    fem, serve = _gpu()
+    cat = serve.Catalogue(0)
+    keys = [("plap", 3.0, 23), ("nh3", 8), ("nh2", 45), ("plap", 1.5, 32), ("nh3", 8), ("nh2", 23)] * 3
+    reqs = []
+    for k, key in enumerate(keys):
+        cat.get(key)
+        reqs.append((key, serve.request_vector(cat.workloads[key], k)))
+    batch = fem.Batch(0)
+    alone = []
+    for key, v in reqs:
+        it = _item(fem, cat.get(key), v)
+        batch.run([it])
+        assert batch.sync_status() == fem.FE_OK
+        alone.append((it[2].item(), it[3].cpu().numpy()))
+    srv = fem.NativeServer(0, 1 << 30, max_batch)
+    t0 = srv.now()
+    sub = []
+    keep = []
+    for k, (key, v) in enumerate(reqs):
+        mesh = cat.get(key)
+        J, g = np.empty(1), np.empty(mesh.ndof)
+        if pinned:
+            vt = torch.from_numpy(v).pin_memory()
+            gt = torch.empty(mesh.ndof, dtype=torch.float64).pin_memory()
+            keep.append((vt, gt))
+            v, g = vt.numpy(), gt.numpy()
+        sub.append((srv.submit(mesh, v, J, g, t0 + 1e-4 * k), J, g))
+    for (ticket, J, g), (Ja, ga) in zip(sub, alone):
+        st, ta, ts, td = srv.wait(ticket)
+        assert st == fem.FE_OK and ta <= ts <= td
+        assert J[0] == Ja
+        np.testing.assert_array_equal(g, ga)
+    stats = srv.stats()
+    assert stats["completed"] == len(reqs) and stats["launches"] == 3 * stats["batches"]
+    if max_batch == 1:
+        assert stats["max_batch"] == 1 and stats["batches"] == len(reqs)
+    srv.close()
+
+
+@pytest.mark.gpu
+def test_native_server_admission_arrivals_and_domain_errors():
+    fem, serve = _gpu()
+    w = mg.neohooke_cube3d(6)
+    mesh = fem.FEMesh.from_workload(w, precisions=(fem.FE_DF64,))
+    need = fem.Batch.work_bytes(mesh) + 16 * mesh.ndof
+    # a request larger than the whole budget is refused at submission
+    small = fem.NativeServer(0, need // 2, 8)
+    with pytest.raises(fem.FEError):
+        small.submit(mesh, w.v.copy(), np.empty(1), np.empty(mesh.ndof))
+    small.close()
+    # a budget of about one request serialises the batches; a future arrival is not started
+    # early; an inverted element gives FE_EDOMAIN and J = +Inf for that request only
+    srv = fem.NativeServer(0, need + 4096, 64)
+    bad = w.coords.ravel().copy()
+    bad[3 * 21] += 2.0
+    t0 = srv.now()
+    outs = []
+    for k, v in enumerate([w.v, bad, w.v]):
+        J, g = np.empty(1), np.empty(mesh.ndof)
+        outs.append((srv.submit(mesh, np.ascontiguousarray(v), J, g, t0 + 0.05 * (k + 1)), J, g))
+    res = [srv.wait(t) for t, _, _ in outs]
+    assert [r[0] for r in res] == [fem.FE_OK, fem.FE_EDOMAIN, fem.FE_OK]
+    for k, (st, ta, ts, td) in enumerate(res):
+        assert ts >= ta >= t0 + 0.05 * (k + 1) - 1e-9
+    assert outs[1][1][0] == math.inf and np.isfinite(outs[0][1][0]) and outs[0][1][0] == outs[2][1][0]
+    assert srv.stats()["max_batch"] == 1
+    srv.close()
