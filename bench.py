@@ -71,9 +71,9 @@ def sources_sha256(prec):
     return h.hexdigest()
 
 
-def recorded_traffic(prec, dim, ne):
-    """DRAM bytes per launch of the element kernel scaled to ne elements, or None when there is
-    no capture for this kernel or its sources changed since."""
+def traffic_record(prec, dim):
+    """The ncu capture of the element kernel, or None when there is none for this kernel or
+    its sources changed since."""
     try:
         with open(TRAFFIC_FILE) as fh:
             rec = json.load(fh)[prec]
@@ -81,7 +81,13 @@ def recorded_traffic(prec, dim, ne):
         return None
     if rec.get("dim") != dim or rec.get("sources_sha256") != sources_sha256(prec):
         return None
-    return float(rec["bytes_per_element"]) * ne
+    return rec
+
+
+def recorded_traffic(prec, dim, ne):
+    """DRAM bytes per launch of the element kernel scaled to ne elements (or None)."""
+    rec = traffic_record(prec, dim)
+    return None if rec is None else float(rec["bytes_per_element"]) * ne
 
 
 def load_peaks():
@@ -322,6 +328,13 @@ def run_ours(args, rank, world, local):
         roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": hbm_achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind}
     roof["traffic"] = recorded_traffic(prec, w.dim, w.ne)
+    trec = traffic_record(prec, w.dim)
+    if trec is not None:
+        sc = w.ne / trec["elements"]
+        roof["traffic_read"] = trec["dram_bytes_read"] * sc
+        roof["traffic_write"] = trec["dram_bytes_write"] * sc
+        roof["traffic_note"] = ("reads are the algorithmic element and node bytes (no re-reads); writes are "
+                                "the local forces (dim+1)*d per element, read back by the patch gather")
     roof["kernel"] = "k_elem_%s (energy+gradient)" % prec
     roof["kernel_ms"] = elem_ms
     roof["algorithmic_bytes_per_launch"] = elem_bytes

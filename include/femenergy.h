@@ -172,9 +172,12 @@ fe_status fe_hessian_vector(fe_ctx* ctx, const double* v_dev, const double* w_de
 fe_status fe_gradient_fd(fe_ctx* ctx, const double* v_dev, double eps, double* g_dev,
                          const int64_t* dofs_dev, int64_t n_dofs);
 
-/* End-to-end call with HOST buffers: copies v_host to the device, evaluates the energy
- * and the exact gradient, copies J and g back and synchronises.  J_host: one double;
- * g_host: n_nodes*d doubles.  Returns FE_EDOMAIN if some det F <= 0. */
+/* End-to-end call with HOST buffers: evaluates the energy and the exact gradient of v_host
+ * and returns J and g in host memory, then synchronises.  J_host: one double; g_host:
+ * n_nodes*d doubles.  Page-locked buffers (cudaMallocHost / cudaHostAlloc, mapped into the
+ * device address space) are read and written by the kernels directly over the host link;
+ * pageable buffers are copied through device staging buffers.  Returns FE_EDOMAIN if some
+ * det F <= 0. */
 fe_status fe_energy_gradient_host(fe_ctx* ctx, const double* v_host, double* J_host,
                                   double* g_host);
 

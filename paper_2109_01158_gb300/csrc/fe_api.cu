@@ -502,18 +502,37 @@ fe_status fe_gradient_fd(fe_ctx* c, const double* v, double eps, double* gout, c
   return launch_fd_f64(c, v, eps, gout, dofs, ndofs);
 }
 
+// Device address of page-locked host memory mapped into the device's address space, or
+// nullptr (pageable memory, or a registration without a mapping).
+static void* mapped_device_ptr(const void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost) ? a.devicePointer : nullptr;
+}
+
 fe_status fe_energy_gradient_host(fe_ctx* c, const double* v_host, double* J_host, double* g_host) {
   fe_status st = check_ready(c);
   if (st) return st;
   if (!v_host || !J_host || !g_host) return set_error(FE_EINVAL, "null argument");
   DeviceGuard g(c->device);
   const size_t n = (size_t)c->nn * c->d;
-  if (!c->stage_v && ((st = dev_alloc(c, &c->stage_v, n)) || (st = dev_alloc(c, &c->stage_g, n))))
+  // Page-locked buffers are read (v, by the node preparation) and written (g, by the patch
+  // gather) by the kernels directly over the host link; pageable ones are staged through
+  // device buffers with one copy each way.
+  const double* vin = static_cast<const double*>(mapped_device_ptr(v_host));
+  double* gout = static_cast<double*>(mapped_device_ptr(g_host));
+  if ((!vin || !gout) && !c->stage_v && ((st = dev_alloc(c, &c->stage_v, n)) || (st = dev_alloc(c, &c->stage_g, n))))
     return st;
-  cudaMemcpyAsync(c->stage_v, v_host, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
-  if ((st = eval(c, c->stage_v, c->stage_J, nullptr, c->stage_g, true, true))) return st;
+  if (!vin) {
+    cudaMemcpyAsync(c->stage_v, v_host, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+    vin = c->stage_v;
+  }
+  if ((st = eval(c, vin, c->stage_J, nullptr, gout ? gout : c->stage_g, true, true))) return st;
   cudaMemcpyAsync(J_host, c->stage_J, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-  cudaMemcpyAsync(g_host, c->stage_g, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+  if (!gout) cudaMemcpyAsync(g_host, c->stage_g, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
   return fe_sync_status(c);
 }
 

@@ -71,14 +71,15 @@ __device__ __forceinline__ void finish_energy(double block_total, double* partia
 
 // ---- phi(x) = x - log(1 + x), x > -1 --------------------------------------------------------
 //
-// Breakpoints c_j = (j - FE_PHI_J0) / 256 with F_j = 1 + c_j; inside
-// [-76.5/256, 108.5/256) the nearest breakpoint gives x = c_j + f with |f| <= 1/512 (exact:
-// c_j is a multiple of 2^-8 within a factor 2 of x, Sterbenz' lemma), and with r = f / F_j
+// Breakpoints c_j = (j - FE_PHI_J0) / 256 with F_j = 1 + c_j (the table covers
+// [-76.5/256, 108.5/256); the kernels use it for |x| < 76.5/256): the nearest breakpoint
+// gives x = c_j + f with |f| <= 1/512 (exact: c_j is a multiple of 2^-8 within a factor 2
+// of x, Sterbenz' lemma), and with r = f / F_j
 //   phi(x) = (c_j - ln F_j) + f (1 - 1/F_j) + (r - log1p(r)),
-//   r - log1p(r) = r^2 (1/2 - r/3 + r^2/4 - r^3/5 + r^4/6 - r^5/7 + r^6/8) + O(r^10),
+//   r - log1p(r) = r^2 (1/2 - r/3 + r^2/4 - r^3/5 + r^4/6 - r^5/7 + r^6/8) + O(r^9),
 // |r| < 2.8e-3, so the truncation is below 2^-53 of the last term.  The three terms never
 // cancel by more than about a factor 4, the table holds c_j - ln F_j to twice double
-// precision (hi + lo), and there is no division.  Outside the interval: x - log1p(x).
+// precision (hi + lo), and there is no division.  Outside: x - log1p(x).
 #include "phi_table_f64.h"
 
 struct __align__(32) PhiRow {
@@ -88,19 +89,35 @@ __device__ const PhiRow kPhiTab[FE_PHI_N] = {FE_PHI_TABLE_ROWS};
 
 __device__ __noinline__ double phi_f64_wide(double x) { return x - log1p(x); }
 
-__device__ __forceinline__ double phi_f64(double x) {
-  constexpr double kLo = -(FE_PHI_J0 + 0.5) / FE_PHI_SCALE;
-  constexpr double kHi = (FE_PHI_N - FE_PHI_J0 - 0.5) / FE_PHI_SCALE;
-  if (!(x >= kLo && x < kHi)) return phi_f64_wide(x);
+// |x| < 76.5/256 by the bit pattern (an integer compare; NaN fails it): the symmetric part of
+// the table interval, the rest of it goes to log1p
+__device__ __forceinline__ bool in_phi_table(double x) {
+  constexpr long long kAbs = 0x3FD3200000000000LL;   // bits of 76.5/256 = 0.298828125
+  return (__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL) < kAbs;
+}
+
+// Row j of the table, f = x - c_j (exact) and r = f / F_j for x inside it.
+struct PhiArg {
+  double2 A, BR;
+  double f, r;
+};
+
+__device__ __forceinline__ PhiArg phi_arg(double x) {
   // round(256 x) by the 1.5 * 2^52 shift: t = 1.5 * 2^52 + round(256 x) exactly
   const double t = fma(x, (double)FE_PHI_SCALE, 0x1.8p52);
-  const double c = (t - 0x1.8p52) * (1.0 / FE_PHI_SCALE);
   int j = __double2loint(t) + FE_PHI_J0;
   j = min(max(j, 0), FE_PHI_N - 1);
   const double2* row = reinterpret_cast<const double2*>(kPhiTab + j);
-  const double2 A = __ldg(row), BR = __ldg(row + 1);
-  const double f = x - c;
-  const double r = f * BR.y;
+  PhiArg a;
+  a.A = __ldg(row);
+  a.BR = __ldg(row + 1);
+  a.f = fma(t - 0x1.8p52, -1.0 / FE_PHI_SCALE, x);   // x - c_j, exact (product and sum)
+  a.r = a.f * a.BR.y;
+  return a;
+}
+
+__device__ __forceinline__ double phi_from(const PhiArg& a) {
+  const double r = a.r;
   double p = 1.0 / 8.0;
   p = fma(p, r, -1.0 / 7.0);
   p = fma(p, r, 1.0 / 6.0);
@@ -109,7 +126,39 @@ __device__ __forceinline__ double phi_f64(double x) {
   p = fma(p, r, -1.0 / 3.0);
   p = fma(p, r, 1.0 / 2.0);
   const double psi = (r * r) * p;
-  return A.x + (A.y + fma(f, BR.x, psi));
+  return a.A.x + (a.A.y + fma(a.f, a.BR.x, psi));
+}
+
+__device__ __forceinline__ double phi_f64(double x) {
+  if (!in_phi_table(x)) return phi_f64_wide(x);
+  return phi_from(phi_arg(x));
+}
+
+// 1/(1 + x) from the same row: inside the table 1 + x = F_j (1 + r), so
+// 1/(1 + x) = (1/F_j)(1 - r + r^2 - ... + r^6) (|r| < 2.8e-3: the next term is below
+// 2^-58 of the sum), which replaces a division.
+__device__ __forceinline__ double rcp_from(const PhiArg& a) {
+  const double r = a.r;
+  double s = 1.0 - r;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) s = fma(-r, s, 1.0);
+  return a.BR.y * s;
+}
+
+__device__ __forceinline__ double rcp1p_f64(double x) {
+  if (!in_phi_table(x)) return 1.0 / (1.0 + x);
+  return rcp_from(phi_arg(x));
+}
+
+// phi(x) and 1/(1 + x) together (the reciprocal bitwise equal to rcp1p_f64's).
+__device__ __forceinline__ double phi_rcp_f64(double x, double* rcp) {
+  if (!in_phi_table(x)) {
+    *rcp = 1.0 / (1.0 + x);
+    return phi_f64_wide(x);
+  }
+  const PhiArg a = phi_arg(x);
+  *rcp = rcp_from(a);
+  return phi_from(a);
 }
 
 // Compressible Neo-Hookean density (eq. neoHook) at F = I + H in displacement form:
@@ -318,20 +367,24 @@ __global__ void __launch_bounds__(kThreads) k_elem_f64(
       }
       const double delta = tr + q;
       const double det = 1.0 + delta;
+      double rdet = 0.0;   // 1 / det F
       if (!(det > 0.0)) {
         bad = true;
         W = CUDART_INF;
       } else if (ENERGY || DENS) {
-        W = mp.C1 * (hsq - 2.0 * q + 2.0 * phi_f64(delta)) + mp.D1 * delta * delta;
+        const double ph = GRAD ? phi_rcp_f64(delta, &rdet) : phi_f64(delta);
+        W = mp.C1 * (hsq - 2.0 * q + 2.0 * ph) + mp.D1 * delta * delta;
       }
+      if (GRAD && !(ENERGY || DENS)) rdet = rcp1p_f64(delta);
       if (GRAD) {
         // dW/dF = 2 C1 F + (2 D1 delta - 2 C1 / det F) cof F.  Near F = I its two terms cancel
         // to O(|H|), leaving a relative error of about u / |H|; a warp with any |H|^2 < 1e-4
         // uses instead the same value as
         //   2 C1 (H - L) + 2 delta (D1 + C1 / det F) cof F,   L = cof F - I,
         // whose diagonal L_jj is formed from H without the 1 (no O(1) term left).
-        const double a = 2.0 * mp.C1 * vT;
-        if (__any_sync(__activemask(), hsq < 1e-4)) {
+        const double a = mp.twoC1 * vT;
+        // hsq < 1e-4 by the bit pattern (hsq >= 0): an integer compare
+        if (__any_sync(__activemask(), __double_as_longlong(hsq) < 0x3F1A36E2EB1C432DLL)) {
           Mat64<DIM> h, cf;
 #pragma unroll
           for (int j = 0; j < DIM; ++j)
@@ -346,7 +399,7 @@ __global__ void __launch_bounds__(kThreads) k_elem_f64(
 #pragma unroll
             for (int m = 0; m < DIM; ++m) P[j][m] = p.m[j][m];
         } else {
-          const double c = vT * (2.0 * mp.D1 * delta - 2.0 * mp.C1 / det);
+          const double c = vT * fma(mp.twoD1, delta, -mp.twoC1 * rdet);
 #pragma unroll
           for (int j = 0; j < D; ++j)
 #pragma unroll
@@ -675,6 +728,8 @@ ModelParams model_params(const fe_ctx* c) {
   mp.p = c->p;
   mp.C1 = c->C1;
   mp.D1 = c->D1;
+  mp.twoC1 = 2.0 * c->C1;
+  mp.twoD1 = 2.0 * c->D1;
   mp.pcase = (c->p == 2.0) ? 2 : (c->p == 3.0) ? 3 : 0;
   return mp;
 }

@@ -29,6 +29,7 @@ constexpr int kStatusTimeout = 4;     // a bounded device wait gave up
 // Model parameters passed by value to the element kernels.
 struct ModelParams {
   double p, C1, D1;
+  double twoC1, twoD1;   // 2 C1 and 2 D1
   int pcase;  // p-Laplacian: 2 -> p == 2, 3 -> p == 3, 0 -> general pow
 };
 

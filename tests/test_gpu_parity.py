@@ -451,11 +451,20 @@ def test_fp32_compensated_error(maker, jtol, gtol):
 # end-to-end host call
 # ----------------------------------------------------------------------------------------
 
-def test_host_call_matches_device_call():
+@pytest.mark.parametrize("pinned", [False, True], ids=["pageable", "pinned"])
+@pytest.mark.parametrize("precision", [0, 2], ids=["f64", "df64"])
+def test_host_call_matches_device_call(pinned, precision):
+    """fe_energy_gradient_host (staged copies for pageable buffers; kernels reading v and
+    writing g in page-locked host memory directly) gives bitwise the device call's J and g."""
     w = mg.neohooke_cube3d(16)
-    gm = _gpu(w)
+    gm = _gpu(w, precisions=(precision,))
     J, g = gm.energy_gradient(_v(w))
-    Jh, gh, st = gm.energy_gradient_host(w.v)
+    if pinned:
+        vt = torch.from_numpy(w.v).pin_memory()
+        gt = torch.zeros(w.ndof, dtype=torch.float64).pin_memory()
+        Jh, gh, st = gm.energy_gradient_host(vt.numpy(), gt.numpy())
+    else:
+        Jh, gh, st = gm.energy_gradient_host(w.v)
     assert st == 0
     assert Jh == J.item()
     np.testing.assert_array_equal(gh, g.cpu().numpy())
