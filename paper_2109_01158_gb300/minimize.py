@@ -344,6 +344,40 @@ def newton_cg(ev, hvp, v0: torch.Tensor, *, gtol: float = 1e-6, relative: bool =
     return NewtonResult(v, J, gn, it, evals, hvps, gn <= tol, time.perf_counter() - t0, hist)
 
 
+def _rotate_yz(v, angle):
+    """Rotate the (y, z) components of every node of v by its angle (the map of eq.
+    (displacement) composed with v)."""
+    V = v.reshape(-1, 3)
+    c, s = torch.cos(angle), torch.sin(angle)
+    out = V.clone()
+    out[:, 1] = c * V[:, 1] + s * V[:, 2]
+    out[:, 2] = -s * V[:, 1] + c * V[:, 2]
+    return out.reshape(-1)
+
+
+def torsion_continuation(ev, hvp, coords, dirichlet, *, lx=0.4, T=24, alpha_max=8.0 * math.pi,
+                         gtol=1e-9, relative=True, max_iter=1000):
+    """Benchmark 4's sequence of minimisations: the bar's right face (x = lx) rotated about the
+    x axis by alpha(t) = alpha_max t / T, the left face fixed, t = 1..T, each problem started
+    from the previous minimiser (trust-region Newton-CG on the kernels).  The start of step 1
+    is the twist of eq. (displacement) with alpha(1); the start of step t > 1 is the previous
+    minimiser rotated by the increment alpha_max/T * x/lx (the face values then are exactly
+    those of alpha(t)).  Yields (t, NewtonResult).  coords, dirichlet: the mesh's (n, 3) node
+    coordinates and per-dof Dirichlet mask, as tensors on the evaluators' device."""
+    x = coords[:, 0]
+    X = coords.reshape(-1)
+    fixed = dirichlet.reshape(-1) != 0
+    v = _rotate_yz(X, alpha_max / T * x / lx)
+    for t in range(1, T + 1):
+        if t > 1:
+            v = _rotate_yz(v, alpha_max / T * x / lx)
+            exact = _rotate_yz(X, alpha_max * t / T * x / lx)
+            v = torch.where(fixed, exact, v)
+        r = newton_cg(ev, hvp, v, gtol=gtol, relative=relative, max_iter=max_iter)
+        v = r.v
+        yield t, r
+
+
 def mesh_hvp(mesh):
     """hvp(v, w) -> Hw with the library's FP64 Hessian-vector kernel."""
     def hvp(v, w):

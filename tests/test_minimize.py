@@ -12,7 +12,8 @@ import oracle
 from paper_2109_01158_gb300 import meshgen as mg
 
 torch = pytest.importorskip("torch")
-from paper_2109_01158_gb300.minimize import lbfgs, lbfgs_batched, newton_cg  # noqa: E402
+from paper_2109_01158_gb300.minimize import lbfgs, lbfgs_batched, newton_cg, torsion_continuation  # noqa: E402
+from conftest import read_golden  # noqa: E402
 
 
 def _oracle_ev(om):
@@ -106,6 +107,33 @@ def test_newton_cg_lshape_matches_lbfgs(p):
     assert abs(res.J - (1.0 / p - 1.0) * float(om.b @ res.v.numpy())) <= 1e-8 * abs(res.J)
 
 
+def _torsion_rows(level):
+    return {int(r["t"]): r["J"] for r in read_golden("benchmark4_torsion.txt") if int(r["level"]) == level}
+
+
+def _check_torsion(J, paper):
+    """Our minimum is at most the printed one (which is rounded to 4 decimals and comes from a
+    trust-region run stopped at its own tolerance), and within 3e-4 of it."""
+    assert J <= paper + 5e-5, (J, paper)
+    assert J >= paper * (1.0 - 3e-4), (J, paper)
+
+
+def test_torsion_continuation_first_steps_level1():
+    """Benchmark 4 at level 1 (2133 free dofs), oracle-driven: the first three steps of the
+    continuation reach the printed minimal energy of t = 3."""
+    w = mg.twisted_bar(1)
+    om = oracle.OracleMesh(w)
+    coords = torch.from_numpy(w.coords)
+    dirichlet = torch.from_numpy(w.dirichlet.astype(np.int64))
+    last = None
+    for t, r in torsion_continuation(_oracle_ev(om), _oracle_hvp(om), coords, dirichlet, T=24):
+        assert r.converged
+        last = r
+        if t == 3:
+            break
+    _check_torsion(last.J, _torsion_rows(1)[3])
+
+
 # ---------------------------------------------------------------------------------------
 # GPU
 # ---------------------------------------------------------------------------------------
@@ -197,3 +225,20 @@ def test_gpu_newton_cg_matches_oracle_driven_and_lbfgs():
     lb = lbfgs(minimize.mesh_evaluator(g3), u0, gtol=1e-8, relative=True)
     assert nt.converged and lb.converged and nt.iters < lb.iters / 10
     assert abs(nt.J - lb.J) <= 1e-13 * abs(lb.J)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("level", [1, 2])
+def test_gpu_torsion_continuation_reproduces_benchmark4(level):
+    """Benchmark 4 on the FP64 kernels (energy, gradient, Hessian-vector products): all 24 steps
+    of the continuation, every printed minimal energy of the table (t = 3, 6, ..., 24)."""
+    fem, minimize = _gpu()
+    w = mg.twisted_bar(level)
+    gm = fem.FEMesh.from_workload(w)
+    coords = torch.from_numpy(w.coords).cuda()
+    dirichlet = torch.from_numpy(w.dirichlet.astype(np.int64)).cuda()
+    rows = _torsion_rows(level)
+    for t, r in torsion_continuation(minimize.mesh_evaluator(gm), minimize.mesh_hvp(gm), coords, dirichlet):
+        assert r.converged, (t, r.iters)
+        if t in rows:
+            _check_torsion(r.J, rows[t])
