@@ -458,8 +458,8 @@ def run_minimize(args, device):
     import torch
     from paper_2109_01158_gb300 import fem
     from paper_2109_01158_gb300 import meshgen as mg
-    from paper_2109_01158_gb300.minimize import (batch_evaluator, lbfgs, lbfgs_batched, mesh_evaluator, mesh_hvp,
-                                                 newton_cg)
+    from paper_2109_01158_gb300.minimize import (batch_evaluator, lbfgs, lbfgs_batched, mesh_cg, mesh_evaluator,
+                                                 mesh_hvp, newton_cg, torsion_continuation)
     n = args.minimize_n
     dev = torch.device("cuda", device)
 
@@ -482,9 +482,9 @@ def run_minimize(args, device):
         r = lbfgs(mesh_evaluator(gm, grad, eps=1e-6), v0, gtol=1e-6, relative=True, max_iter=args.minimize_iters)
         out["runs"][name] = {"J": r.J, "iters": r.iters, "evals": r.evals, "converged": r.converged,
                              "seconds": r.seconds, "gnorm": r.gnorm, "g0": r.history[0][1]}
-    # trust-region Newton-CG on the FP64 Hessian-vector products
+    # trust-region Newton-CG on the FP64 Hessian-vector products (device-resident inner CG)
     gm.set_precision(fem.FE_F64)
-    r = newton_cg(mesh_evaluator(gm), mesh_hvp(gm), v0, gtol=1e-6, relative=True)
+    r = newton_cg(mesh_evaluator(gm), mesh_hvp(gm), v0, gtol=1e-6, relative=True, cg=mesh_cg(gm))
     out["runs"]["f64_newton_cg"] = {"J": r.J, "iters": r.iters, "evals": r.evals, "hessian_vector_products": r.hvps,
                                     "converged": r.converged, "seconds": r.seconds, "gnorm": r.gnorm,
                                     "g0": r.history[0][1]}
@@ -502,6 +502,37 @@ def run_minimize(args, device):
     rs = lbfgs_batched(batch_evaluator(batch, meshes, device),
                        [torch.zeros(wk.ndof, dtype=torch.float64, device=dev) for wk in ws],
                        gtol=1e-6, relative=True, max_iter=args.minimize_iters)
+    # Benchmark 4: the torsion continuation (24 minimisations) on the level-3 bar, FP64
+    # kernels with trust-region Newton-CG, against the minimal energies the paper prints
+    paper3 = {3: 1.4631, 6: 5.8533, 9: 13.1735, 12: 23.4286, 15: 36.6236, 18: 52.7641, 21: 71.7883, 24: 93.7238}
+    wb = mg.twisted_bar(3)
+    gb = fem.FEMesh.from_workload(wb, device=device)
+    tors = {"workload": f"Benchmark 4 torsion, bar level 3 ({wb.ne} tets, "
+                        f"{int((wb.dirichlet == 0).sum())} free dofs), t = 1..24, alpha = 8 pi t / 24",
+            "steps": []}
+    t_start = time.perf_counter()
+    for t, r in torsion_continuation(mesh_evaluator(gb), mesh_hvp(gb), torch.from_numpy(wb.coords).to(dev),
+                                     torch.from_numpy(wb.dirichlet.astype(np.int64)).to(dev), cg=mesh_cg(gb)):
+        rec = {"t": t, "J": r.J, "iters": r.iters, "hessian_vector_products": r.hvps, "converged": r.converged,
+               "seconds": r.seconds}
+        if t in paper3:
+            rec["J_paper"] = paper3[t]
+        tors["steps"].append(rec)
+    tors["seconds"] = time.perf_counter() - t_start
+    out["torsion_benchmark4_level3"] = tors
+    # Benchmark 6: the L-shape p-Laplacian (p = 3, f = -10) at level 8 (784,385 free dofs),
+    # componentwise density (the reading of the printed minima), FP64 Newton-CG from v = 0
+    lc, le, lb = mg.lshape_tri(8)
+    wl = mg.Workload("lshape8", 2, 1, lc, le, lb.astype(np.uint8), mg.MODEL_PLAPLACE_LP, p=3.0,
+                     f=np.full(lc.shape[0], -10.0), v=np.zeros(lc.shape[0]))
+    gl = fem.FEMesh.from_workload(wl, device=device)
+    r = newton_cg(mesh_evaluator(gl), mesh_hvp(gl), torch.zeros(wl.nn, dtype=torch.float64, device=dev),
+                  gtol=1e-10, max_iter=5000, cg=mesh_cg(gl))
+    out["lshape_benchmark6_level8"] = {
+        "workload": f"Benchmark 6 L-shape level 8 ({wl.ne} triangles, {int((wl.dirichlet == 0).sum())} free dofs)",
+        "J": r.J, "J_paper": -8.1649, "iters": r.iters, "hessian_vector_products": r.hvps,
+        "converged": r.converged, "seconds": r.seconds,
+        "paper": "617.92 s, 22 trust-region iterations (exact gradient; MATLAB on an M1)"}
     out[f"lockstep_8x{nl}^3x6"] = {"seconds": rs[0].seconds, "iters": [r.iters for r in rs],
                                    "evals": [r.evals for r in rs],
                                    "converged": all(r.converged for r in rs), "J": [r.J for r in rs]}

@@ -49,7 +49,12 @@ typedef enum {
     FE_EBUSY = 6     /* resource in use                                                */
 } fe_status;
 
-typedef enum { FE_PLAPLACE = 0, FE_NEOHOOKE = 1 } fe_model;
+/* FE_PLAPLACE: W = (1/p) |grad v|^p with the Euclidean norm, (1/p)(|grad v|^2)^(p/2).
+ * FE_PLAPLACE_LP: W = (1/p) sum_m |dv/dx_m|^p, the same eq. pLaplacian read with the l^p norm
+ * of the gradient (the two agree for p = 2); the minimal energies printed in the table of
+ * Benchmark 6 are those of this reading.  Evaluated in FP64 only (not by the FE_DF64,
+ * FE_F32_COMP, batched or no-allocation calls, which return FE_EINVAL for it). */
+typedef enum { FE_PLAPLACE = 0, FE_NEOHOOKE = 1, FE_PLAPLACE_LP = 2 } fe_model;
 
 /* Arithmetic of the element kernels (none is prescribed by the paper, which runs MATLAB
  * doubles).  FE_F64: IEEE double throughout.  FE_F32_COMP: per-element float arithmetic in
@@ -104,7 +109,8 @@ fe_status fe_mesh_upload(fe_ctx* ctx, int dim, int d, int64_t n_nodes,
                          const int32_t* elems_host, const uint8_t* dirichlet_host,
                          int order);
 
-/* Select the density: FE_PLAPLACE with exponent p > 1 (eq. pLaplacian; requires d = 1),
+/* Select the density: FE_PLAPLACE or FE_PLAPLACE_LP with exponent p > 1 (eq. pLaplacian;
+ * requires d = 1),
  * or FE_NEOHOOKE with constants C1, D1 (eq. neoHook; requires d = dim).  For material
  * data, C1 = mu/2 and D1 = K/2 with mu = E/(2(1+nu)), K = E/(3(1-2nu)) (Benchmark 2). */
 fe_status fe_set_model(fe_ctx* ctx, int model, double p, double C1, double D1);
@@ -160,6 +166,28 @@ fe_status fe_energy_gradient(fe_ctx* ctx, const double* v_dev, double* J_dev, do
  * evaluated in FP64 (needs the FP64 precompute).  Neo-Hookean with some det F <= 0:
  * fe_sync_status returns FE_EDOMAIN. */
 fe_status fe_hessian_vector(fe_ctx* ctx, const double* v_dev, const double* w_dev, double* Hw_dev);
+
+/* Steihaug's truncated conjugate gradients (Nocedal & Wright, Alg. 7.2; not in the paper, the
+ * inner solver of a trust-region Newton method like the one the paper minimises with, Sec. 7):
+ * from z = 0, approximately minimises m(z) = g.z + z.H z / 2 over ||z||_2 <= radius, where H
+ * is the Hessian of J at v on the free dofs (the product of fe_hessian_vector, FP64).  Stops
+ * at the first of: ||g + H z||_2 <= tol; a direction d with d.H d <= 0, or a step that would
+ * leave the ball (in both cases z moves along d to the boundary); max_cg products.
+ *   v_dev      n_nodes*d doubles (device, caller's dof order): the point, as set by fe_set_input
+ *   g_dev      n_nodes*d doubles (device): the gradient at v, 0 on Dirichlet dofs (as
+ *              fe_gradient_exact returns it); not modified
+ *   radius     > 0 and finite; tol >= 0 and finite; max_cg >= 0
+ *   z_dev      n_nodes*d doubles (device, written): the step (0 on Dirichlet dofs)
+ *   Hz_dev     n_nodes*d doubles (device, written): H z
+ *   iters      host int (written): Hessian-vector products used; 0 when ||g|| <= tol already
+ *   boundary   host int (written): 1 when z ended on the boundary, else 0
+ * All vector work runs on the device (the dot products are fixed-order reductions, so the
+ * results are bitwise reproducible); the call returns when the solve has finished.  Needs the
+ * FP64 precompute; the first call allocates 3 vectors of n_nodes*d doubles of work space.
+ * FE_EINVAL for a bad argument; Neo-Hookean with some det F <= 0 at v: fe_sync_status returns
+ * FE_EDOMAIN and z is unspecified. */
+fe_status fe_cg_steihaug(fe_ctx* ctx, const double* v_dev, const double* g_dev, double radius, double tol,
+                         int max_cg, double* z_dev, double* Hz_dev, int* iters, int* boundary);
 
 /* Central-difference gradient over nodal patches (Sec. 6.1, eqs. CD, CDS, jgradpm,
  * sumpatch): for dof n of node i, component j,

@@ -107,6 +107,7 @@ void free_precompute(fe_ctx* c) {
   dev_free(c, &c->r32, ne * k * c->d);
   dev_free(c, &c->stage_v, nn * c->d);
   dev_free(c, &c->stage_g, nn * c->d);
+  dev_free(c, &c->cg_vec, 3 * nn * c->d);
   c->have_pre = false;
   c->pre_mask = 0;
 }
@@ -171,6 +172,8 @@ fe_status check_ready(fe_ctx* c, bool need_model = true) {
 
 fe_status eval(fe_ctx* c, const double* v, double* J, double* dens, double* g, bool want_energy,
                bool want_grad) {
+  if (c->model == FE_PLAPLACE_LP && c->precision != FE_F64)
+    return set_error(FE_EINVAL, "the componentwise p-Laplacian is evaluated in FP64 only");
   if (c->precision == FE_F32_COMP) return launch_eval_f32(c, v, J, dens, g, want_energy, want_grad);
   if (c->precision == FE_DF64) return launch_eval_df64(c, v, J, dens, g, want_energy, want_grad);
   return launch_eval_f64(c, v, J, dens, g, want_energy, want_grad);
@@ -230,6 +233,10 @@ fe_status fe_destroy(fe_ctx* c) {
   dev_free(c, &c->counter, 1);
   dev_free(c, &c->status, 1);
   dev_free(c, &c->stage_J, 1);
+  dev_free(c, &c->cg_part, 2 * kMaxNodeBlocks);
+  dev_free(c, &c->cg_ticket, 1);
+  dev_free(c, &c->cg_state, 1);
+  if (c->cg_host) cudaFreeHost(c->cg_host);
   delete c;
   return FE_OK;
 }
@@ -333,7 +340,7 @@ fe_status fe_mesh_upload(fe_ctx* c, int dim, int d, int64_t nn, const double* co
 fe_status fe_set_model(fe_ctx* c, int model, double p, double C1, double D1) {
   if (!c) return set_error(FE_EINVAL, "null context");
   if (!c->have_mesh) return set_error(FE_EINVAL, "upload the mesh before the model");
-  if (model == FE_PLAPLACE) {
+  if (model == FE_PLAPLACE || model == FE_PLAPLACE_LP) {
     if (c->d != 1) return set_error(FE_EINVAL, "the p-Laplacian needs d = 1");
     if (!(p > 1.0) || !std::isfinite(p)) return set_error(FE_EINVAL, "p must be > 1");
   } else if (model == FE_NEOHOOKE) {
@@ -487,6 +494,33 @@ fe_status fe_hessian_vector(fe_ctx* c, const double* v, const double* w, double*
   DeviceGuard g(c->device);
   if (!c->w_hvp && (st = dev_alloc(c, &c->w_hvp, (size_t)c->nn * padded_d(c->d)))) return st;
   return launch_hvp_f64(c, v, w, Hw);
+}
+
+fe_status fe_cg_steihaug(fe_ctx* c, const double* v, const double* g, double radius, double tol, int max_cg,
+                         double* z, double* Hz, int* iters, int* boundary) {
+  fe_status st = check_ready(c);
+  if (st) return st;
+  if (!v || !g || !z || !Hz || !iters || !boundary) return set_error(FE_EINVAL, "null argument");
+  if (!(radius > 0.0) || !std::isfinite(radius)) return set_error(FE_EINVAL, "radius must be finite and > 0");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return set_error(FE_EINVAL, "tol must be finite and >= 0");
+  if (max_cg < 0) return set_error(FE_EINVAL, "negative max_cg");
+  if (!(c->pre_mask & (1u << FE_F64)))
+    return set_error(FE_EINVAL, "the Hessian-vector product needs the FP64 precompute");
+  DeviceGuard dg(c->device);
+  const size_t n = (size_t)c->nn * c->d;
+  if (!c->w_hvp && (st = dev_alloc(c, &c->w_hvp, (size_t)c->nn * padded_d(c->d)))) return st;
+  if (!c->cg_vec && (st = dev_alloc(c, &c->cg_vec, 3 * n))) return st;
+  if (!c->cg_part && (st = dev_alloc(c, &c->cg_part, 2 * kMaxNodeBlocks))) return st;
+  if (!c->cg_ticket) {
+    if ((st = dev_alloc(c, &c->cg_ticket, 1))) return st;
+    if ((st = cuda_check(cudaMemsetAsync(c->cg_ticket, 0, sizeof(unsigned), c->stream), "cg ticket"))) return st;
+  }
+  if (!c->cg_state && (st = dev_alloc(c, &c->cg_state, 1))) return st;
+  if (!c->cg_host && (st = cuda_check(cudaMallocHost((void**)&c->cg_host, sizeof(CgState)), "cg host state"))) {
+    c->cg_host = nullptr;
+    return st;
+  }
+  return launch_cg_steihaug(c, v, g, radius, tol, max_cg, z, Hz, iters, boundary);
 }
 
 fe_status fe_gradient_fd(fe_ctx* c, const double* v, double eps, double* gout, const int64_t* dofs,

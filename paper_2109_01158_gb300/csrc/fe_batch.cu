@@ -239,6 +239,8 @@ fe_status batch_enqueue(cudaStream_t s, const fe_batch_item* items, int n, void*
     const fe_ctx* m = q.mesh;
     if (!m || !m->have_pre || !m->model_set || !(m->pre_mask & (1u << FE_DF64)))
       return set_error(FE_EINVAL, "batch item: mesh must be precomputed with FE_DF64 and have a model");
+    if (m->model != FE_PLAPLACE && m->model != FE_NEOHOOKE)
+      return set_error(FE_EINVAL, "batch item: the batched kernels evaluate FE_PLAPLACE and FE_NEOHOOKE");
     if (!q.v || !q.J || !q.g || !q.work) return set_error(FE_EINVAL, "batch item: null v, J, g or work");
     if (reinterpret_cast<uintptr_t>(q.work) & 255u) return set_error(FE_EINVAL, "batch item: work not 256-byte aligned");
     const WorkLayout L = work_layout(m);

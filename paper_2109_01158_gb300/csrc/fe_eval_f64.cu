@@ -199,6 +199,23 @@ __device__ __forceinline__ double plap_density(double s, const ModelParams& mp) 
   return s > 0.0 ? pow(s, 0.5 * mp.p) / mp.p : 0.0;
 }
 
+// Componentwise p-Laplacian (FE_PLAPLACE_LP): |a|^p and |a|^(p-2) of one gradient component.
+__device__ __forceinline__ void plap_lp_terms(double a, const ModelParams& mp, double* ap, double* ap2) {
+  const double x = fabs(a);
+  if (mp.pcase == 2) {
+    *ap = x * x;
+    *ap2 = 1.0;
+  } else if (mp.pcase == 3) {
+    *ap = x * x * x;
+    *ap2 = x;
+  } else if (x > 0.0) {
+    *ap2 = pow(x, mp.p - 2.0);
+    *ap = *ap2 * x * x;
+  } else {
+    *ap = *ap2 = 0.0;
+  }
+}
+
 __device__ __forceinline__ double plap_coef(double s, const ModelParams& mp) {
   if (mp.pcase == 2) return 1.0;
   if (mp.pcase == 3) return sqrt(s);
@@ -406,6 +423,17 @@ __global__ void __launch_bounds__(kThreads) k_elem_f64(
             for (int m = 0; m < DIM; ++m) P[j][m] = fma(a, Fm[j][m], c * Cm[j][m]);
         }
       }
+    } else if constexpr (MODEL == FE_PLAPLACE_LP) {
+      // W = (1/p) sum_m |H_m|^p, dW/dH_m = |H_m|^(p-2) H_m
+      double sp = 0.0;
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) {
+        double ap, ap2;
+        plap_lp_terms(H[0][m], mp, &ap, &ap2);
+        sp += ap;
+        if (GRAD) P[0][m] = vT * ap2 * H[0][m];
+      }
+      if (ENERGY || DENS) W = sp / mp.p;
     } else {
       double s = 0.0;
 #pragma unroll
@@ -475,6 +503,15 @@ __device__ __forceinline__ double fd_density(double ul[DIM + 1][D], const double
 #pragma unroll
       for (int m = 0; m < DIM; ++m) Hx[jj][m] = (jj == j) ? row[m] : H[jj][m];
     return nh_density_disp<DIM>(Hx, mp, bad);
+  } else if constexpr (MODEL == FE_PLAPLACE_LP) {
+    double sp = 0.0;
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) {
+      double ap, ap2;
+      plap_lp_terms(row[m], mp, &ap, &ap2);
+      sp += ap;
+    }
+    return sp / mp.p;
   } else {
     double s = 0.0;
 #pragma unroll
@@ -740,6 +777,10 @@ fe_status launch_eval_f64(fe_ctx* c, const double* v, double* J, double* dens, d
     if (c->dim == 2) return eval_t<2, 2, FE_NEOHOOKE>(c, v, J, dens, g, want_energy, want_grad);
     return eval_t<3, 3, FE_NEOHOOKE>(c, v, J, dens, g, want_energy, want_grad);
   }
+  if (c->model == FE_PLAPLACE_LP) {
+    if (c->dim == 2) return eval_t<2, 1, FE_PLAPLACE_LP>(c, v, J, dens, g, want_energy, want_grad);
+    return eval_t<3, 1, FE_PLAPLACE_LP>(c, v, J, dens, g, want_energy, want_grad);
+  }
   if (c->dim == 2) return eval_t<2, 1, FE_PLAPLACE>(c, v, J, dens, g, want_energy, want_grad);
   return eval_t<3, 1, FE_PLAPLACE>(c, v, J, dens, g, want_energy, want_grad);
 }
@@ -783,6 +824,9 @@ fe_status launch_fd_f64(fe_ctx* c, const double* v, double eps, double* g, const
   if (c->model == FE_NEOHOOKE)
     st = (c->dim == 2) ? fd_t<2, 2, FE_NEOHOOKE>(c, v, eps, g, dofs, ndofs, rfd, iperm)
                        : fd_t<3, 3, FE_NEOHOOKE>(c, v, eps, g, dofs, ndofs, rfd, iperm);
+  else if (c->model == FE_PLAPLACE_LP)
+    st = (c->dim == 2) ? fd_t<2, 1, FE_PLAPLACE_LP>(c, v, eps, g, dofs, ndofs, rfd, iperm)
+                       : fd_t<3, 1, FE_PLAPLACE_LP>(c, v, eps, g, dofs, ndofs, rfd, iperm);
   else
     st = (c->dim == 2) ? fd_t<2, 1, FE_PLAPLACE>(c, v, eps, g, dofs, ndofs, rfd, iperm)
                        : fd_t<3, 1, FE_PLAPLACE>(c, v, eps, g, dofs, ndofs, rfd, iperm);

@@ -15,7 +15,7 @@
 //   dP = 2 C1 dF + (2 C1 / det^2 + 2 D1) (cof : dF) cof + (2 D1 (det - 1) - 2 C1 / det) d(cof);
 // every term is O(|dF|), so no O(1) terms cancel near F = I.  p-Laplacian, s = |grad v|^2:
 //   dP = s^((p-2)/2) dF + (p - 2) s^((p-4)/2) (grad v . dF) grad v,  dP = dF for p = 2 and
-//   0 at grad v = 0 otherwise.
+//   0 at grad v = 0 otherwise; componentwise p-Laplacian: dP_m = (p - 1) |v_m|^(p-2) dF_m.
 #include "fe_internal.cuh"
 #include "gather_bulk.cuh"
 
@@ -43,8 +43,10 @@ __device__ __forceinline__ void load_vec(const double* __restrict__ u, int32_t n
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_w_prep(int64_t nn, const double* __restrict__ w,
                                                      const int32_t* __restrict__ perm,
-                                                     const uint8_t* __restrict__ dir, double* __restrict__ wd) {
+                                                     const uint8_t* __restrict__ dir, double* __restrict__ wd,
+                                                     const int* skip) {
   constexpr int DP = D == 3 ? 4 : D;
+  if (skip && *skip) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
     const int64_t src = perm ? (int64_t)perm[i] : i;
@@ -62,8 +64,9 @@ __global__ void __launch_bounds__(kThreads) k_hvp_f64(int64_t ne, const int32_t*
                                                       const double* __restrict__ dphi, const double* __restrict__ vol,
                                                       const double* __restrict__ u, const double* __restrict__ wd,
                                                       const int32_t* __restrict__ slot, ModelParams mp,
-                                                      double* __restrict__ r, int* status) {
+                                                      double* __restrict__ r, int* status, const int* skip) {
   constexpr int K = DIM + 1;
+  if (skip && *skip) return;
   bool bad = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
@@ -154,6 +157,17 @@ __global__ void __launch_bounds__(kThreads) k_hvp_f64(int64_t ne, const int32_t*
       for (int j = 0; j < DIM; ++j)
 #pragma unroll
         for (int m = 0; m < DIM; ++m) dP[j][m] = fma(a, dF[j][m], fma(bcoef, C[j][m], ccoef * dC[j][m]));
+    } else if constexpr (MODEL == FE_PLAPLACE_LP) {
+      // dP_m = (p - 1) |H_m|^(p-2) dF_m (dF_m for p = 2)
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) {
+        const double x = fabs(H[0][m]);
+        double c;
+        if (mp.pcase == 2) c = 1.0;
+        else if (mp.pcase == 3) c = 2.0 * x;
+        else c = (x > 0.0) ? (mp.p - 1.0) * pow(x, mp.p - 2.0) : 0.0;
+        dP[0][m] = vT * c * dF[0][m];
+      }
     } else {
       double s = 0.0, hd = 0.0;
 #pragma unroll
@@ -198,29 +212,37 @@ __global__ void __launch_bounds__(kThreads) k_hvp_f64(int64_t ne, const int32_t*
 }
 
 template <int DIM, int D, int MODEL>
-fe_status hvp_t(fe_ctx* c, const double* v, const double* w, double* Hw) {
+fe_status hvp_dir_t(fe_ctx* c, const double* w, double* Hw, const int* skip) {
   cudaStream_t s = c->stream;
   const ModelParams mp = model_params(c);
-  fe_status st = launch_node_prep_f64(c, v);
-  if (st) return st;
   const int nb_node = grid_for(c->nn, kMaxNodeBlocks);
-  k_w_prep<D><<<nb_node, kThreads, 0, s>>>(c->nn, w, c->perm, c->dir, c->w_hvp);
+  k_w_prep<D><<<nb_node, kThreads, 0, s>>>(c->nn, w, c->perm, c->dir, c->w_hvp, skip);
   c->launches++;
   if (c->ne > 0) {
     k_hvp_f64<DIM, D, MODEL><<<grid_for(c->ne, kMaxElemBlocks), kThreads, 0, s>>>(
-        c->ne, c->elems, c->dphi, c->vol, c->u, c->w_hvp, c->slot, mp, c->r, c->status);
+        c->ne, c->elems, c->dphi, c->vol, c->u, c->w_hvp, c->slot, mp, c->r, c->status, skip);
     c->launches++;
   }
-  if ((st = launch_gather_bulk<D, AccF64>(c, c->r, Hw, nullptr))) return st;
+  fe_status st = launch_gather_bulk<D, AccF64>(c, c->r, Hw, nullptr, skip);
+  if (st) return st;
   c->launches++;
   return cuda_check(cudaGetLastError(), "hessian-vector launch");
 }
 
 }  // namespace
 
+fe_status launch_hvp_dir_f64(fe_ctx* c, const double* w, double* Hw, const int* skip) {
+  if (c->model == FE_NEOHOOKE)
+    return c->dim == 2 ? hvp_dir_t<2, 2, FE_NEOHOOKE>(c, w, Hw, skip) : hvp_dir_t<3, 3, FE_NEOHOOKE>(c, w, Hw, skip);
+  if (c->model == FE_PLAPLACE_LP)
+    return c->dim == 2 ? hvp_dir_t<2, 1, FE_PLAPLACE_LP>(c, w, Hw, skip) : hvp_dir_t<3, 1, FE_PLAPLACE_LP>(c, w, Hw, skip);
+  return c->dim == 2 ? hvp_dir_t<2, 1, FE_PLAPLACE>(c, w, Hw, skip) : hvp_dir_t<3, 1, FE_PLAPLACE>(c, w, Hw, skip);
+}
+
 fe_status launch_hvp_f64(fe_ctx* c, const double* v, const double* w, double* Hw) {
-  if (c->model == FE_NEOHOOKE) return c->dim == 2 ? hvp_t<2, 2, FE_NEOHOOKE>(c, v, w, Hw) : hvp_t<3, 3, FE_NEOHOOKE>(c, v, w, Hw);
-  return c->dim == 2 ? hvp_t<2, 1, FE_PLAPLACE>(c, v, w, Hw) : hvp_t<3, 1, FE_PLAPLACE>(c, v, w, Hw);
+  fe_status st = launch_node_prep_f64(c, v);
+  if (st) return st;
+  return launch_hvp_dir_f64(c, w, Hw, nullptr);
 }
 
 }  // namespace fe

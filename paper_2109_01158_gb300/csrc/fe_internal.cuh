@@ -42,6 +42,20 @@ inline int grid_for(int64_t n, int max_blocks) {
 // Padded stride (in components) of the per-node displacement buffer: 1, 2 or 4.
 inline int padded_d(int d) { return d == 3 ? 4 : d; }
 
+// Scalars of the device-resident conjugate-gradient solver (fe_cg.cu).
+struct CgState {
+  double rr;       // r.r of the current residual
+  double rrn;      // r.r after the last step
+  double dd, zd, zz;  // d.d, z.d, z.z of the current direction and iterate
+  double dHd;      // d.H d
+  double radius2;  // squared trust-region radius
+  double tol;      // stop at ||r|| <= tol
+  int k;           // Hessian-vector products used
+  int done;        // 1 once the solve has stopped
+  int boundary;    // 1 if it stopped on the boundary
+  int max_cg;
+};
+
 }  // namespace fe
 
 // Context: all device buffers are in the internal ("device") numbering.
@@ -97,6 +111,11 @@ struct fe_ctx {
   double* stage_v = nullptr;   // staging for the *_host call
   double* stage_g = nullptr;
   double* stage_J = nullptr;
+  double* cg_vec = nullptr;    // 3*nn*d: residual, direction and H direction of the CG solver
+  double* cg_part = nullptr;   // 2*kMaxNodeBlocks partial sums of the CG solver
+  unsigned* cg_ticket = nullptr;  // last-block ticket of the CG solver
+  fe::CgState* cg_state = nullptr;  // device scalars of the CG solver
+  fe::CgState* cg_host = nullptr;   // page-locked host copy of them
 
   int64_t launches = 0;
   size_t bytes = 0;
@@ -131,6 +150,12 @@ fe_status batch_enqueue(cudaStream_t s, const fe_batch_item* items, int n, void*
 // fe_eval_f64.cu / fe_hessian.cu
 fe_status launch_node_prep_f64(fe_ctx* c, const double* v);
 fe_status launch_hvp_f64(fe_ctx* c, const double* v, const double* w, double* Hw);
+// The product along w at the v last prepared by launch_node_prep_f64 (c->u); does nothing
+// when skip (nullable device flag) is nonzero.
+fe_status launch_hvp_dir_f64(fe_ctx* c, const double* w, double* Hw, const int* skip);
+// fe_cg.cu: Steihaug's CG on the device (buffers cg_* allocated by the caller).
+fe_status launch_cg_steihaug(fe_ctx* c, const double* v, const double* g, double radius, double tol, int max_cg,
+                             double* z, double* Hz, int* iters, int* boundary);
 
 fe_status launch_precompute(fe_ctx* c);
 fe_status launch_load_vector(fe_ctx* c);

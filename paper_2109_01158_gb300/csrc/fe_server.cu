@@ -414,6 +414,8 @@ fe_status fe_server_submit(fe_server* s, const fe_ctx* mesh, const double* v_hos
   if (!mesh->have_pre || !mesh->model_set || !(mesh->pre_mask & (1u << FE_DF64)))
     return set_error(FE_EINVAL, "server request: mesh must be precomputed with FE_DF64 and have a model");
   if (mesh->device != s->device) return set_error(FE_EINVAL, "server request: mesh on another device");
+  if (mesh->model != FE_PLAPLACE && mesh->model != FE_NEOHOOKE)
+    return set_error(FE_EINVAL, "server request: the batched kernels evaluate FE_PLAPLACE and FE_NEOHOOKE");
   Req* r = new (std::nothrow) Req();
   if (!r) return set_error(FE_ENOMEM, "host allocation");
   r->mesh = mesh;

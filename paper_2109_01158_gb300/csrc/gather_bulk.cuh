@@ -55,8 +55,9 @@ template <int D, class Acc>
 __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
     int64_t nn, const int32_t* __restrict__ row_ptr, const typename Acc::T* __restrict__ r,
     const double* __restrict__ b, const uint8_t* __restrict__ dir, const int32_t* __restrict__ perm,
-    double* __restrict__ g, int* status) {
+    double* __restrict__ g, int* status, const int* skip) {
   using T = typename Acc::T;
+  if (skip && *skip) return;  // a solver loop enqueued this launch after it had finished
   extern __shared__ __align__(128) unsigned char gsmem[];
   __shared__ __align__(8) uint64_t bars[kGatherWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -129,8 +130,10 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
 
 // Launch on the context stream: one block of 8 warps per SM (160 KB of shared memory each).
 // b: the load vector subtracted from the sums (the context's b unless given; nullptr = 0).
+// skip: nullptr, or a device flag; the launch does nothing when it is nonzero.
 template <int D, class Acc>
-inline fe_status launch_gather_bulk(fe_ctx* c, const typename Acc::T* r, double* g, const double* b) {
+inline fe_status launch_gather_bulk(fe_ctx* c, const typename Acc::T* r, double* g, const double* b,
+                                    const int* skip = nullptr) {
   static bool configured[64] = {false};
   if (c->device < 0 || c->device >= 64 || !configured[c->device]) {
     cudaError_t e = cudaFuncSetAttribute(k_gather_bulk<D, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -145,7 +148,7 @@ inline fe_status launch_gather_bulk(fe_ctx* c, const typename Acc::T* r, double*
   if (blocks > sms) blocks = sms;
   if (blocks < 1) blocks = 1;
   k_gather_bulk<D, Acc><<<(unsigned)blocks, kGatherWarps * 32, kGatherSmem, c->stream>>>(
-      c->nn, c->row_ptr, r, b, c->dir, c->perm, g, c->status);
+      c->nn, c->row_ptr, r, b, c->dir, c->perm, g, c->status, skip);
   return cuda_check(cudaGetLastError(), "gather launch");
 }
 

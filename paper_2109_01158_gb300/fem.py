@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfemenergy.so")
 
 FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_EDOMAIN, FE_ETIMEOUT, FE_EBUSY = range(7)
-FE_PLAPLACE, FE_NEOHOOKE = 0, 1
+FE_PLAPLACE, FE_NEOHOOKE, FE_PLAPLACE_LP = 0, 1, 2
 FE_F64, FE_F32_COMP, FE_DF64 = 0, 1, 2
 FE_ORDER_NONE, FE_ORDER_MORTON = 0, 1
 FE_INPUT_DEFORMATION, FE_INPUT_DISPLACEMENT = 0, 1
@@ -59,6 +59,7 @@ _SIGNATURES = {
     "fe_energy_gradient": [_vp, _vp, _vp, _vp],
     "fe_gradient_fd": [_vp, _vp, _dbl, _vp, _vp, _i64],
     "fe_hessian_vector": [_vp, _vp, _vp, _vp],
+    "fe_cg_steihaug": [_vp, _vp, _vp, _dbl, _dbl, _int, _vp, _vp, _vp, _vp],
     "fe_energy_gradient_host": [_vp, _vp, _vp, _vp],
     "fe_sync_status": [_vp],
     "fe_get_shape_gradients": [_vp, _vp, _vp],
@@ -145,6 +146,7 @@ fe_gradient_exact = _checked("fe_gradient_exact")
 fe_energy_gradient = _checked("fe_energy_gradient")
 fe_gradient_fd = _checked("fe_gradient_fd")
 fe_hessian_vector = _checked("fe_hessian_vector")
+fe_cg_steihaug = _checked("fe_cg_steihaug")
 fe_energy_gradient_host = _checked("fe_energy_gradient_host")
 fe_get_shape_gradients = _checked("fe_get_shape_gradients")
 fe_get_patches = _checked("fe_get_patches")
@@ -422,6 +424,18 @@ class FEMesh:
         Hw = out if out is not None else torch.empty(self.ndof, dtype=torch.float64, device=self.device)
         fe_hessian_vector(self.ctx, _ptr(v), _ptr(w), _ptr(Hw))
         return Hw
+
+    def cg_steihaug(self, v, g, radius, tol, max_cg, z=None, Hz=None):
+        """Steihaug's truncated CG on the device for min g.z + z.H(v) z / 2, ||z|| <= radius.
+        Returns (z, Hz, iterations, hit_boundary)."""
+        v, g = self._vec(v), self._vec(g)
+        self._sync_stream()
+        z = z if z is not None else torch.empty(self.ndof, dtype=torch.float64, device=self.device)
+        Hz = Hz if Hz is not None else torch.empty(self.ndof, dtype=torch.float64, device=self.device)
+        k, bnd = ctypes.c_int(0), ctypes.c_int(0)
+        fe_cg_steihaug(self.ctx, _ptr(v), _ptr(g), float(radius), float(tol), int(max_cg), _ptr(z), _ptr(Hz),
+                       ctypes.byref(k), ctypes.byref(bnd))
+        return z, Hz, k.value, bool(bnd.value)
 
     def energy_gradient_host(self, v_host, g_host=None):
         """End-to-end call on host buffers (numpy float64; pinned memory is fastest)."""

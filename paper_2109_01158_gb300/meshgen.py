@@ -159,6 +159,7 @@ def lame_c1_d1(E: float, nu: float):
 
 MODEL_PLAPLACE = 0
 MODEL_NEOHOOKE = 1
+MODEL_PLAPLACE_LP = 2   # (1/p) sum_m |dv/dx_m|^p: the l^p-norm reading of |grad v|^p
 
 
 @dataclass

@@ -283,8 +283,8 @@ def _cg_steihaug(g, hv, radius, tol, max_cg):
 
 
 def newton_cg(ev, hvp, v0: torch.Tensor, *, gtol: float = 1e-6, relative: bool = False,
-              max_iter: int = 1000, max_cg: int = 5000, eta_max: float = 0.5,
-              eps_f: float | None = None, radius_max: float = 1e30) -> NewtonResult:
+              max_iter: int = 1000, max_cg: int = 5000, eta_max: float = 0.1,
+              eps_f: float | None = None, radius_max: float = 1e30, cg=None) -> NewtonResult:
     """Trust-region Newton-CG (Nocedal & Wright, Alg. 4.1 with Steihaug's CG), the analogue
     of the trust-region method the paper minimises with (Sec. 7), driven by the kernels'
     Hessian-vector products hvp(v, w) -> Hw.  The inner CG stops at ||r|| <= eta ||g||,
@@ -292,7 +292,8 @@ def newton_cg(ev, hvp, v0: torch.Tensor, *, gtol: float = 1e-6, relative: bool =
     of non-positive curvature (the p-Laplacian's Hessian vanishes where grad v = 0).  The
     first radius is the length of the Cauchy step.  A step is accepted when the ratio of
     actual to predicted decrease exceeds 1e-4, or -- at the rounding level of J -- when J
-    does not rise above it and ||g|| decreases."""
+    does not rise above it and ||g|| decreases.  cg(v, g, radius, tol, max_cg) -> (z, Hz, k,
+    hit_boundary) replaces the Python CG over hvp (e.g. the device solver of mesh_cg)."""
     t0 = time.perf_counter()
     eps_f = _noise(ev, eps_f)
     J, g = ev(v0)
@@ -311,14 +312,18 @@ def newton_cg(ev, hvp, v0: torch.Tensor, *, gtol: float = 1e-6, relative: bool =
     rejected = 0
     while gn > tol and it < max_iter and rejected < 60:
         eta = min(eta_max, math.sqrt(g2 / max(g0_2, 1e-300)))
-        cnt = [0]
+        if cg is not None:
+            z, Hz, k, boundary = cg(v, g, radius, eta * g2, max_cg)
+            hvps += k
+        else:
+            cnt = [0]
 
-        def hv(w):
-            cnt[0] += 1
-            return hvp(v, w)
+            def hv(w):
+                cnt[0] += 1
+                return hvp(v, w)
 
-        z, Hz, k, boundary = _cg_steihaug(g, hv, radius, eta * g2, max_cg)
-        hvps += cnt[0]
+            z, Hz, k, boundary = _cg_steihaug(g, hv, radius, eta * g2, max_cg)
+            hvps += cnt[0]
         pred = -(float(torch.dot(g, z).item()) + 0.5 * float(torch.dot(z, Hz).item()))
         v_new = v + z
         J_new, g_new = ev(v_new)
@@ -356,7 +361,7 @@ def _rotate_yz(v, angle):
 
 
 def torsion_continuation(ev, hvp, coords, dirichlet, *, lx=0.4, T=24, alpha_max=8.0 * math.pi,
-                         gtol=1e-9, relative=True, max_iter=1000):
+                         gtol=1e-9, relative=True, max_iter=1000, cg=None):
     """Benchmark 4's sequence of minimisations: the bar's right face (x = lx) rotated about the
     x axis by alpha(t) = alpha_max t / T, the left face fixed, t = 1..T, each problem started
     from the previous minimiser (trust-region Newton-CG on the kernels).  The start of step 1
@@ -373,7 +378,7 @@ def torsion_continuation(ev, hvp, coords, dirichlet, *, lx=0.4, T=24, alpha_max=
             v = _rotate_yz(v, alpha_max / T * x / lx)
             exact = _rotate_yz(X, alpha_max * t / T * x / lx)
             v = torch.where(fixed, exact, v)
-        r = newton_cg(ev, hvp, v, gtol=gtol, relative=relative, max_iter=max_iter)
+        r = newton_cg(ev, hvp, v, gtol=gtol, relative=relative, max_iter=max_iter, cg=cg)
         v = r.v
         yield t, r
 
@@ -383,6 +388,14 @@ def mesh_hvp(mesh):
     def hvp(v, w):
         return mesh.hessian_vector(v, w)
     return hvp
+
+
+def mesh_cg(mesh):
+    """cg(v, g, radius, tol, max_cg) for newton_cg: the library's device-resident Steihaug CG
+    over the same Hessian-vector kernel."""
+    def cg(v, g, radius, tol, max_cg):
+        return mesh.cg_steihaug(v, g, radius, tol, max_cg)
+    return cg
 
 
 # ----------------------------------------------------------------------------------------

@@ -238,7 +238,8 @@ def test_gpu_torsion_continuation_reproduces_benchmark4(level):
     coords = torch.from_numpy(w.coords).cuda()
     dirichlet = torch.from_numpy(w.dirichlet.astype(np.int64)).cuda()
     rows = _torsion_rows(level)
-    for t, r in torsion_continuation(minimize.mesh_evaluator(gm), minimize.mesh_hvp(gm), coords, dirichlet):
+    for t, r in torsion_continuation(minimize.mesh_evaluator(gm), minimize.mesh_hvp(gm), coords, dirichlet,
+                                     cg=minimize.mesh_cg(gm)):
         assert r.converged, (t, r.iters)
         if t in rows:
             _check_torsion(r.J, rows[t])
