@@ -12,7 +12,9 @@ trial point with det F <= 0 has J = +Inf and is rejected like any point without 
 `lbfgs` runs one minimisation through an evaluator `ev(v) -> (J, g)`; `lbfgs_batched` runs
 many instances in lockstep, evaluating every active instance's trial point in one batched
 launch (fe_batch_energy_gradient) per line-search round.  `newton_cg` is a trust-region
-Newton-CG method on the kernels' Hessian-vector products (fe_hessian_vector).
+Newton-CG method on the kernels' Hessian-vector products (fe_hessian_vector), with the inner
+CG on the host (torch) or on the device (fe_cg_steihaug); `nested_newton` runs it on a
+sequence of uniformly refined meshes, each started from the previous minimiser.
 """
 from __future__ import annotations
 
@@ -20,6 +22,7 @@ import math
 import time
 from dataclasses import dataclass, field
 
+import numpy as np
 import torch
 
 
@@ -361,14 +364,15 @@ def _rotate_yz(v, angle):
 
 
 def torsion_continuation(ev, hvp, coords, dirichlet, *, lx=0.4, T=24, alpha_max=8.0 * math.pi,
-                         gtol=1e-9, relative=True, max_iter=1000, cg=None):
+                         gtol=1e-9, relative=True, max_iter=1000, cg=None, **newton_kw):
     """Benchmark 4's sequence of minimisations: the bar's right face (x = lx) rotated about the
     x axis by alpha(t) = alpha_max t / T, the left face fixed, t = 1..T, each problem started
     from the previous minimiser (trust-region Newton-CG on the kernels).  The start of step 1
     is the twist of eq. (displacement) with alpha(1); the start of step t > 1 is the previous
     minimiser rotated by the increment alpha_max/T * x/lx (the face values then are exactly
     those of alpha(t)).  Yields (t, NewtonResult).  coords, dirichlet: the mesh's (n, 3) node
-    coordinates and per-dof Dirichlet mask, as tensors on the evaluators' device."""
+    coordinates and per-dof Dirichlet mask, as tensors on the evaluators' device; cg and any
+    other keyword (eta_max, max_cg, ...) go to newton_cg."""
     x = coords[:, 0]
     X = coords.reshape(-1)
     fixed = dirichlet.reshape(-1) != 0
@@ -378,7 +382,7 @@ def torsion_continuation(ev, hvp, coords, dirichlet, *, lx=0.4, T=24, alpha_max=
             v = _rotate_yz(v, alpha_max / T * x / lx)
             exact = _rotate_yz(X, alpha_max * t / T * x / lx)
             v = torch.where(fixed, exact, v)
-        r = newton_cg(ev, hvp, v, gtol=gtol, relative=relative, max_iter=max_iter, cg=cg)
+        r = newton_cg(ev, hvp, v, gtol=gtol, relative=relative, max_iter=max_iter, cg=cg, **newton_kw)
         v = r.v
         yield t, r
 
@@ -449,3 +453,69 @@ def batch_evaluator(batch, meshes, device=0):
         return [(J.item(), g) for J, g in outs]
 
     return batch_eval
+
+
+# ----------------------------------------------------------------------------------------
+# Nested iteration over uniformly refined meshes
+# ----------------------------------------------------------------------------------------
+
+def prolongation_pairs(coarse_coords, coarse_elems, fine_coords):
+    """For a fine mesh whose nodes are the coarse nodes and the midpoints of the coarse edges
+    (one uniform refinement of P1 simplices), the coarse node pair (a, b) of every fine node:
+    the coarse P1 function takes the value (v_a + v_b) / 2 there (a == b at coarse nodes).
+    When the fine elements refine the coarse ones, this is the exact injection of the coarse
+    space into the fine one.  Returns an int64 array (n_fine, 2); ValueError for a fine node
+    that is neither.  Node matching uses coordinates quantised to 2^-20 of the bounding box."""
+    cc = np.asarray(coarse_coords, dtype=np.float64)
+    ce = np.asarray(coarse_elems, dtype=np.int64)
+    fc = np.asarray(fine_coords, dtype=np.float64)
+    k = ce.shape[1]
+    nc = cc.shape[0]
+    edges = np.sort(np.concatenate([ce[:, [i, j]] for i in range(k) for j in range(i + 1, k)]), axis=1)
+    ekey = np.unique(edges[:, 0] * nc + edges[:, 1])
+    edges = np.stack([ekey // nc, ekey % nc], axis=1)
+    own = np.arange(nc, dtype=np.int64)
+    pairs = np.concatenate([np.stack([own, own], axis=1), edges])
+    pts = np.concatenate([cc, 0.5 * (cc[edges[:, 0]] + cc[edges[:, 1]])])
+    lo = np.minimum(pts.min(axis=0), fc.min(axis=0))
+    ext = np.maximum(np.maximum(pts.max(axis=0), fc.max(axis=0)) - lo, 1e-300)
+
+    def keys(x):
+        q = np.rint((x - lo) / ext * (1 << 20)).astype(np.int64)
+        out = np.zeros(x.shape[0], dtype=np.int64)
+        for m in range(x.shape[1]):
+            out = (out << 21) | q[:, m]
+        return out
+    kc, kf = keys(pts), keys(fc)
+    order = np.argsort(kc, kind="stable")
+    pos = np.searchsorted(kc[order], kf)
+    pos = np.minimum(pos, len(order) - 1)
+    hit = kc[order][pos] == kf
+    if not hit.all():
+        raise ValueError(f"{int((~hit).sum())} fine nodes are neither coarse nodes nor coarse edge midpoints")
+    return pairs[order[pos]]
+
+
+def prolong(v, pairs, d=1):
+    """The coarse P1 function v (d components per node) at the fine nodes given by pairs."""
+    idx = torch.as_tensor(pairs, device=v.device)
+    V = v.reshape(-1, d)
+    return (0.5 * (V[idx[:, 0]] + V[idx[:, 1]])).reshape(-1)
+
+
+def nested_newton(levels, v0, *, d=1, **newton_kw):
+    """Nested iteration: trust-region Newton-CG on each mesh of a uniformly refined sequence,
+    the first started from v0 and each later one from the previous minimiser prolonged to it.
+    levels: list of (ev, hvp, cg, coords, elems) per mesh, coarse to fine (cg may be None);
+    newton_kw go to newton_cg.  Returns the list of NewtonResult."""
+    out = []
+    v = v0
+    prev = None
+    for ev, hvp, cg, coords, elems in levels:
+        if prev is not None:
+            v = prolong(v, prolongation_pairs(prev[0], prev[1], coords), d)
+        r = newton_cg(ev, hvp, v, cg=cg, **newton_kw)
+        out.append(r)
+        v = r.v
+        prev = (coords, elems)
+    return out
