@@ -459,7 +459,7 @@ def run_minimize(args, device):
     from paper_2109_01158_gb300 import fem
     from paper_2109_01158_gb300 import meshgen as mg
     from paper_2109_01158_gb300.minimize import (batch_evaluator, lbfgs, lbfgs_batched, mesh_cg, mesh_evaluator,
-                                                 mesh_hvp, newton_cg, torsion_continuation)
+                                                 mesh_hvp, nested_newton, newton_cg, torsion_continuation)
     n = args.minimize_n
     dev = torch.device("cuda", device)
 
@@ -476,10 +476,16 @@ def run_minimize(args, device):
     out = {"workload": f"neohooke3d_{n}^3x6 gravity (0,0,-1e-2), {w.ne} tets, {w.ndof} dofs",
            "criterion": "||g||_inf <= 1e-6 ||g_0||_inf", "unknown": "displacement u = v - X",
            "runs": {}}
-    for name, prec, grad in (("df64_exact", fem.FE_DF64, "exact"), ("f64_exact", fem.FE_F64, "exact"),
-                             ("f32_exact", fem.FE_F32_COMP, "exact"), ("f64_fd", fem.FE_F64, "fd")):
+    # L-BFGS pairs and directions in the library's kernels (fe_lbfgs); one run with the same
+    # recursion in torch vector operations for comparison
+    for name, prec, grad, devmem in (("df64_exact", fem.FE_DF64, "exact", True),
+                                     ("f64_exact", fem.FE_F64, "exact", True),
+                                     ("f64_exact_torch_memory", fem.FE_F64, "exact", False),
+                                     ("f32_exact", fem.FE_F32_COMP, "exact", True),
+                                     ("f64_fd", fem.FE_F64, "fd", True)):
         gm.set_precision(prec)
-        r = lbfgs(mesh_evaluator(gm, grad, eps=1e-6), v0, gtol=1e-6, relative=True, max_iter=args.minimize_iters)
+        r = lbfgs(mesh_evaluator(gm, grad, eps=1e-6), v0, gtol=1e-6, relative=True, max_iter=args.minimize_iters,
+                  device_memory=devmem)
         out["runs"][name] = {"J": r.J, "iters": r.iters, "evals": r.evals, "converged": r.converged,
                              "seconds": r.seconds, "gnorm": r.gnorm, "g0": r.history[0][1]}
     # trust-region Newton-CG on the FP64 Hessian-vector products (device-resident inner CG)
@@ -501,7 +507,7 @@ def run_minimize(args, device):
     batch = fem.Batch(device)
     rs = lbfgs_batched(batch_evaluator(batch, meshes, device),
                        [torch.zeros(wk.ndof, dtype=torch.float64, device=dev) for wk in ws],
-                       gtol=1e-6, relative=True, max_iter=args.minimize_iters)
+                       gtol=1e-6, relative=True, max_iter=args.minimize_iters, device_memory=True)
     # Benchmark 4: the torsion continuation (24 minimisations) on the level-3 bar, FP64
     # kernels with trust-region Newton-CG, against the minimal energies the paper prints
     paper3 = {3: 1.4631, 6: 5.8533, 9: 13.1735, 12: 23.4286, 15: 36.6236, 18: 52.7641, 21: 71.7883, 24: 93.7238}
@@ -512,7 +518,8 @@ def run_minimize(args, device):
             "steps": []}
     t_start = time.perf_counter()
     for t, r in torsion_continuation(mesh_evaluator(gb), mesh_hvp(gb), torch.from_numpy(wb.coords).to(dev),
-                                     torch.from_numpy(wb.dirichlet.astype(np.int64)).to(dev), cg=mesh_cg(gb)):
+                                     torch.from_numpy(wb.dirichlet.astype(np.int64)).to(dev), cg=mesh_cg(gb),
+                                     eta_max=0.5):
         rec = {"t": t, "J": r.J, "iters": r.iters, "hessian_vector_products": r.hvps, "converged": r.converged,
                "seconds": r.seconds}
         if t in paper3:
@@ -521,19 +528,48 @@ def run_minimize(args, device):
     tors["seconds"] = time.perf_counter() - t_start
     out["torsion_benchmark4_level3"] = tors
     # Benchmark 6: the L-shape p-Laplacian (p = 3, f = -10) at level 8 (784,385 free dofs),
-    # componentwise density (the reading of the printed minima), FP64 Newton-CG from v = 0
-    lc, le, lb = mg.lshape_tri(8)
-    wl = mg.Workload("lshape8", 2, 1, lc, le, lb.astype(np.uint8), mg.MODEL_PLAPLACE_LP, p=3.0,
-                     f=np.full(lc.shape[0], -10.0), v=np.zeros(lc.shape[0]))
-    gl = fem.FEMesh.from_workload(wl, device=device)
+    # componentwise density (the reading of the printed minima), FP64 Newton-CG: from v = 0
+    # as the paper, and by nested iteration over levels 1..8
+    lmeshes = []
+    for L in range(1, 9):
+        lc, le, lb = mg.lshape_tri(L)
+        wl = mg.Workload(f"lshape{L}", 2, 1, lc, le, lb.astype(np.uint8), mg.MODEL_PLAPLACE_LP, p=3.0,
+                         f=np.full(lc.shape[0], -10.0), v=np.zeros(lc.shape[0]))
+        lmeshes.append((wl, fem.FEMesh.from_workload(wl, device=device)))
+    wl, gl = lmeshes[-1]
     r = newton_cg(mesh_evaluator(gl), mesh_hvp(gl), torch.zeros(wl.nn, dtype=torch.float64, device=dev),
                   gtol=1e-10, max_iter=5000, cg=mesh_cg(gl))
+    t_nest = time.perf_counter()
+    rn = nested_newton([(mesh_evaluator(g), mesh_hvp(g), mesh_cg(g), w.coords, w.elems) for w, g in lmeshes],
+                       torch.zeros(lmeshes[0][0].nn, dtype=torch.float64, device=dev), gtol=1e-10, max_iter=5000)
+    t_nest = time.perf_counter() - t_nest
     out["lshape_benchmark6_level8"] = {
         "workload": f"Benchmark 6 L-shape level 8 ({wl.ne} triangles, {int((wl.dirichlet == 0).sum())} free dofs)",
         "J": r.J, "J_paper": -8.1649, "iters": r.iters, "hessian_vector_products": r.hvps,
         "converged": r.converged, "seconds": r.seconds,
+        "nested": {"J": rn[-1].J, "iters_per_level": [x.iters for x in rn],
+                   "hessian_vector_products_per_level": [x.hvps for x in rn],
+                   "converged": all(x.converged for x in rn), "seconds_level8": rn[-1].seconds,
+                   "seconds_total": t_nest},
         "paper": "617.92 s, 22 trust-region iterations (exact gradient; MATLAB on an M1)"}
-    out[f"lockstep_8x{nl}^3x6"] = {"seconds": rs[0].seconds, "iters": [r.iters for r in rs],
+    # whole minimisations served by continuous batching: 16 gravity-cube requests (12^3..24^3 x 6,
+    # loads 1 + k/16), Poisson arrivals at 40/s; batched rounds vs one request at a time
+    from paper_2109_01158_gb300 import serve
+    msrv = serve.MinimizeServer(device)
+    served = {}
+    for mode in ("serial", "batched"):
+        reqs = serve.make_minimize_requests(16, rate=40.0, device=device)
+        served[mode] = (msrv.run(reqs, mode), reqs)
+    msrv.close()
+    same = all(a.result.J == b.result.J and torch.equal(a.result.v, b.result.v)
+               for a, b in zip(served["batched"][1], served["serial"][1]))
+    out["served_minimisations"] = {
+        "workload": "16 L-BFGS requests, 3D Neo-Hookean gravity cubes 12^3..24^3 x 6, Poisson arrivals 40/s, "
+                    "||g||_inf <= 1e-6 ||g0||_inf, double-float kernels",
+        "batched": served["batched"][0].as_dict(), "serial": served["serial"][0].as_dict(),
+        "results_identical_alone_and_in_the_mix": same,
+        "converged": all(r.result.converged for r in served["batched"][1])}
+    out[f"lockstep_8x{nl}^3x6"] = {"seconds": max(r.seconds for r in rs), "iters": [r.iters for r in rs],
                                    "evals": [r.evals for r in rs],
                                    "converged": all(r.converged for r in rs), "J": [r.J for r in rs]}
     return out

@@ -189,6 +189,33 @@ fe_status fe_hessian_vector(fe_ctx* ctx, const double* v_dev, const double* w_de
 fe_status fe_cg_steihaug(fe_ctx* ctx, const double* v_dev, const double* g_dev, double radius, double tol,
                          int max_cg, double* z_dev, double* Hz_dev, int* iters, int* boundary);
 
+/* ---- L-BFGS memory on the device (not in the paper: the minimiser driven by the kernels) ----
+ * The m most recent pairs s = v_new - v, y = g_new - g of a minimisation (oldest first) and
+ * the direction d = -H g of the limited-memory BFGS inverse Hessian H, computed in the compact
+ * representation of Byrd, Nocedal & Schnabel (1994, Thm. 2.2), with H_0 = (s.y / y.y) I of
+ * the newest pair: the same H as the two-loop recursion (Nocedal & Wright, Alg. 7.4) in exact
+ * arithmetic.  With no pairs, d = -g / ||g||.  Vectors are n doubles on the device; the
+ * memory holds 2 (m + 1) n doubles.  Reductions are fixed-order: results are bitwise
+ * reproducible.  Each call enqueues on the stream given at creation and returns once its
+ * scalar is on the host. */
+typedef struct fe_lbfgs fe_lbfgs;
+
+/* n >= 1 unknowns, 1 <= m <= 16 pairs; stream: a cudaStream_t (NULL = legacy default). */
+fe_status fe_lbfgs_create(fe_lbfgs** out, int device, void* stream, int64_t n, int m);
+fe_status fe_lbfgs_destroy(fe_lbfgs* lb);
+/* Forget every pair (the next direction is -g / ||g||). */
+fe_status fe_lbfgs_reset(fe_lbfgs* lb);
+/* Pairs in use (0..m). */
+fe_status fe_lbfgs_pairs(const fe_lbfgs* lb, int* count);
+/* Offer the pair s = v_new - v, y = g_new - g (device vectors of n doubles; not modified).
+ * *sy (host) receives s.y; the pair is kept when s.y > 0, replacing the oldest one when m
+ * pairs are held, and discarded otherwise. */
+fe_status fe_lbfgs_update(fe_lbfgs* lb, const double* v_new_dev, const double* v_dev, const double* g_new_dev,
+                          const double* g_dev, double* sy);
+/* d_dev (n doubles, device, written) = -H g_dev; *gd (host) = g.d.  g_dev and d_dev must not
+ * overlap. */
+fe_status fe_lbfgs_direction(fe_lbfgs* lb, const double* g_dev, double* d_dev, double* gd);
+
 /* Central-difference gradient over nodal patches (Sec. 6.1, eqs. CD, CDS, jgradpm,
  * sumpatch): for dof n of node i, component j,
  *   g_n = ( sum_{T in T^i} |T| W(F_T^+) - sum_{T in T^i} |T| W(F_T^-) ) / (2 eps) - b_n,

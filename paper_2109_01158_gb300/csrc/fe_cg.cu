@@ -15,62 +15,13 @@
 //   k_cg_dir                                d = -r + beta d; d.d, z.d
 // The host enqueues iterations in batches (2, 4, ... 32) and reads the state between batches;
 // launches enqueued after the solve has finished see the done flag and return at once.
-// The dot products are fixed-order trees over a grid that depends only on the vector length,
-// so results are bitwise reproducible.
+// The dot products are the fixed-order reductions of reduce.cuh, so results are bitwise
+// reproducible.
 #include "fe_internal.cuh"
+#include "reduce.cuh"
 
 namespace fe {
 namespace {
-
-__device__ __forceinline__ double cg_warp_sum(double x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-  return x;
-}
-
-// Fixed-tree sums over the block of NV values per thread; the totals are valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void cg_block_sum(double (&x)[NV]) {
-  __shared__ double sh[NV][kThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    x[j] = cg_warp_sum(x[j]);
-    if (lane == 0) sh[j][warp] = x[j];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    x[j] = (threadIdx.x < kThreads / 32) ? sh[j][threadIdx.x] : 0.0;
-    if (warp == 0) x[j] = cg_warp_sum(x[j]);
-  }
-}
-
-// Block partial sums to part[block * NV + j]; the block that arrives last sums the partials
-// in block order.  Returns true in thread 0 of that block, with the totals in tot.
-template <int NV>
-__device__ __forceinline__ bool cg_finish(double (&acc)[NV], double* part, unsigned* ticket, double (&tot)[NV]) {
-  __shared__ bool am_last;
-  cg_block_sum<NV>(acc);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) part[(int64_t)blockIdx.x * NV + j] = acc[j];
-    __threadfence();
-    am_last = atomicAdd(ticket, 1u) == gridDim.x - 1u;
-  }
-  __syncthreads();
-  if (!am_last) return false;
-  __threadfence();
-#pragma unroll
-  for (int j = 0; j < NV; ++j) tot[j] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads)
-#pragma unroll
-    for (int j = 0; j < NV; ++j) tot[j] += __ldcg(part + (int64_t)b * NV + j);
-  cg_block_sum<NV>(tot);
-  if (threadIdx.x == 0) *ticket = 0u;
-  return threadIdx.x == 0;
-}
 
 // tau >= 0 with ||z + tau d|| = radius, from zz = z.z, zd = z.d, dd = d.d.
 __device__ __forceinline__ double cg_to_boundary(double zz, double zd, double dd, double radius2) {
@@ -93,7 +44,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(int64_t n, const double* _
     acc[0] = fma(gi, gi, acc[0]);
   }
   double tot[1];
-  if (cg_finish<1>(acc, part, ticket, tot)) {
+  if (red_finish<1>(acc, part, ticket, tot)) {
     st->rr = st->rrn = st->dd = tot[0];
     st->zd = st->zz = st->dHd = 0.0;
     st->radius2 = radius * radius;
@@ -114,7 +65,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_curv(int64_t n, const double* _
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     acc[0] = fma(d[i], Hd[i], acc[0]);
   double tot[1];
-  if (cg_finish<1>(acc, part, ticket, tot)) st->dHd = tot[0];
+  if (red_finish<1>(acc, part, ticket, tot)) st->dHd = tot[0];
 }
 
 __global__ void __launch_bounds__(kThreads) k_cg_step(int64_t n, double* __restrict__ z, double* __restrict__ Hz,
@@ -143,7 +94,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_step(int64_t n, double* __restr
     }
   }
   double tot[2];
-  if (cg_finish<2>(acc, part, ticket, tot)) {
+  if (red_finish<2>(acc, part, ticket, tot)) {
     const int k = st->k + 1;
     st->k = k;
     if (stop) {
@@ -171,7 +122,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_dir(int64_t n, const double* __
     acc[1] = fma(z[i], di, acc[1]);
   }
   double tot[2];
-  if (cg_finish<2>(acc, part, ticket, tot)) {
+  if (red_finish<2>(acc, part, ticket, tot)) {
     st->dd = tot[0];
     st->zd = tot[1];
     st->rr = st->rrn;

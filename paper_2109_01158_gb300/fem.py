@@ -60,6 +60,12 @@ _SIGNATURES = {
     "fe_gradient_fd": [_vp, _vp, _dbl, _vp, _vp, _i64],
     "fe_hessian_vector": [_vp, _vp, _vp, _vp],
     "fe_cg_steihaug": [_vp, _vp, _vp, _dbl, _dbl, _int, _vp, _vp, _vp, _vp],
+    "fe_lbfgs_create": [_vp, _int, _vp, _i64, _int],
+    "fe_lbfgs_destroy": [_vp],
+    "fe_lbfgs_reset": [_vp],
+    "fe_lbfgs_pairs": [_vp, _vp],
+    "fe_lbfgs_update": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "fe_lbfgs_direction": [_vp, _vp, _vp, _vp],
     "fe_energy_gradient_host": [_vp, _vp, _vp, _vp],
     "fe_sync_status": [_vp],
     "fe_get_shape_gradients": [_vp, _vp, _vp],
@@ -147,6 +153,68 @@ fe_energy_gradient = _checked("fe_energy_gradient")
 fe_gradient_fd = _checked("fe_gradient_fd")
 fe_hessian_vector = _checked("fe_hessian_vector")
 fe_cg_steihaug = _checked("fe_cg_steihaug")
+fe_lbfgs_create = _checked("fe_lbfgs_create")
+fe_lbfgs_destroy = _checked("fe_lbfgs_destroy")
+fe_lbfgs_reset = _checked("fe_lbfgs_reset")
+fe_lbfgs_pairs = _checked("fe_lbfgs_pairs")
+fe_lbfgs_update = _checked("fe_lbfgs_update")
+fe_lbfgs_direction = _checked("fe_lbfgs_direction")
+
+
+class LbfgsMemory:
+    """The L-BFGS pairs of one minimisation on the device (fe_lbfgs): update(v_new, v, g_new, g)
+    offers a pair and returns s.y (kept when > 0); direction(g) returns (d, g.d) with
+    d = -H g of the limited-memory inverse Hessian."""
+
+    def __init__(self, n: int, m: int = 10, device=0):
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        self.n, self.m = int(n), int(m)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            fe_lbfgs_create(ctypes.byref(h), self.device.index or 0, ctypes.c_void_p(stream), self.n, self.m)
+        self.handle = h
+
+    @staticmethod
+    def device_bytes(n: int, m: int = 10) -> int:
+        return 8 * 2 * (m + 1) * int(n)
+
+    def _vec(self, x):
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.numel() == self.n):
+            raise TypeError(f"expected a float64 CUDA tensor of {self.n} entries")
+        return x.contiguous()
+
+    def reset(self):
+        fe_lbfgs_reset(self.handle)
+
+    def pairs(self) -> int:
+        k = ctypes.c_int(0)
+        fe_lbfgs_pairs(self.handle, ctypes.byref(k))
+        return k.value
+
+    def update(self, v_new, v, g_new, g) -> float:
+        v_new, v, g_new, g = self._vec(v_new), self._vec(v), self._vec(g_new), self._vec(g)
+        sy = ctypes.c_double(0.0)
+        fe_lbfgs_update(self.handle, _ptr(v_new), _ptr(v), _ptr(g_new), _ptr(g), ctypes.byref(sy))
+        return sy.value
+
+    def direction(self, g, out=None):
+        g = self._vec(g)
+        d = out if out is not None else torch.empty_like(g)
+        gd = ctypes.c_double(0.0)
+        fe_lbfgs_direction(self.handle, _ptr(g), _ptr(d), ctypes.byref(gd))
+        return d, gd.value
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            fe_lbfgs_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 fe_energy_gradient_host = _checked("fe_energy_gradient_host")
 fe_get_shape_gradients = _checked("fe_get_shape_gradients")
 fe_get_patches = _checked("fe_get_patches")

@@ -140,96 +140,141 @@ class _State:
         self.iters += 1
 
 
+class _DeviceState(_State):
+    """_State with the pairs and the direction on the device (fem.LbfgsMemory: the compact
+    representation of the same inverse Hessian, in fused kernels)."""
+
+    def __init__(self, v, J, g, m):
+        super().__init__(v, J, g, m)
+        from .fem import LbfgsMemory
+        self.mem = LbfgsMemory(v.numel(), m, v.device)
+
+    def direction(self):
+        d, gd = self.mem.direction(self.g)
+        if not gd < 0.0 and self.mem.pairs() > 0:
+            self.mem.reset()
+            d, gd = self.mem.direction(self.g)
+        return d, gd
+
+    def accept(self, v_new, J_new, g_new):
+        self.mem.update(v_new, self.v, g_new, self.g)
+        self.v, self.J, self.g = v_new, J_new, g_new
+        self.iters += 1
+
+    def close(self):
+        self.mem.close()
+
+
 def _noise(ev, eps_f):
     """Relative rounding level of J: the caller's, else the evaluator's `eps_f`, else 1e-10."""
     return eps_f if eps_f is not None else getattr(ev, "eps_f", 1e-10)
 
 
+class LbfgsJob:
+    """One L-BFGS minimisation as a state machine, so that a loop can drive many at once:
+    trial() is the point whose (J, g) the job needs next, feed(J, g) consumes them.  The first
+    trial is v0; then each iteration computes a direction and feeds line-search trials until
+    one is accepted.  done turns True when ||g||_inf <= tol, the iteration limit is reached, a
+    direction is not a descent direction, or a line search gives up after max_evals_per_iter
+    trials; result() then returns the LBFGSResult.  Driving one job with ev gives `lbfgs`."""
+
+    def __init__(self, v0, *, m: int = 10, gtol: float = 1e-6, relative: bool = False, max_iter: int = 20000,
+                 c1: float = 1e-4, sigma: float = 0.9, eps_f: float = 1e-10, max_evals_per_iter: int = 60,
+                 device_memory: bool = False):
+        self.v0 = v0
+        self.device_memory = device_memory and v0.is_cuda
+        self.m, self.gtol, self.relative, self.max_iter = m, gtol, relative, max_iter
+        self.c1, self.sigma, self.eps_f, self.max_evals = c1, sigma, eps_f, max_evals_per_iter
+        self.st = None
+        self.done = False
+        self.t0 = time.perf_counter()
+        self.seconds = 0.0
+        self._trial = v0
+
+    def trial(self):
+        return self._trial
+
+    def feed(self, J, g):
+        J = float(J)
+        if self.st is None:
+            self.st = (_DeviceState if self.device_memory else _State)(self.v0.clone(), J, g, self.m)
+            self.gn = _gnorm(g)
+            self.tol = self.gtol * (self.gn if self.relative else 1.0)
+            self.st.history.append((J, self.gn))
+            self._next_iteration()
+            return
+        st = self.st
+        st.evals += 1
+        if self.ls.update(J, float(torch.dot(g, self.d).item())):
+            st.accept(self._trial, J, g)
+            self.gn = _gnorm(st.g)
+            st.history.append((st.J, self.gn))
+            self._next_iteration()
+            return
+        self.n_search += 1
+        if self.n_search >= self.max_evals:
+            self._finish()
+        else:
+            self._trial = st.v + self.ls.t * self.d
+
+    def _next_iteration(self):
+        st = self.st
+        if not (self.gn > self.tol and st.iters < self.max_iter):
+            self._finish()
+            return
+        self.d, gd = st.direction()
+        if not gd < 0.0:
+            self._finish()
+            return
+        self.ls = _LineSearch(st.J, gd, self.c1, self.sigma, self.eps_f)
+        self.n_search = 0
+        self._trial = st.v + self.ls.t * self.d
+
+    def _finish(self):
+        self.done = True
+        self._trial = None
+        self.seconds = time.perf_counter() - self.t0
+        if isinstance(self.st, _DeviceState):
+            self.st.close()
+
+    def result(self) -> LBFGSResult:
+        st = self.st
+        return LBFGSResult(st.v, st.J, self.gn, st.iters, st.evals, self.gn <= self.tol, self.seconds, st.history)
+
+
 def lbfgs(ev, v0: torch.Tensor, *, m: int = 10, gtol: float = 1e-6, relative: bool = False,
           max_iter: int = 20000, c1: float = 1e-4, sigma: float = 0.9, eps_f: float | None = None,
-          max_evals_per_iter: int = 60) -> LBFGSResult:
+          max_evals_per_iter: int = 60, device_memory: bool = False) -> LBFGSResult:
     """Minimise J from v0.  Stops when ||g||_inf <= gtol (times ||g0||_inf if relative), or when
     a line search finds no acceptable step (converged is then False).  eps_f is the relative
-    rounding level of the evaluated J used by the approximate Wolfe test."""
-    t0 = time.perf_counter()
-    eps_f = _noise(ev, eps_f)
-    J, g = ev(v0)
-    st = _State(v0.clone(), float(J), g, m)
-    tol = gtol * (_gnorm(g) if relative else 1.0)
-    gn = _gnorm(g)
-    st.history.append((st.J, gn))
-    while gn > tol and st.iters < max_iter:
-        d, gd = st.direction()
-        if not gd < 0.0:
-            break
-        ls = _LineSearch(st.J, gd, c1, sigma, eps_f)
-        for _ in range(max_evals_per_iter):
-            v_new = st.v + ls.t * d
-            J_new, g_new = ev(v_new)
-            st.evals += 1
-            J_new = float(J_new)
-            if ls.update(J_new, float(torch.dot(g_new, d).item())):
-                break
-        else:
-            break
-        st.accept(v_new, J_new, g_new)
-        gn = _gnorm(st.g)
-        st.history.append((st.J, gn))
-    return LBFGSResult(st.v, st.J, gn, st.iters, st.evals, gn <= tol, time.perf_counter() - t0, st.history)
+    rounding level of the evaluated J used by the approximate Wolfe test.  device_memory keeps
+    the pairs and computes the directions in the library's kernels (fe_lbfgs; CUDA v0 only)
+    instead of torch vector operations."""
+    job = LbfgsJob(v0, m=m, gtol=gtol, relative=relative, max_iter=max_iter, c1=c1, sigma=sigma,
+                   eps_f=_noise(ev, eps_f), max_evals_per_iter=max_evals_per_iter, device_memory=device_memory)
+    while not job.done:
+        J, g = ev(job.trial())
+        job.feed(J, g)
+    return job.result()
 
 
 def lbfgs_batched(batch_eval, v0s, *, m: int = 10, gtol: float = 1e-6, relative: bool = False,
                   max_iter: int = 20000, c1: float = 1e-4, sigma: float = 0.9, eps_f: float | None = None,
-                  max_evals_per_iter: int = 60):
-    """Lockstep L-BFGS over several instances.  batch_eval(list of (k, v)) -> list of (J, g)
-    evaluates the trial points of the listed instances in one batched launch; each instance
-    follows exactly the iterates `lbfgs` would produce for it alone."""
-    t0 = time.perf_counter()
+                  max_evals_per_iter: int = 60, device_memory: bool = False):
+    """Several L-BFGS instances driven together.  batch_eval(list of (k, v)) -> list of (J, g)
+    evaluates the pending trial point of every unfinished instance in one batched launch; each
+    instance follows exactly the iterates `lbfgs` would produce for it alone."""
     eps_f = _noise(batch_eval, eps_f)
-    first = batch_eval(list(enumerate(v0s)))
-    states = [_State(v.clone(), float(J), g, m) for v, (J, g) in zip(v0s, first)]
-    tols = []
-    for s in states:
-        gn = _gnorm(s.g)
-        tols.append(gtol * (gn if relative else 1.0))
-        s.history.append((s.J, gn))
-        s.done = gn <= tols[-1]
+    jobs = [LbfgsJob(v, m=m, gtol=gtol, relative=relative, max_iter=max_iter, c1=c1, sigma=sigma, eps_f=eps_f,
+                     max_evals_per_iter=max_evals_per_iter, device_memory=device_memory) for v in v0s]
     while True:
-        active = [k for k, s in enumerate(states) if not s.done and s.iters < max_iter]
+        active = [k for k, j in enumerate(jobs) if not j.done]
         if not active:
             break
-        dirs, searches = {}, {}
-        for k in active:
-            s = states[k]
-            d, gd = s.direction()
-            if not gd < 0.0:
-                s.done = True
-                continue
-            dirs[k], searches[k] = d, _LineSearch(s.J, gd, c1, sigma, eps_f)
-        searching = list(searches)
-        for _ in range(max_evals_per_iter):
-            if not searching:
-                break
-            trial = [(k, states[k].v + searches[k].t * dirs[k]) for k in searching]
-            res = batch_eval(trial)
-            still = []
-            for (k, v_new), (J_new, g_new) in zip(trial, res):
-                s = states[k]
-                s.evals += 1
-                J_new = float(J_new)
-                if searches[k].update(J_new, float(torch.dot(g_new, dirs[k]).item())):
-                    s.accept(v_new, J_new, g_new)
-                    gn = _gnorm(s.g)
-                    s.history.append((s.J, gn))
-                    s.done = gn <= tols[k]
-                else:
-                    still.append(k)
-            searching = still
-        for k in searching:                # no acceptable step: stop that instance
-            states[k].done = True
-    secs = time.perf_counter() - t0
-    return [LBFGSResult(s.v, s.J, _gnorm(s.g), s.iters, s.evals, _gnorm(s.g) <= tols[k], secs, s.history)
-            for k, s in enumerate(states)]
+        res = batch_eval([(k, jobs[k].trial()) for k in active])
+        for k, (J, g) in zip(active, res):
+            jobs[k].feed(J, g)
+    return [j.result() for j in jobs]
 
 
 @dataclass

@@ -248,3 +248,158 @@ def serial_capacity(server: Server, requests) -> float:
     burst = [Request(r.rid, r.key, 0.0, r.v, ne=r.ne) for r in requests]
     st = server.run(burst, mode="serial", keep_results=False)
     return st.req_per_s
+
+
+# ----------------------------------------------------------------------------------------
+# Whole minimisations
+# ----------------------------------------------------------------------------------------
+
+@dataclass
+class MinimizeRequest:
+    """An L-BFGS minimisation of J on a resident mesh (FE_DF64; for Neo-Hookean usually with
+    displacement input), from the device vector v0, to ||g||_inf <= gtol (times ||g0||_inf if
+    relative).  arrival: seconds from the start of the stream."""
+    rid: int
+    mesh: object
+    v0: torch.Tensor
+    arrival: float
+    gtol: float = 1e-6
+    relative: bool = True
+    t_admit: float = math.nan
+    t_done: float = math.nan
+    result: object = None
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.arrival
+
+
+@dataclass
+class MinimizeStats:
+    mode: str
+    n: int
+    wall_s: float
+    p50_s: float
+    p99_s: float
+    mean_s: float
+    rounds: int
+    max_active: int
+    evaluations: int
+    minimisations_per_s: float
+    evaluations_per_s: float
+    latencies_s: list = field(default_factory=list)
+
+    def as_dict(self):
+        d = dict(self.__dict__)
+        d.pop("latencies_s")
+        return d
+
+
+class MinimizeServer:
+    """Continuous batching of whole minimisations.  Each admitted request is an L-BFGS job
+    (minimize.LbfgsJob) whose iterate, gradient and curvature pairs stay on the device, with
+    its directions computed by the library's L-BFGS kernels (fe_lbfgs).  A request is admitted
+    once it has arrived and its device bytes (the batched kernels' scratch, the 2 (m + 1)
+    vectors of the L-BFGS memory and 6 more of its mesh's size) fit in the HBM budget.  Every round evaluates the
+    pending trial point of every admitted job in one batched launch (fe_batch, three kernels
+    whatever the number of jobs), feeds each job its J and g, and retires the jobs that have
+    finished, which frees their bytes for the next arrivals.  Mode 'serial' admits one job at
+    a time, in arrival order, with the same kernels.  A job's evaluations do not depend on the
+    other jobs in the launch, so its iterates are the same in either mode."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 4 << 30, max_active: int = 64, m: int = 10):
+        from . import minimize
+        self._mz = minimize
+        self.device = torch.device("cuda", device)
+        self.batch = fem.Batch(device)
+        self.budget = int(hbm_budget)
+        self.max_active = max_active
+        self.m = m
+
+    def job_bytes(self, mesh) -> int:
+        return fem.Batch.work_bytes(mesh) + 256 + fem.LbfgsMemory.device_bytes(mesh.ndof, self.m) + 8 * mesh.ndof * 6
+
+    def close(self):
+        self.batch.close()
+
+    def run(self, requests: list, mode: str = "batched") -> MinimizeStats:
+        assert mode in ("batched", "serial")
+        cap = self.max_active if mode == "batched" else 1
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        active = []            # (request, job, work tensor, bytes)
+        used = 0
+        rounds = evals = max_active = 0
+        torch.cuda.synchronize(self.device)
+        t0 = time.perf_counter()
+        while pending or active:
+            now = time.perf_counter() - t0
+            while pending and len(active) < cap and pending[0].arrival <= now:
+                r = pending[0]
+                nb = self.job_bytes(r.mesh)
+                if active and used + nb > self.budget:
+                    break
+                pending.pop(0)
+                wb = fem.Batch.work_bytes(r.mesh)
+                buf = torch.empty(wb + 256, dtype=torch.uint8, device=self.device)
+                off = (-buf.data_ptr()) % 256
+                job = self._mz.LbfgsJob(r.v0, m=self.m, gtol=r.gtol, relative=r.relative,
+                                        eps_f=self._mz.EPS_F[fem.FE_DF64], device_memory=True)
+                r.t_admit = now
+                active.append((r, job, buf[off: off + wb], nb))
+                used += nb
+            if not active:
+                wait = pending[0].arrival - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 1e-3))
+                continue
+            max_active = max(max_active, len(active))
+            Js = torch.empty(len(active), dtype=torch.float64, device=self.device)
+            items, gs = [], []
+            for k, (r, job, work, _) in enumerate(active):
+                g = torch.empty(r.mesh.ndof, dtype=torch.float64, device=self.device)
+                items.append((r.mesh, job.trial().contiguous(), Js[k], g, work))
+                gs.append(g)
+            self.batch.run(items)
+            self.batch.sync_status()
+            Jh = Js.cpu().tolist()
+            rounds += 1
+            evals += len(active)
+            still = []
+            for (r, job, work, nb), J, g in zip(active, Jh, gs):
+                job.feed(J, g)
+                if job.done:
+                    r.t_done = time.perf_counter() - t0
+                    r.result = job.result()
+                    used -= nb
+                else:
+                    still.append((r, job, work, nb))
+            active = still
+        wall = max(r.t_done for r in requests) if requests else 0.0
+        lat = np.array([r.latency for r in requests])
+        return MinimizeStats(mode, len(requests), wall, float(np.percentile(lat, 50)), float(np.percentile(lat, 99)),
+                             float(lat.mean()), rounds, max_active, evals, len(requests) / wall, evals / wall,
+                             lat.tolist())
+
+
+def gravity_cube(n: int, scale: float = 1.0, device: int = 0):
+    """A minimisation request's mesh: the 3D Neo-Hookean cube n^3 x 6, face x = 0 clamped,
+    gravity (0, 0, -1e-2 scale), resident as FE_DF64 with displacement input; and u0 = 0."""
+    w = mg.neohooke_cube3d(n)
+    w.f = np.tile([0.0, 0.0, -1e-2 * scale], w.nn)
+    w.v = w.coords.ravel().copy()
+    mesh = fem.FEMesh.from_workload(w, device=device, precisions=(fem.FE_DF64,))
+    mesh.set_input(fem.FE_INPUT_DISPLACEMENT)
+    return mesh, torch.zeros(w.ndof, dtype=torch.float64, device=torch.device("cuda", device))
+
+
+def make_minimize_requests(n: int = 16, sizes=(12, 16, 20, 24), rate: float = 20.0, seed: int = 5, device: int = 0,
+                           gtol: float = 1e-6):
+    """n minimisation requests: gravity cubes of sizes drawn from `sizes`, loads scaled by
+    1 + k/n, Poisson arrivals of rate `rate` per second (seeded)."""
+    pick = (mg.uniform(seed, np.arange(n), 0.0, len(sizes)).astype(np.int64)).clip(0, len(sizes) - 1)
+    arr = poisson_arrivals(n, rate, seed)
+    reqs = []
+    for k in range(n):
+        mesh, u0 = gravity_cube(int(sizes[pick[k]]), 1.0 + k / n, device)
+        reqs.append(MinimizeRequest(k, mesh, u0, float(arr[k]), gtol=gtol, relative=True))
+    return reqs

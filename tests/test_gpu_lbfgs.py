@@ -1,0 +1,93 @@
+"""The device L-BFGS memory (fe_lbfgs, compact representation) against the two-loop
+recursion in torch on the same pairs, through the ring of pairs (fewer than m, exactly m,
+wrapped around), a rejected pair and a reset; and L-BFGS minimisations driven by it."""
+import numpy as np
+import pytest
+
+from paper_2109_01158_gb300 import meshgen as mg
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+def _fem():
+    from paper_2109_01158_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_01158_gb300 import fem
+    return fem
+
+
+def _pairs(n, count, seed):
+    """count pairs of a strictly convex quadratic with a spread spectrum: y = A s."""
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    diag = torch.exp(torch.linspace(0.0, 6.0, n, dtype=torch.float64))
+    out = []
+    v = torch.randn(n, generator=gen, dtype=torch.float64)
+    for _ in range(count):
+        v_new = v + torch.randn(n, generator=gen, dtype=torch.float64) * 0.1
+        out.append((v_new.cuda(), v.cuda(), (diag * v_new).cuda(), (diag * v).cuda()))
+        v = v_new
+    return out
+
+
+@pytest.mark.parametrize("count", [0, 1, 3, 10, 17])
+def test_device_direction_matches_two_loop(count):
+    fem = _fem()
+    from paper_2109_01158_gb300.minimize import _State
+    n, m = 4099, 10
+    mem = fem.LbfgsMemory(n, m)
+    g0 = torch.randn(n, dtype=torch.float64, generator=torch.Generator().manual_seed(99)).cuda()
+    ref = _State(torch.zeros(n, dtype=torch.float64, device="cuda"), 0.0, g0, m)
+    for v_new, v, g_new, g in _pairs(n, count, seed=count):
+        sy = mem.update(v_new, v, g_new, g)
+        assert sy > 0.0
+        ref.g = g
+        ref.v = v
+        ref.accept(v_new, 0.0, g_new)
+    assert mem.pairs() == min(count, m)
+    ref.g = g0
+    d_ref, gd_ref = ref.direction()
+    d, gd = mem.direction(g0)
+    scale = float(d_ref.abs().max())
+    assert float((d - d_ref).abs().max()) <= 1e-11 * scale
+    assert abs(gd - gd_ref) <= 1e-11 * abs(gd_ref) and gd < 0.0
+    d2, gd2 = mem.direction(g0)
+    assert torch.equal(d, d2) and gd == gd2
+    mem.close()
+
+
+def test_rejected_pair_and_reset():
+    fem = _fem()
+    n = 1000
+    mem = fem.LbfgsMemory(n, 4)
+    (v_new, v, g_new, g), = _pairs(n, 1, seed=5)
+    assert mem.update(v_new, v, g_new, g) > 0.0 and mem.pairs() == 1
+    assert mem.update(v_new, v, g, g_new) < 0.0 and mem.pairs() == 1     # s.y < 0: not kept
+    mem.reset()
+    assert mem.pairs() == 0
+    d, gd = mem.direction(g)
+    torch.testing.assert_close(d, -g / g.norm(), rtol=1e-15, atol=0.0)
+    assert abs(gd + float(g.norm())) <= 1e-14 * float(g.norm())
+    with pytest.raises(fem.FEError):
+        fem.LbfgsMemory(n, 17)
+    mem.close()
+
+
+def test_lbfgs_with_device_memory_reaches_the_same_minimum():
+    fem = _fem()
+    from paper_2109_01158_gb300 import minimize
+    w = mg.neohooke_cube3d(12)
+    w.f = np.tile([0.0, 0.0, -1e-2], w.nn)
+    gm = fem.FEMesh.from_workload(w)
+    gm.set_input(fem.FE_INPUT_DISPLACEMENT)
+    u0 = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+    ref = minimize.lbfgs(minimize.mesh_evaluator(gm), u0, gtol=1e-8, relative=True)
+    dev = minimize.lbfgs(minimize.mesh_evaluator(gm), u0, gtol=1e-8, relative=True, device_memory=True)
+    again = minimize.lbfgs(minimize.mesh_evaluator(gm), u0, gtol=1e-8, relative=True, device_memory=True)
+    assert ref.converged and dev.converged
+    assert abs(dev.J - ref.J) <= 1e-13 * abs(ref.J)
+    assert dev.iters <= 1.2 * ref.iters + 5
+    assert again.J == dev.J and again.iters == dev.iters and torch.equal(again.v, dev.v)

@@ -79,3 +79,26 @@ def test_gpu_benchmark6_minimal_energies(level):
                              cg=minimize.mesh_cg(gm))
     assert res.converged
     assert abs(res.J - row["J_min"]) <= 5e-5, (res.J, row["J_min"])
+
+
+def test_gpu_nested_newton_to_level7():
+    """Nested iteration on the FP64 kernels and the device CG: levels 1..7, each started from
+    the previous minimiser, every level's printed J(u) to its 4 decimals, few Newton steps per
+    level."""
+    fem = _fem()
+    from paper_2109_01158_gb300 import minimize
+    table = {int(r["level"]): r["J_min"] for r in read_golden("benchmark6_lshape.txt")}
+    levels = []
+    for L in range(1, 8):
+        coords, elems, bnd = mg.lshape_tri(L)
+        nn = coords.shape[0]
+        w = mg.Workload(f"lshape{L}", 2, 1, coords, elems, bnd.astype(np.uint8), mg.MODEL_PLAPLACE_LP,
+                        p=3.0, f=np.full(nn, -10.0), v=np.zeros(nn))
+        gm = fem.FEMesh.from_workload(w)
+        levels.append((minimize.mesh_evaluator(gm), minimize.mesh_hvp(gm), minimize.mesh_cg(gm), coords, elems))
+    n1 = mg.lshape_tri(1)[0].shape[0]
+    res = minimize.nested_newton(levels, torch.zeros(n1, dtype=torch.float64, device="cuda"), gtol=1e-10)
+    for L, r in zip(range(1, 8), res):
+        assert r.converged and abs(r.J - table[L]) <= 5e-5, (L, r.J)
+        if L > 1:
+            assert r.iters <= 12, (L, r.iters)

@@ -243,3 +243,21 @@ def test_gpu_torsion_continuation_reproduces_benchmark4(level):
         assert r.converged, (t, r.iters)
         if t in rows:
             _check_torsion(r.J, rows[t])
+
+
+def test_lbfgs_batched_follows_each_instance_alone():
+    """Jobs driven together take exactly the iterates of each job driven alone (CPU oracle)."""
+    oms = []
+    for k, p in enumerate((2.0, 3.0, 4.5)):
+        w = mg.plaplace_square(8, p=p, f=-10.0 * (1 + k))
+        w.v = np.zeros(w.nn)
+        oms.append((w, oracle.OracleMesh(w)))
+
+    def batch_eval(trials):
+        return [_oracle_ev(oms[k][1])(v) for k, v in trials]
+    res = lbfgs_batched(batch_eval, [torch.zeros(w.nn, dtype=torch.float64) for w, _ in oms], gtol=1e-9)
+    for (w, om), r in zip(oms, res):
+        single = lbfgs(_oracle_ev(om), torch.zeros(w.nn, dtype=torch.float64), gtol=1e-9)
+        assert r.converged and single.converged
+        assert r.J == single.J and r.iters == single.iters and r.evals == single.evals
+        assert torch.equal(r.v, single.v)
