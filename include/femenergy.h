@@ -215,6 +215,11 @@ fe_status fe_lbfgs_update(fe_lbfgs* lb, const double* v_new_dev, const double* v
 /* d_dev (n doubles, device, written) = -H g_dev; *gd (host) = g.d.  g_dev and d_dev must not
  * overlap. */
 fe_status fe_lbfgs_direction(fe_lbfgs* lb, const double* g_dev, double* d_dev, double* gd);
+/* One accepted L-BFGS step in one host round trip: fe_lbfgs_update with (v_new, v, g_new, g),
+ * then fe_lbfgs_direction at g_new into d_dev, and max_i |g_new_i|.  out3 (host, 3 doubles)
+ * receives s.y, g_new.d and max |g_new|.  The same pairs and direction as the two calls. */
+fe_status fe_lbfgs_step(fe_lbfgs* lb, const double* v_new_dev, const double* v_dev, const double* g_new_dev,
+                        const double* g_dev, double* d_dev, double* out3);
 
 /* Central-difference gradient over nodal patches (Sec. 6.1, eqs. CD, CDS, jgradpm,
  * sumpatch): for dof n of node i, component j,

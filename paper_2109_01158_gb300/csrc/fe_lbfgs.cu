@@ -39,7 +39,7 @@ struct fe_lbfgs {
   double* SY = nullptr;     // (m + 1)^2: SY[i * (m + 1) + j] = s_i . y_j
   double* YY = nullptr;     // (m + 1)^2: y_i . y_j
   double* coef = nullptr;   // 1 + 2 kMaxPairs direction coefficients
-  double* scal = nullptr;   // [0] s.y of the last update, [1] g.d of the last direction
+  double* scal = nullptr;   // [0] s.y of the last update, [1] g.d of the last direction, [2] max |g|
   double* part = nullptr;   // partial sums
   unsigned* ticket = nullptr;
   double* host = nullptr;   // page-locked copy of scal
@@ -177,6 +177,35 @@ __global__ void __launch_bounds__(kThreads) k_lb_combine(int64_t n, const double
   if (red_finish<1>(acc, part, ticket, tot)) scal[1] = tot[0];
 }
 
+// max_e |g_e| (order-independent), finished by the last block into scal[2].
+__global__ void __launch_bounds__(kThreads) k_lb_maxabs(int64_t n, const double* __restrict__ g, double* scal,
+                                                        double* part, unsigned* ticket) {
+  __shared__ double sh[kThreads / 32];
+  __shared__ bool am_last;
+  double x = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) x = fmax(x, fabs(g[e]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = sh[0];
+    for (int w = 1; w < kThreads / 32; ++w) b = fmax(b, sh[w]);
+    part[blockIdx.x] = b;
+    __threadfence();
+    am_last = atomicAdd(ticket, 1u) == gridDim.x - 1u;
+  }
+  __syncthreads();
+  if (!am_last || threadIdx.x != 0) return;
+  __threadfence();
+  double m = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) m = fmax(m, __ldcg(part + b));
+  scal[2] = m;
+  *ticket = 0u;
+}
+
 template <int K>
 void lb_launch_update(fe_lbfgs* L, const double* v_new, const double* v, const double* g_new, const double* g,
                       const LbSlots& sl, int nb) {
@@ -223,7 +252,7 @@ LbSlots slots_of(const fe_lbfgs* L) {
 }
 
 fe_status lb_read_scalars(fe_lbfgs* L) {
-  fe_status st = cuda_check(cudaMemcpyAsync(L->host, L->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, L->stream),
+  fe_status st = cuda_check(cudaMemcpyAsync(L->host, L->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, L->stream),
                             "lbfgs scalars");
   if (st) return st;
   return cuda_check(cudaStreamSynchronize(L->stream), "lbfgs sync");
@@ -257,11 +286,11 @@ fe_status fe_lbfgs_create(fe_lbfgs** out, int device, void* stream, int64_t n, i
       (st = cuda_check(cudaMalloc((void**)&L->SY, ld2 * sizeof(double)), "cudaMalloc")) ||
       (st = cuda_check(cudaMalloc((void**)&L->YY, ld2 * sizeof(double)), "cudaMalloc")) ||
       (st = cuda_check(cudaMalloc((void**)&L->coef, (1 + 2 * kMaxPairs) * sizeof(double)), "cudaMalloc")) ||
-      (st = cuda_check(cudaMalloc((void**)&L->scal, 2 * sizeof(double)), "cudaMalloc")) ||
+      (st = cuda_check(cudaMalloc((void**)&L->scal, 3 * sizeof(double)), "cudaMalloc")) ||
       (st = cuda_check(cudaMalloc((void**)&L->part, part * sizeof(double)), "cudaMalloc")) ||
       (st = cuda_check(cudaMalloc((void**)&L->ticket, sizeof(unsigned)), "cudaMalloc")) ||
       (st = cuda_check(cudaMemset(L->ticket, 0, sizeof(unsigned)), "cudaMemset")) ||
-      (st = cuda_check(cudaMallocHost((void**)&L->host, 2 * sizeof(double)), "cudaMallocHost"))) {
+      (st = cuda_check(cudaMallocHost((void**)&L->host, 3 * sizeof(double)), "cudaMallocHost"))) {
     fe_lbfgs_destroy(L);
     return st;
   }
@@ -299,6 +328,70 @@ fe_status fe_lbfgs_pairs(const fe_lbfgs* L, int* count) {
   return FE_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The spare slot (holding the last offered pair) joins the pairs in use.
+void lb_keep_spare(fe_lbfgs* L) {
+  if (L->count < L->m) {
+    // the next spare is a slot none of the pairs in use holds (m + 1 slots, at most m pairs)
+    L->ring[L->count++] = L->spare;
+    bool used[kMaxPairs + 1] = {false};
+    for (int i = 0; i < L->count; ++i) used[L->ring[i]] = true;
+    for (int i = 0; i <= L->m; ++i)
+      if (!used[i]) {
+        L->spare = i;
+        break;
+      }
+  } else {
+    const int oldest = L->ring[0];
+    for (int i = 0; i + 1 < L->m; ++i) L->ring[i] = L->ring[i + 1];
+    L->ring[L->m - 1] = L->spare;
+    L->spare = oldest;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+fe_status fe_lbfgs_step(fe_lbfgs* L, const double* v_new, const double* v, const double* g_new, const double* g,
+                        double* d, double* out3) {
+  if (!L || !v_new || !v || !g_new || !g || !d || !out3) return set_error(FE_EINVAL, "null argument");
+  LbDeviceGuard guard(L->device);
+  const int nb = grid_for(L->n, kMaxNodeBlocks);
+  // offer the pair, keep it provisionally, and compute the next direction and max |g_new|
+  const int count0 = L->count, spare0 = L->spare;
+  int ring0[kMaxPairs];
+  for (int i = 0; i < count0; ++i) ring0[i] = L->ring[i];
+  lb_dispatch(L->count, L, v_new, v, g_new, g, nullptr, slots_of(L), nb, true);
+  lb_keep_spare(L);
+  lb_dispatch(L->count, L, g_new, nullptr, nullptr, nullptr, d, slots_of(L), nb, false);
+  k_lb_maxabs<<<nb, kThreads, 0, L->stream>>>(L->n, g_new, L->scal, L->part, L->ticket);
+  fe_status st = cuda_check(cudaGetLastError(), "lbfgs step launch");
+  if (st || (st = lb_read_scalars(L))) return st;
+  if (!(L->host[0] > 0.0)) {
+    // s.y <= 0: drop the pair and compute the direction from the pairs kept before
+    L->count = count0;
+    L->spare = spare0;
+    for (int i = 0; i < count0; ++i) L->ring[i] = ring0[i];
+    const double sy = L->host[0], gmax = L->host[2];
+    lb_dispatch(L->count, L, g_new, nullptr, nullptr, nullptr, d, slots_of(L), nb, false);
+    if ((st = cuda_check(cudaGetLastError(), "lbfgs direction launch")) || (st = lb_read_scalars(L))) return st;
+    L->host[0] = sy;
+    L->host[2] = gmax;
+  }
+  out3[0] = L->host[0];
+  out3[1] = L->host[1];
+  out3[2] = L->host[2];
+  return FE_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
 fe_status fe_lbfgs_update(fe_lbfgs* L, const double* v_new, const double* v, const double* g_new, const double* g,
                           double* sy) {
   if (!L || !v_new || !v || !g_new || !g || !sy) return set_error(FE_EINVAL, "null argument");
@@ -309,25 +402,7 @@ fe_status fe_lbfgs_update(fe_lbfgs* L, const double* v_new, const double* v, con
   fe_status st = cuda_check(cudaGetLastError(), "lbfgs update launch");
   if (st || (st = lb_read_scalars(L))) return st;
   *sy = L->host[0];
-  if (*sy > 0.0) {
-    if (L->count < L->m) {
-      // the spare joins the pairs in use; the next spare is a slot none of them holds (there
-      // are m + 1 slots and at most m pairs)
-      L->ring[L->count++] = L->spare;
-      bool used[kMaxPairs + 1] = {false};
-      for (int i = 0; i < L->count; ++i) used[L->ring[i]] = true;
-      for (int i = 0; i <= L->m; ++i)
-        if (!used[i]) {
-          L->spare = i;
-          break;
-        }
-    } else {
-      const int oldest = L->ring[0];
-      for (int i = 0; i + 1 < L->m; ++i) L->ring[i] = L->ring[i + 1];
-      L->ring[L->m - 1] = L->spare;
-      L->spare = oldest;
-    }
-  }
+  if (*sy > 0.0) lb_keep_spare(L);
   return FE_OK;
 }
 

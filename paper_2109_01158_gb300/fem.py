@@ -66,6 +66,7 @@ _SIGNATURES = {
     "fe_lbfgs_pairs": [_vp, _vp],
     "fe_lbfgs_update": [_vp, _vp, _vp, _vp, _vp, _vp],
     "fe_lbfgs_direction": [_vp, _vp, _vp, _vp],
+    "fe_lbfgs_step": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "fe_energy_gradient_host": [_vp, _vp, _vp, _vp],
     "fe_sync_status": [_vp],
     "fe_get_shape_gradients": [_vp, _vp, _vp],
@@ -159,6 +160,7 @@ fe_lbfgs_reset = _checked("fe_lbfgs_reset")
 fe_lbfgs_pairs = _checked("fe_lbfgs_pairs")
 fe_lbfgs_update = _checked("fe_lbfgs_update")
 fe_lbfgs_direction = _checked("fe_lbfgs_direction")
+fe_lbfgs_step = _checked("fe_lbfgs_step")
 
 
 class LbfgsMemory:
@@ -204,6 +206,15 @@ class LbfgsMemory:
         gd = ctypes.c_double(0.0)
         fe_lbfgs_direction(self.handle, _ptr(g), _ptr(d), ctypes.byref(gd))
         return d, gd.value
+
+    def step(self, v_new, v, g_new, g, out=None):
+        """update(v_new, v, g_new, g) and direction(g_new) in one host round trip: returns
+        (d, s.y, g_new.d, max |g_new|)."""
+        v_new, v, g_new, g = self._vec(v_new), self._vec(v), self._vec(g_new), self._vec(g)
+        d = out if out is not None else torch.empty_like(g)
+        o = (ctypes.c_double * 3)()
+        fe_lbfgs_step(self.handle, _ptr(v_new), _ptr(v), _ptr(g_new), _ptr(g), _ptr(d), o)
+        return d, o[0], o[1], o[2]
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

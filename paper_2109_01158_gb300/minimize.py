@@ -161,6 +161,17 @@ class _DeviceState(_State):
         self.v, self.J, self.g = v_new, J_new, g_new
         self.iters += 1
 
+    def accept_step(self, v_new, J_new, g_new):
+        """accept(), the next direction() and ||g_new||_inf in one host round trip: returns
+        (d, g_new.d, ||g_new||_inf)."""
+        d, _, gd, gmax = self.mem.step(v_new, self.v, g_new, self.g)
+        self.v, self.J, self.g = v_new, J_new, g_new
+        self.iters += 1
+        if not gd < 0.0 and self.mem.pairs() > 0:
+            self.mem.reset()
+            d, gd = self.mem.direction(self.g)
+        return d, gd, gmax
+
     def close(self):
         self.mem.close()
 
@@ -194,7 +205,19 @@ class LbfgsJob:
     def trial(self):
         return self._trial
 
-    def feed(self, J, g):
+    def search_direction(self):
+        """The direction of the current line search (None before the first evaluation)."""
+        return None if (self.st is None or self.done) else self.d
+
+    def feed(self, J, g, gd=None):
+        """J (a float or a device scalar) and g at trial(); gd: g.d along search_direction()
+        when the caller has it already (else it is computed here, read together with J)."""
+        if self.st is not None and gd is None:
+            gdt = torch.dot(g, self.d)
+            if isinstance(J, torch.Tensor):
+                J, gd = torch.stack([J.reshape(()).to(gdt.dtype), gdt]).tolist()
+            else:
+                gd = float(gdt.item())
         J = float(J)
         if self.st is None:
             self.st = (_DeviceState if self.device_memory else _State)(self.v0.clone(), J, g, self.m)
@@ -205,11 +228,16 @@ class LbfgsJob:
             return
         st = self.st
         st.evals += 1
-        if self.ls.update(J, float(torch.dot(g, self.d).item())):
-            st.accept(self._trial, J, g)
-            self.gn = _gnorm(st.g)
-            st.history.append((st.J, self.gn))
-            self._next_iteration()
+        if self.ls.update(J, float(gd)):
+            if isinstance(st, _DeviceState):
+                d, gdn, self.gn = st.accept_step(self._trial, J, g)
+                st.history.append((st.J, self.gn))
+                self._next_iteration((d, gdn))
+            else:
+                st.accept(self._trial, J, g)
+                self.gn = _gnorm(st.g)
+                st.history.append((st.J, self.gn))
+                self._next_iteration()
             return
         self.n_search += 1
         if self.n_search >= self.max_evals:
@@ -217,12 +245,12 @@ class LbfgsJob:
         else:
             self._trial = st.v + self.ls.t * self.d
 
-    def _next_iteration(self):
+    def _next_iteration(self, direction=None):
         st = self.st
         if not (self.gn > self.tol and st.iters < self.max_iter):
             self._finish()
             return
-        self.d, gd = st.direction()
+        self.d, gd = direction if direction is not None else st.direction()
         if not gd < 0.0:
             self._finish()
             return
@@ -458,17 +486,18 @@ EPS_F = {0: 1e-10, 1: 1e-6, 2: 1e-10}
 
 def mesh_evaluator(mesh, gradient: str = "exact", eps: float = 1e-6):
     """ev(v) -> (J, g) with the library's kernels: exact gradient or patch central
-    differences (the energy comes from the same call in the exact case).  ev.eps_f is the
+    differences (the energy comes from the same call in the exact case).  J is a device
+    scalar, read by the caller (float(J)) when it needs it.  ev.eps_f is the
     rounding level of J at the mesh's active precision when the evaluator is made."""
     if gradient == "exact":
         def ev(v):
             J, g = mesh.energy_gradient(v)
-            return J.item(), g
+            return J, g
     elif gradient == "fd":
         def ev(v):
             J = mesh.energy(v)
             g = mesh.gradient_fd(v, eps)
-            return J.item(), g
+            return J, g
     else:
         raise ValueError(gradient)
     ev.eps_f = EPS_F.get(mesh.precision, 1e-10)

@@ -361,12 +361,16 @@ class MinimizeServer:
                 gs.append(g)
             self.batch.run(items)
             self.batch.sync_status()
-            Jh = Js.cpu().tolist()
+            # every job's J and g.d along its search direction in one read
+            dirs = [job.search_direction() for _, job, _, _ in active]
+            gds = [torch.dot(g, d) for g, d in zip(gs, dirs) if d is not None]
+            host = torch.cat([Js] + ([torch.stack(gds)] if gds else [])).tolist()
+            Jh, gdh = host[:len(active)], iter(host[len(active):])
             rounds += 1
             evals += len(active)
             still = []
-            for (r, job, work, nb), J, g in zip(active, Jh, gs):
-                job.feed(J, g)
+            for (r, job, work, nb), J, g, d in zip(active, Jh, gs, dirs):
+                job.feed(J, g, None if d is None else next(gdh))
                 if job.done:
                     r.t_done = time.perf_counter() - t0
                     r.result = job.result()

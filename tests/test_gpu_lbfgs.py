@@ -91,3 +91,26 @@ def test_lbfgs_with_device_memory_reaches_the_same_minimum():
     assert abs(dev.J - ref.J) <= 1e-13 * abs(ref.J)
     assert dev.iters <= 1.2 * ref.iters + 5
     assert again.J == dev.J and again.iters == dev.iters and torch.equal(again.v, dev.v)
+
+
+def test_step_equals_update_then_direction():
+    """fe_lbfgs_step gives bitwise the pairs and directions of update + direction, and drops a
+    pair with s.y <= 0 (the direction then comes from the pairs kept before)."""
+    fem = _fem()
+    n, m = 3001, 4
+    a, b = fem.LbfgsMemory(n, m), fem.LbfgsMemory(n, m)
+    for v_new, v, g_new, g in _pairs(n, 7, seed=11):
+        a.update(v_new, v, g_new, g)
+        da, gda = a.direction(g_new)
+        db, sy, gdb, gmax = b.step(v_new, v, g_new, g)
+        assert sy > 0.0 and a.pairs() == b.pairs()
+        assert torch.equal(da, db) and gda == gdb
+        assert gmax == float(g_new.abs().max())
+    # a pair with s.y < 0 is not kept
+    k = b.pairs()
+    db, sy, gdb, _ = b.step(v, v_new, g_new, g)
+    assert sy < 0.0 and b.pairs() == k
+    da, gda = a.direction(g_new)
+    assert torch.equal(da, db) and gda == gdb
+    a.close()
+    b.close()
