@@ -409,6 +409,26 @@ def run_ours(args, rank, world, local):
     hms = e0.elapsed_time(e1) / nh
     variants["f64_hessian_vector"] = {"value": w.ne / (hms / 1e3) / 1e9, "unit": "Gelem/s", "ms_per_call": hms}
 
+    # the paper's central-difference gradient over patches (Sec. 6.1), every dof, FP64:
+    # 2 (dim + 1) d density evaluations per element
+    if gm.precision != fem.FE_F64:
+        gm.set_precision(fem.FE_F64)
+    for _ in range(2):
+        gm.gradient_fd(v, 1e-6)
+    nf = max(3, args.steps // 20)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(nf):
+        gm.gradient_fd(v, 1e-6)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    fms = e0.elapsed_time(e1) / nf
+    assert gm.sync_status() == fem.FE_OK
+    n_w = 2 * (w.dim + 1) * w.d
+    variants["f64_fd_gradient"] = {"value": w.ne / (fms / 1e3) / 1e9, "unit": "Gelem/s", "ms_per_call": fms,
+                                   "density_evaluations_per_element": n_w, "eps": 1e-6}
+    gm.set_precision(code[prec])
+
     line = {
         "metric": "energy+grad throughput", "value": value, "unit": "Gelem/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,

@@ -108,6 +108,7 @@ void free_precompute(fe_ctx* c) {
   dev_free(c, &c->stage_v, nn * c->d);
   dev_free(c, &c->stage_g, nn * c->d);
   dev_free(c, &c->cg_vec, 3 * nn * c->d);
+  dev_free(c, &c->hvp_cache, hvp_cache_doubles(c));
   c->have_pre = false;
   c->pre_mask = 0;
 }
@@ -510,6 +511,7 @@ fe_status fe_cg_steihaug(fe_ctx* c, const double* v, const double* g, double rad
   const size_t n = (size_t)c->nn * c->d;
   if (!c->w_hvp && (st = dev_alloc(c, &c->w_hvp, (size_t)c->nn * padded_d(c->d)))) return st;
   if (!c->cg_vec && (st = dev_alloc(c, &c->cg_vec, 3 * n))) return st;
+  if (!c->hvp_cache && (st = dev_alloc(c, &c->hvp_cache, hvp_cache_doubles(c)))) return st;
   if (!c->cg_part && (st = dev_alloc(c, &c->cg_part, 2 * kMaxNodeBlocks))) return st;
   if (!c->cg_ticket) {
     if ((st = dev_alloc(c, &c->cg_ticket, 1))) return st;

@@ -8,7 +8,8 @@
 // every kernel reads them at entry, so all blocks take the same branch, and the block that
 // finishes a kernel's reduction last (a ticket counter) writes the new scalars and the flags.
 // One CG iteration is five launches on the context stream:
-//   k_w_prep + k_hvp_f64 + k_gather_bulk   Hd = H d
+//   k_w_prep + k_hvp_cached_f64 + k_gather_bulk   Hd = H d (the v-dependent terms of H are
+//                                           computed once per solve by k_hvp_prep_f64)
 //   k_cg_curv                               dHd = d.Hd
 //   k_cg_step                               z += a d, Hz += a Hd, r += a Hd; r.r, z.z
 //                                           (a = r.r / dHd, or the step to the boundary)
@@ -141,7 +142,7 @@ fe_status launch_cg_steihaug(fe_ctx* c, const double* v, const double* g, double
   CgState* st_dev = c->cg_state;
   const int* skip = &st_dev->done;
   const int nb = grid_for(n, kMaxNodeBlocks);
-  fe_status st = launch_node_prep_f64(c, v);
+  fe_status st = launch_hvp_prepare_f64(c, v);
   if (st) return st;
   k_cg_init<<<nb, kThreads, 0, s>>>(n, g, z, Hz, r, d, st_dev, c->cg_part, c->cg_ticket, radius, tol, max_cg);
   c->launches++;
@@ -153,7 +154,7 @@ fe_status launch_cg_steihaug(fe_ctx* c, const double* v, const double* g, double
   int batch = 2;
   for (;;) {
     for (int b = 0; b < batch; ++b) {
-      if ((st = launch_hvp_dir_f64(c, d, Hd, skip))) return st;
+      if ((st = launch_hvp_cached_f64(c, d, Hd, skip))) return st;
       k_cg_curv<<<nb, kThreads, 0, s>>>(n, d, Hd, st_dev, c->cg_part, c->cg_ticket);
       k_cg_step<<<nb, kThreads, 0, s>>>(n, z, Hz, r, d, Hd, st_dev, c->cg_part, c->cg_ticket);
       k_cg_dir<<<nb, kThreads, 0, s>>>(n, z, r, d, st_dev, c->cg_part, c->cg_ticket);

@@ -219,7 +219,7 @@ __device__ __forceinline__ void finish_energy_nt(double block_total, double* par
 // Element kernel: persistent blocks stream tiles of the element arrays through shared-memory
 // stages with bulk copies (tile_stream.cuh); one element per thread and tile.
 template <int DIM, int D, int MODEL, bool ENERGY, bool GRAD, bool DENS>
-__global__ void __launch_bounds__(kTile, 20) k_elem_f32(
+__global__ void __launch_bounds__(kTile, kTileMinBlocks) k_elem_f32(
     int64_t ne, TileArrays<F32Arrays<DIM, GRAD>::N> A, const float2* __restrict__ u,
     const int32_t* __restrict__ eperm, ModelParams mp, float* __restrict__ r,
     double* __restrict__ dens, double* partials, const double* node_partials, int n_node_blocks,

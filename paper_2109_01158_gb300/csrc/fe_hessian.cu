@@ -211,6 +211,268 @@ __global__ void __launch_bounds__(kThreads) k_hvp_f64(int64_t ne, const int32_t*
   if (bad) atomicOr(status, kStatusDomain);
 }
 
+// ---- products at a fixed point (the inner CG of a Newton step) ---------------------------
+//
+// Within one CG solve v is fixed, so the part of k_hvp_f64 that depends on v alone is computed
+// once (k_hvp_prep_f64) into a structure-of-arrays cache, and each product (k_hvp_cached_f64)
+// reads it instead of gathering u and rebuilding F, cof F and the coefficients.  Both kernels
+// evaluate the same expressions as k_hvp_f64.  Cache entries per element:
+//   Neo-Hookean            F, cof F, 2 C1 |T|, |T| (2 C1 / det^2 + 2 D1), |T| (2 D1 (det - 1) - 2 C1 / det)
+//   componentwise p-Lap.   |T| (p - 1) |H_m|^(p-2)                       (m < dim)
+//   p-Laplacian            H, c1 = s^((p-2)/2), c2 = (p - 2) c1 / s, |T|
+
+template <int DIM, int MODEL>
+constexpr int hvp_cache_width() {
+  return MODEL == FE_NEOHOOKE ? 2 * DIM * DIM + 3 : (MODEL == FE_PLAPLACE_LP ? DIM : DIM + 3);
+}
+
+template <int DIM, int D, int MODEL>
+__global__ void __launch_bounds__(kThreads) k_hvp_prep_f64(int64_t ne, const int32_t* __restrict__ elems,
+                                                           const double* __restrict__ dphi,
+                                                           const double* __restrict__ vol,
+                                                           const double* __restrict__ u, ModelParams mp,
+                                                           double* __restrict__ cache, int* status) {
+  constexpr int K = DIM + 1;
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
+    double ul[K][D];
+#pragma unroll
+    for (int l = 0; l < K; ++l) load_vec<D>(u, __ldg(elems + (int64_t)l * ne + e), ul[l]);
+    double g[DIM][DIM];
+#pragma unroll
+    for (int l = 0; l < DIM; ++l)
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) g[l][m] = __ldg(dphi + ((int64_t)l * DIM + m) * ne + e);
+    const double vT = __ldg(vol + e);
+    double H[D][DIM];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double a[DIM];
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) a[l] = ul[l + 1][j] - ul[0][j];
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) {
+        double s = a[0] * g[0][m];
+#pragma unroll
+        for (int l = 1; l < DIM; ++l) s = fma(a[l], g[l][m], s);
+        H[j][m] = s;
+      }
+    }
+    double* out = cache + e;
+    if constexpr (MODEL == FE_NEOHOOKE) {
+      double F[DIM][DIM], C[DIM][DIM];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) F[j][m] = (j == m) ? 1.0 + H[j][m] : H[j][m];
+      double delta;
+      if constexpr (DIM == 3) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            const int r0 = j == 0 ? 1 : 0, r1 = j == 2 ? 1 : 2;
+            const int c0 = m == 0 ? 1 : 0, c1 = m == 2 ? 1 : 2;
+            const double mn = F[r0][c0] * F[r1][c1] - F[r0][c1] * F[r1][c0];
+            const double sg = ((j + m) & 1) ? -1.0 : 1.0;
+            C[j][m] = sg * mn;
+          }
+        const double M00 = H[1][1] * H[2][2] - H[1][2] * H[2][1];
+        const double X = H[1][1] + H[2][2] + M00;
+        delta = H[0][0] + X + H[0][0] * X + H[0][1] * C[0][1] + H[0][2] * C[0][2];
+      } else {
+        C[0][0] = F[1][1];
+        C[0][1] = -F[1][0];
+        C[1][0] = -F[0][1];
+        C[1][1] = F[0][0];
+        delta = H[0][0] + H[1][1] + (H[0][0] * H[1][1] - H[0][1] * H[1][0]);
+      }
+      const double det = 1.0 + delta;
+      if (!(det > 0.0)) bad = true;
+      const double rdet = 1.0 / det;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) {
+          out[(int64_t)(j * DIM + m) * ne] = F[j][m];
+          out[(int64_t)(DIM * DIM + j * DIM + m) * ne] = C[j][m];
+        }
+      out[(int64_t)(2 * DIM * DIM) * ne] = 2.0 * mp.C1 * vT;
+      out[(int64_t)(2 * DIM * DIM + 1) * ne] = vT * (2.0 * mp.C1 * rdet * rdet + 2.0 * mp.D1);
+      out[(int64_t)(2 * DIM * DIM + 2) * ne] = vT * (2.0 * mp.D1 * delta - 2.0 * mp.C1 * rdet);
+    } else if constexpr (MODEL == FE_PLAPLACE_LP) {
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) {
+        const double x = fabs(H[0][m]);
+        double c;
+        if (mp.pcase == 2) c = 1.0;
+        else if (mp.pcase == 3) c = 2.0 * x;
+        else c = (x > 0.0) ? (mp.p - 1.0) * pow(x, mp.p - 2.0) : 0.0;
+        out[(int64_t)m * ne] = vT * c;
+      }
+    } else {
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) s = fma(H[0][m], H[0][m], s);
+      double c1, c2;
+      if (mp.pcase == 2) {
+        c1 = 1.0;
+        c2 = 0.0;
+      } else if (s > 0.0) {
+        c1 = (mp.pcase == 3) ? sqrt(s) : pow(s, 0.5 * (mp.p - 2.0));
+        c2 = (mp.p - 2.0) * c1 / s;
+      } else {
+        c1 = c2 = 0.0;
+      }
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) out[(int64_t)m * ne] = H[0][m];
+      out[(int64_t)DIM * ne] = c1;
+      out[(int64_t)(DIM + 1) * ne] = c2;
+      out[(int64_t)(DIM + 2) * ne] = vT;
+    }
+  }
+  if (bad) atomicOr(status, kStatusDomain);
+}
+
+template <int DIM, int D, int MODEL>
+__global__ void __launch_bounds__(kThreads) k_hvp_cached_f64(int64_t ne, const int32_t* __restrict__ elems,
+                                                             const double* __restrict__ dphi,
+                                                             const double* __restrict__ cache,
+                                                             const double* __restrict__ wd,
+                                                             const int32_t* __restrict__ slot,
+                                                             double* __restrict__ r, const int* skip) {
+  constexpr int K = DIM + 1;
+  if (skip && *skip) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
+    double wl[K][D];
+#pragma unroll
+    for (int l = 0; l < K; ++l) load_vec<D>(wd, __ldg(elems + (int64_t)l * ne + e), wl[l]);
+    double g[DIM][DIM];
+#pragma unroll
+    for (int l = 0; l < DIM; ++l)
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) g[l][m] = __ldg(dphi + ((int64_t)l * DIM + m) * ne + e);
+    double dF[D][DIM];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double b[DIM];
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) b[l] = wl[l + 1][j] - wl[0][j];
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) {
+        double t = b[0] * g[0][m];
+#pragma unroll
+        for (int l = 1; l < DIM; ++l) t = fma(b[l], g[l][m], t);
+        dF[j][m] = t;
+      }
+    }
+    const double* in = cache + e;
+    double dP[D][DIM];
+    if constexpr (MODEL == FE_NEOHOOKE) {
+      double F[DIM][DIM], C[DIM][DIM], dC[DIM][DIM];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) {
+          F[j][m] = __ldg(in + (int64_t)(j * DIM + m) * ne);
+          C[j][m] = __ldg(in + (int64_t)(DIM * DIM + j * DIM + m) * ne);
+        }
+      if constexpr (DIM == 3) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            const int r0 = j == 0 ? 1 : 0, r1 = j == 2 ? 1 : 2;
+            const int c0 = m == 0 ? 1 : 0, c1 = m == 2 ? 1 : 2;
+            const double dmn = dF[r0][c0] * F[r1][c1] + F[r0][c0] * dF[r1][c1] - dF[r0][c1] * F[r1][c0] -
+                               F[r0][c1] * dF[r1][c0];
+            const double sg = ((j + m) & 1) ? -1.0 : 1.0;
+            dC[j][m] = sg * dmn;
+          }
+      } else {
+        dC[0][0] = dF[1][1];
+        dC[0][1] = -dF[1][0];
+        dC[1][0] = -dF[0][1];
+        dC[1][1] = dF[0][0];
+      }
+      double cdf = 0.0;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) cdf = fma(C[j][m], dF[j][m], cdf);
+      const double a = __ldg(in + (int64_t)(2 * DIM * DIM) * ne);
+      const double bcoef = __ldg(in + (int64_t)(2 * DIM * DIM + 1) * ne) * cdf;
+      const double ccoef = __ldg(in + (int64_t)(2 * DIM * DIM + 2) * ne);
+#pragma unroll
+      for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) dP[j][m] = fma(a, dF[j][m], fma(bcoef, C[j][m], ccoef * dC[j][m]));
+    } else if constexpr (MODEL == FE_PLAPLACE_LP) {
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) dP[0][m] = __ldg(in + (int64_t)m * ne) * dF[0][m];
+    } else {
+      double H[DIM], hd = 0.0;
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) {
+        H[m] = __ldg(in + (int64_t)m * ne);
+        hd = fma(H[m], dF[0][m], hd);
+      }
+      const double c1 = __ldg(in + (int64_t)DIM * ne), c2 = __ldg(in + (int64_t)(DIM + 1) * ne);
+      const double vT = __ldg(in + (int64_t)(DIM + 2) * ne);
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) dP[0][m] = vT * fma(c1, dF[0][m], c2 * hd * H[m]);
+    }
+    double r0[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) r0[j] = 0.0;
+#pragma unroll
+    for (int l = 1; l <= DIM; ++l) {
+      const int64_t q = __ldg(slot + (int64_t)l * ne + e);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        double s = dP[j][0] * g[l - 1][0];
+#pragma unroll
+        for (int m = 1; m < DIM; ++m) s = fma(dP[j][m], g[l - 1][m], s);
+        r[q * D + j] = s;
+        r0[j] -= s;
+      }
+    }
+    const int64_t q0 = __ldg(slot + e);
+#pragma unroll
+    for (int j = 0; j < D; ++j) r[q0 * D + j] = r0[j];
+  }
+}
+
+template <int DIM, int D, int MODEL>
+fe_status hvp_prepare_t(fe_ctx* c, const double* v) {
+  fe_status st = launch_node_prep_f64(c, v);
+  if (st) return st;
+  if (c->ne > 0) {
+    k_hvp_prep_f64<DIM, D, MODEL><<<grid_for(c->ne, kMaxElemBlocks), kThreads, 0, c->stream>>>(
+        c->ne, c->elems, c->dphi, c->vol, c->u, model_params(c), c->hvp_cache, c->status);
+    c->launches++;
+  }
+  return cuda_check(cudaGetLastError(), "hessian-vector preparation");
+}
+
+template <int DIM, int D, int MODEL>
+fe_status hvp_cached_t(fe_ctx* c, const double* w, double* Hw, const int* skip) {
+  cudaStream_t s = c->stream;
+  k_w_prep<D><<<grid_for(c->nn, kMaxNodeBlocks), kThreads, 0, s>>>(c->nn, w, c->perm, c->dir, c->w_hvp, skip);
+  c->launches++;
+  if (c->ne > 0) {
+    k_hvp_cached_f64<DIM, D, MODEL><<<grid_for(c->ne, kMaxElemBlocks), kThreads, 0, s>>>(
+        c->ne, c->elems, c->dphi, c->hvp_cache, c->w_hvp, c->slot, c->r, skip);
+    c->launches++;
+  }
+  fe_status st = launch_gather_bulk<D, AccF64>(c, c->r, Hw, nullptr, skip);
+  if (st) return st;
+  c->launches++;
+  return cuda_check(cudaGetLastError(), "cached hessian-vector launch");
+}
+
 template <int DIM, int D, int MODEL>
 fe_status hvp_dir_t(fe_ctx* c, const double* w, double* Hw, const int* skip) {
   cudaStream_t s = c->stream;
@@ -237,6 +499,32 @@ fe_status launch_hvp_dir_f64(fe_ctx* c, const double* w, double* Hw, const int* 
   if (c->model == FE_PLAPLACE_LP)
     return c->dim == 2 ? hvp_dir_t<2, 1, FE_PLAPLACE_LP>(c, w, Hw, skip) : hvp_dir_t<3, 1, FE_PLAPLACE_LP>(c, w, Hw, skip);
   return c->dim == 2 ? hvp_dir_t<2, 1, FE_PLAPLACE>(c, w, Hw, skip) : hvp_dir_t<3, 1, FE_PLAPLACE>(c, w, Hw, skip);
+}
+
+// Sized by the components per node (not the model, which a scalar mesh may switch between
+// the two p-Laplacians): the widest cache of the models the mesh admits.
+size_t hvp_cache_doubles(const fe_ctx* c) {
+  const int dim = c->dim;
+  const int width = c->d > 1 ? 2 * dim * dim + 3 : dim + 3;
+  return (size_t)width * (size_t)c->ne;
+}
+
+fe_status launch_hvp_prepare_f64(fe_ctx* c, const double* v) {
+  if (c->model == FE_NEOHOOKE)
+    return c->dim == 2 ? hvp_prepare_t<2, 2, FE_NEOHOOKE>(c, v) : hvp_prepare_t<3, 3, FE_NEOHOOKE>(c, v);
+  if (c->model == FE_PLAPLACE_LP)
+    return c->dim == 2 ? hvp_prepare_t<2, 1, FE_PLAPLACE_LP>(c, v) : hvp_prepare_t<3, 1, FE_PLAPLACE_LP>(c, v);
+  return c->dim == 2 ? hvp_prepare_t<2, 1, FE_PLAPLACE>(c, v) : hvp_prepare_t<3, 1, FE_PLAPLACE>(c, v);
+}
+
+fe_status launch_hvp_cached_f64(fe_ctx* c, const double* w, double* Hw, const int* skip) {
+  if (c->model == FE_NEOHOOKE)
+    return c->dim == 2 ? hvp_cached_t<2, 2, FE_NEOHOOKE>(c, w, Hw, skip)
+                       : hvp_cached_t<3, 3, FE_NEOHOOKE>(c, w, Hw, skip);
+  if (c->model == FE_PLAPLACE_LP)
+    return c->dim == 2 ? hvp_cached_t<2, 1, FE_PLAPLACE_LP>(c, w, Hw, skip)
+                       : hvp_cached_t<3, 1, FE_PLAPLACE_LP>(c, w, Hw, skip);
+  return c->dim == 2 ? hvp_cached_t<2, 1, FE_PLAPLACE>(c, w, Hw, skip) : hvp_cached_t<3, 1, FE_PLAPLACE>(c, w, Hw, skip);
 }
 
 fe_status launch_hvp_f64(fe_ctx* c, const double* v, const double* w, double* Hw) {

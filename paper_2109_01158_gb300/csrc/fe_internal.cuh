@@ -111,6 +111,7 @@ struct fe_ctx {
   double* stage_v = nullptr;   // staging for the *_host call
   double* stage_g = nullptr;
   double* stage_J = nullptr;
+  double* hvp_cache = nullptr; // per-element terms of the Hessian at the CG solver's point
   double* cg_vec = nullptr;    // 3*nn*d: residual, direction and H direction of the CG solver
   double* cg_part = nullptr;   // 2*kMaxNodeBlocks partial sums of the CG solver
   unsigned* cg_ticket = nullptr;  // last-block ticket of the CG solver
@@ -153,6 +154,11 @@ fe_status launch_hvp_f64(fe_ctx* c, const double* v, const double* w, double* Hw
 // The product along w at the v last prepared by launch_node_prep_f64 (c->u); does nothing
 // when skip (nullable device flag) is nonzero.
 fe_status launch_hvp_dir_f64(fe_ctx* c, const double* w, double* Hw, const int* skip);
+// Products at a fixed point: prepare stores the v-dependent per-element terms in c->hvp_cache
+// (hvp_cache_doubles(c) doubles); cached computes Hw from them, bitwise as launch_hvp_f64.
+size_t hvp_cache_doubles(const fe_ctx* c);
+fe_status launch_hvp_prepare_f64(fe_ctx* c, const double* v);
+fe_status launch_hvp_cached_f64(fe_ctx* c, const double* w, double* Hw, const int* skip);
 // fe_cg.cu: Steihaug's CG on the device (buffers cg_* allocated by the caller).
 fe_status launch_cg_steihaug(fe_ctx* c, const double* v, const double* g, double radius, double tol, int max_cg,
                              double* z, double* Hz, int* iters, int* boundary);

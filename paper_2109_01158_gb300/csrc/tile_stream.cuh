@@ -15,9 +15,10 @@
 
 namespace fe {
 
-constexpr int kTile = 32;          // elements per tile = threads per block (one warp)
+constexpr int kTile = 32;                             // elements per tile = threads per block
 constexpr int kStages = 3;
-constexpr int kTileBlocks = 2432;  // fixed persistent grid (16 one-warp blocks on each of 152 SMs)
+constexpr int kTileMinBlocks = 20 * 32 / kTile;       // blocks per SM asked of the compiler: 20 warps
+constexpr int kTileBlocks = 152 * (512 / kTile);      // fixed persistent grid: 512 threads on each of 152 SMs
 
 template <int NARR>
 struct TileArrays {

@@ -143,3 +143,21 @@ def test_newton_with_device_cg_reaches_the_oracle_minimum(level):
                              cg=minimize.mesh_cg(gm))
     assert ref.converged and res.converged
     assert abs(res.J - ref.J) <= 1e-11 * abs(ref.J)
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_cached_products_equal_fe_hessian_vector(case):
+    """Inside the device CG the v-dependent terms of the Hessian are computed once per solve;
+    one CG step from z = 0 returns Hz = a H(-g), which must agree with fe_hessian_vector to
+    rounding."""
+    fem = _fem()
+    name, w = _cases()[case]
+    gm = fem.FEMesh.from_workload(w)
+    v = _dev(w.v)
+    _, g = gm.energy_gradient(v)
+    z, Hz, k, b = gm.cg_steihaug(v, g, 1e30, 0.0, 1)
+    assert (k, b) == (1, False)
+    i = int((-g).abs().argmax())
+    a = float(z[i] / (-g[i]))
+    ref = a * gm.hessian_vector(v, -g)
+    assert float((Hz - ref).abs().max()) <= 1e-14 * float(ref.abs().max()), name
