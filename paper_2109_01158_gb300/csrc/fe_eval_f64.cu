@@ -575,6 +575,102 @@ __global__ void __launch_bounds__(kThreads) k_elem_fd_f64(int64_t ne, const int3
   if (bad) atomicOr(status, kStatusDomain);
 }
 
+// Full mode, Neo-Hookean: the perturbation of row j of F by +-eps grad(phi_l) (the GG layer of
+// the dof (l, j), with grad(phi_0) = -sum_l grad(phi_l)) changes the terms of the displacement
+// form exactly as follows (det F is linear in each row, |H|^2 is quadratic):
+//   q  -> q + e (cof F - I)_j . grad(phi_l),   tr H -> tr H + e grad(phi_l)_j,
+//   |H|^2 -> |H|^2 + e (2 H_j . grad(phi_l) + e |grad(phi_l)|^2),   delta = tr H + q,
+// so each of the 2 (dim + 1) dim densities costs a few operations and one phi instead of a
+// full density.  (cof F - I) is formed from H without the 1 on its diagonal.  Writes
+// |T| (W+ - W-) / (2 eps) to the CSR position of (T, l), which the bulk gather sums over the
+// patch (the central difference of eq. CD restricted to the patch, eq. CDS).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_elem_fd_nh_f64(int64_t ne, const int32_t* __restrict__ elems,
+                                                             const double* __restrict__ dphi,
+                                                             const double* __restrict__ vol,
+                                                             const double* __restrict__ u,
+                                                             const int32_t* __restrict__ slot, ModelParams mp,
+                                                             double eps, double* __restrict__ r, int* status) {
+  bool bad = false;
+  const double inv2e = 1.0 / (2.0 * eps);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
+    double ul[DIM + 1][DIM], g[DIM][DIM], H[DIM][DIM];
+    element_state<DIM, DIM>(e, ne, elems, dphi, u, ul, g, H);
+    const double vT = __ldg(vol + e);
+    double tr = 0.0, hsq = 0.0, q, L[DIM][DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      tr += H[j][j];
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) hsq = fma(H[j][m], H[j][m], hsq);
+    }
+    if constexpr (DIM == 3) {
+      L[0][0] = H[1][1] + H[2][2] + (H[1][1] * H[2][2] - H[1][2] * H[2][1]);
+      L[1][1] = H[0][0] + H[2][2] + (H[0][0] * H[2][2] - H[0][2] * H[2][0]);
+      L[2][2] = H[0][0] + H[1][1] + (H[0][0] * H[1][1] - H[0][1] * H[1][0]);
+      L[0][1] = H[1][2] * H[2][0] - H[1][0] * (1.0 + H[2][2]);
+      L[0][2] = H[1][0] * H[2][1] - (1.0 + H[1][1]) * H[2][0];
+      L[1][0] = H[0][2] * H[2][1] - H[0][1] * (1.0 + H[2][2]);
+      L[1][2] = H[0][1] * H[2][0] - (1.0 + H[0][0]) * H[2][1];
+      L[2][0] = H[0][1] * H[1][2] - H[0][2] * (1.0 + H[1][1]);
+      L[2][1] = H[0][2] * H[1][0] - (1.0 + H[0][0]) * H[1][2];
+      const double M00 = H[1][1] * H[2][2] - H[1][2] * H[2][1];
+      q = M00 + H[0][0] * L[0][0] + H[0][1] * L[0][1] + H[0][2] * L[0][2];
+    } else {
+      L[0][0] = H[1][1];
+      L[1][1] = H[0][0];
+      L[0][1] = -H[1][0];
+      L[1][0] = -H[0][1];
+      q = H[0][0] * H[1][1] - H[0][1] * H[1][0];
+    }
+#pragma unroll
+    for (int lc = 0; lc <= DIM; ++lc) {
+      double gv[DIM];
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) {
+        if (lc > 0) {
+          gv[m] = g[lc - 1][m];
+        } else {
+          double t = 0.0;
+#pragma unroll
+          for (int l = 0; l < DIM; ++l) t -= g[l][m];
+          gv[m] = t;
+        }
+      }
+      double gg = 0.0;
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) gg = fma(gv[m], gv[m], gg);
+      const int64_t qs = __ldg(slot + (int64_t)lc * ne + e);
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        double lg = 0.0, hg = 0.0;
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) {
+          lg = fma(L[j][m], gv[m], lg);
+          hg = fma(H[j][m], gv[m], hg);
+        }
+        double Wpm[2];
+#pragma unroll
+        for (int sgn = 0; sgn < 2; ++sgn) {
+          const double ee = sgn == 0 ? eps : -eps;
+          const double qx = fma(ee, lg, q);
+          const double dl = fma(ee, gv[j], tr) + qx;
+          const double hs = fma(ee, fma(ee, gg, 2.0 * hg), hsq);
+          if (!(1.0 + dl > 0.0)) {
+            bad = true;
+            Wpm[sgn] = CUDART_INF;
+          } else {
+            Wpm[sgn] = mp.C1 * (hs - 2.0 * qx + 2.0 * phi_f64(dl)) + mp.D1 * dl * dl;
+          }
+        }
+        r[qs * DIM + j] = (vT * Wpm[0] - vT * Wpm[1]) * inv2e;
+      }
+    }
+  }
+  if (bad) atomicOr(status, kStatusDomain);
+}
+
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_gather_fd(int64_t nn, const int32_t* __restrict__ row_ptr,
                                                         const double* __restrict__ rp,
@@ -740,6 +836,19 @@ fe_status fd_t(fe_ctx* c, const double* v, double eps, double* g, const int64_t*
       prof_end(c, kStageFdGather);
       c->launches++;
     }
+  } else if constexpr (MODEL == FE_NEOHOOKE) {
+    if (c->ne > 0) {
+      prof_begin(c, kStageFdElem);
+      k_elem_fd_nh_f64<DIM><<<grid_for(c->ne, kMaxElemBlocks), kThreads, 0, s>>>(
+          c->ne, c->elems, c->dphi, c->vol, c->u, c->slot, mp, eps, c->r, c->status);
+      prof_end(c, kStageFdElem);
+      c->launches++;
+    }
+    prof_begin(c, kStageFdGather);
+    const fe_status gs = launch_gather_bulk<D, AccF64>(c, c->r, g);
+    prof_end(c, kStageFdGather);
+    if (gs) return gs;
+    c->launches++;
   } else {
     const int64_t nslot = c->ne * (DIM + 1) * D;
     if (c->ne > 0) {
@@ -810,7 +919,7 @@ fe_status launch_fd_f64(fe_ctx* c, const double* v, double eps, double* g, const
   int32_t* iperm = nullptr;
   cudaStream_t s = c->stream;
   fe_status st;
-  if (!dofs) {
+  if (!dofs && c->model != FE_NEOHOOKE) {
     const size_t bytes = sizeof(double) * 2 * (size_t)c->ne * (c->dim + 1) * c->d;
     if ((st = cuda_check(cudaMallocAsync((void**)&rfd, bytes > 0 ? bytes : 8, s), "alloc fd"))) return st;
   } else if (c->perm) {

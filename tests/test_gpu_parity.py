@@ -369,6 +369,25 @@ def test_c3_fd_subset_10k():
     check_grad(g, gex, rtol=1e-6, extra_abs=extra)
 
 
+def test_c3_fd_full_matches_subset_and_exact():
+    """3D Neo-Hookean 128^3x6: the central-difference gradient on every dof (full mode, which
+    updates the terms of the density per perturbed row) agrees with the subset mode (which
+    rebuilds each perturbed density) on 10^4 random free dofs, and with the exact gradient
+    within O(eps^2) + rounding."""
+    w = mg.neohooke_cube3d(128)
+    free = np.flatnonzero(w.dirichlet == 0)
+    dofs = free[np.sort(np.argsort(mg.splitmix64(3, np.arange(free.size)))[:10000])].astype(np.int64)
+    om = oracle.OracleMesh(w)
+    gm = _gpu(w)
+    v = _v(w)
+    full = gm.gradient_fd(v, 1e-6).cpu().numpy()
+    assert gm.sync_status() == 0
+    extra = fd_extra(om, w.v, 1e-6)
+    check_grad(full[dofs], gm.gradient_fd(v, 1e-6, dofs).cpu().numpy(), extra_abs=extra)
+    check_grad(full, gm.gradient_exact(v).cpu().numpy(), rtol=1e-6, extra_abs=extra)
+    assert np.all(full[w.dirichlet != 0] == 0.0)
+
+
 def test_fd_small_strain_matches_exact_gradient():
     """Near F = I (displacements of 1e-6, eps = 1e-7) the patch energies are evaluated in
     displacement form, so their rounding is relative to W, not to the O(1) terms of the
