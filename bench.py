@@ -409,6 +409,21 @@ def run_ours(args, rank, world, local):
     hms = e0.elapsed_time(e1) / nh
     variants["f64_hessian_vector"] = {"value": w.ne / (hms / 1e3) / 1e9, "unit": "Gelem/s", "ms_per_call": hms}
 
+    # one trust-region Newton step's inner solve: 50 Steihaug CG steps on the device (products
+    # from the per-solve cache of the Hessian terms at v), FP64
+    _, gv = gm.energy_gradient(v)
+    gm.cg_steihaug(v, gv, 1e30, 0.0, 5)
+    ncg = 50
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    _, _, kcg, _ = gm.cg_steihaug(v, gv, 1e30, 0.0, ncg)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    cms = e0.elapsed_time(e1)
+    variants["f64_cg_steihaug"] = {"value": w.ne * kcg / (cms / 1e3) / 1e9, "unit": "Gelem/s",
+                                   "ms_per_cg_step": cms / max(kcg, 1), "cg_steps": kcg,
+                                   "note": "products per second x elements; includes the per-solve preparation"}
+
     # the paper's central-difference gradient over patches (Sec. 6.1), every dof, FP64:
     # 2 (dim + 1) d density evaluations per element
     if gm.precision != fem.FE_F64:
