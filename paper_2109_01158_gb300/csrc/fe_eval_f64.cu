@@ -351,10 +351,10 @@ __global__ void __launch_bounds__(kThreads) k_elem_f64(
       // Displacement form of eq. neoHook with F = I + H (same value, no cancellation of O(1)
       // terms): delta = det F - 1 = tr H + q, q = i2(H) + det H, and
       //   I1 - dim - 2 log det F = |H|^2 - 2 q + 2 phi(delta),  phi(x) = x - log(1 + x).
-      double Fm[DIM][DIM], Cm[DIM][DIM], q, tr = 0.0, hsq = 0.0, X0 = 0.0;
+      double Fm[DIM][DIM], Cm[DIM][DIM], q, tr = H[0][0], hsq = 0.0, X0 = 0.0;
 #pragma unroll
       for (int j = 0; j < DIM; ++j) {
-        tr += H[j][j];
+        if (j > 0) tr += H[j][j];
 #pragma unroll
         for (int m = 0; m < DIM; ++m) {
           Fm[j][m] = (j == m) ? 1.0 + H[j][m] : H[j][m];
@@ -451,8 +451,6 @@ __global__ void __launch_bounds__(kThreads) k_elem_f64(
       // r_l = |T| P grad(phi_l) for l >= 1, r_0 = -sum_{l>=1} r_l (grad(phi_0) = -sum grad(phi_l))
       double r0[D];
 #pragma unroll
-      for (int j = 0; j < D; ++j) r0[j] = 0.0;
-#pragma unroll
       for (int l = 1; l <= DIM; ++l) {
         const int64_t q = __ldg(slot + (int64_t)l * ne + e);
 #pragma unroll
@@ -461,7 +459,7 @@ __global__ void __launch_bounds__(kThreads) k_elem_f64(
 #pragma unroll
           for (int m = 1; m < DIM; ++m) s = fma(P[j][m], g[l - 1][m], s);
           r[q * D + j] = s;
-          r0[j] -= s;
+          r0[j] = (l == 1) ? -s : r0[j] - s;   // (the first term needs no addition)
         }
       }
       const int64_t q0 = __ldg(slot + e);
@@ -598,10 +596,10 @@ __global__ void __launch_bounds__(kThreads) k_elem_fd_nh_f64(int64_t ne, const i
     double ul[DIM + 1][DIM], g[DIM][DIM], H[DIM][DIM];
     element_state<DIM, DIM>(e, ne, elems, dphi, u, ul, g, H);
     const double vT = __ldg(vol + e);
-    double tr = 0.0, hsq = 0.0, q, L[DIM][DIM];
+    double tr = H[0][0], hsq = 0.0, q, L[DIM][DIM];
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
-      tr += H[j][j];
+      if (j > 0) tr += H[j][j];
 #pragma unroll
       for (int m = 0; m < DIM; ++m) hsq = fma(H[j][m], H[j][m], hsq);
     }

@@ -191,8 +191,6 @@ __global__ void __launch_bounds__(kThreads) k_hvp_f64(int64_t ne, const int32_t*
     // local contributions dP grad(phi_l) (l >= 1); l = 0 gets minus their sum
     double r0[D];
 #pragma unroll
-    for (int j = 0; j < D; ++j) r0[j] = 0.0;
-#pragma unroll
     for (int l = 1; l <= DIM; ++l) {
       const int64_t q = __ldg(slot + (int64_t)l * ne + e);
 #pragma unroll
@@ -201,7 +199,7 @@ __global__ void __launch_bounds__(kThreads) k_hvp_f64(int64_t ne, const int32_t*
 #pragma unroll
         for (int m = 1; m < DIM; ++m) s = fma(dP[j][m], g[l - 1][m], s);
         r[q * D + j] = s;
-        r0[j] -= s;
+        r0[j] = (l == 1) ? -s : r0[j] - s;
       }
     }
     const int64_t q0 = __ldg(slot + e);
@@ -426,8 +424,6 @@ __global__ void __launch_bounds__(kThreads) k_hvp_cached_f64(int64_t ne, const i
     }
     double r0[D];
 #pragma unroll
-    for (int j = 0; j < D; ++j) r0[j] = 0.0;
-#pragma unroll
     for (int l = 1; l <= DIM; ++l) {
       const int64_t q = __ldg(slot + (int64_t)l * ne + e);
 #pragma unroll
@@ -436,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) k_hvp_cached_f64(int64_t ne, const i
 #pragma unroll
         for (int m = 1; m < DIM; ++m) s = fma(dP[j][m], g[l - 1][m], s);
         r[q * D + j] = s;
-        r0[j] -= s;
+        r0[j] = (l == 1) ? -s : r0[j] - s;
       }
     }
     const int64_t q0 = __ldg(slot + e);
