@@ -256,8 +256,6 @@ __device__ __forceinline__ df elem_df_one(int64_t e, int64_t ne, const int32_t* 
     if (GRAD) {
       df r0[D];
 #pragma unroll
-      for (int j = 0; j < D; ++j) r0[j] = {0.f, 0.f};
-#pragma unroll
       for (int l = 1; l <= DIM; ++l) {
         const int64_t q = __ldg(slot + (int64_t)l * ne + e);
 #pragma unroll
@@ -265,7 +263,7 @@ __device__ __forceinline__ df elem_df_one(int64_t e, int64_t ne, const int32_t* 
           const df s = (DIM == 3) ? df_dot3(P[j][0], g[l - 1][0], P[j][1], g[l - 1][1], P[j][DIM - 1], g[l - 1][DIM - 1])
                                   : df_dot2(P[j][0], g[l - 1][0], P[j][DIM - 1], g[l - 1][DIM - 1]);
           r[q * D + j] = make_float2(s.hi, s.lo);
-          r0[j] = df_sub(r0[j], s);
+          r0[j] = (l == 1) ? df_neg(s) : df_sub(r0[j], s);   // (the first term needs no addition)
         }
       }
       const int64_t q0 = __ldg(slot + e);

@@ -395,8 +395,6 @@ __global__ void __launch_bounds__(kTile, kTileMinBlocks) k_elem_f32(
     if (GRAD) {
       float r0[D];
 #pragma unroll
-      for (int j = 0; j < D; ++j) r0[j] = 0.f;
-#pragma unroll
       for (int l = 1; l <= DIM; ++l) {
         const int64_t q = tile_get<int32_t>(st, L, AR::kSlots + l, tid, 4);
 #pragma unroll
@@ -405,7 +403,7 @@ __global__ void __launch_bounds__(kTile, kTileMinBlocks) k_elem_f32(
 #pragma unroll
           for (int m = 1; m < DIM; ++m) s = fmaf(P[j][m], g[l - 1][m], s);
           r[q * D + j] = s;
-          r0[j] -= s;
+          r0[j] = (l == 1) ? -s : r0[j] - s;
         }
       }
       const int64_t q0 = tile_get<int32_t>(st, L, AR::kSlots, tid, 4);
