@@ -461,6 +461,8 @@ def run_ours(args, rank, world, local):
         line["serving"] = run_serving(args, local)
     if rank == 0 and args.minimize:
         line["minimize"] = run_minimize(args, local)
+    if rank == 0 and args.paper_tables:
+        line["paper_tables"] = run_paper_tables(args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ws = oracle_sample(w, args.sample_fraction)
         ts = time_oracle(ws, 2)
@@ -504,6 +506,52 @@ def run_serving(args, device):
         out["loads"].append(rec)
     server.close()
     return out
+
+
+# Tables 2 and 3 of the paper (twisted bar, levels 1-5): seconds for 10 evaluations on an
+# M1 in MATLAB -- energy; exact gradient; central-difference gradient.
+PAPER_TABLE2_10X = {1: 0.01, 2: 0.02, 3: 0.08, 4: 0.76, 5: 12.82}
+PAPER_TABLE3_EXACT_10X = {1: 0.12, 2: 0.14, 3: 1.18, 4: 12.47, 5: 487.34}
+PAPER_TABLE3_CD_10X = {1: 0.08, 2: 0.15, 3: 1.51, 4: 15.64, 5: 533.24}
+
+
+def run_paper_tables(args, device):
+    """The evaluations of Benchmarks 2 and 3 on their own meshes (the twisted bar, levels 1-5,
+    FP64): energy, exact gradient and central-difference gradient (eps = 1e-6), each timed
+    over 10 calls by events after warm-up, beside the paper's times for 10 evaluations."""
+    import torch
+    from paper_2109_01158_gb300 import fem
+    from paper_2109_01158_gb300 import meshgen as mg
+    dev = torch.device("cuda", device)
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for level in range(1, 6):
+        w = mg.twisted_bar(level)
+        gm = fem.FEMesh.from_workload(w, device=device)
+        v = torch.from_numpy(w.v).to(dev)
+        calls = {"energy": lambda: gm.energy(v), "gradient_exact": lambda: gm.gradient_exact(v),
+                 "gradient_cd": lambda: gm.gradient_fd(v, 1e-6)}
+        rec = {"level": level, "tets": w.ne, "free_dofs": int((w.dirichlet == 0).sum())}
+        for name, fn in calls.items():
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(10):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            rec[name + "_10x_s"] = e0.elapsed_time(e1) / 1e3
+        assert gm.sync_status() == fem.FE_OK
+        rec["J_grad"] = float(gm.energy(v).item()) if w.f is None else None
+        rec["paper_10x_s"] = {"energy": PAPER_TABLE2_10X[level], "gradient_exact": PAPER_TABLE3_EXACT_10X[level],
+                              "gradient_cd": PAPER_TABLE3_CD_10X[level]}
+        rows.append(rec)
+        del gm
+    return {"workload": "Benchmarks 2 and 3: twisted bar, 80*2^(L-1) x 2^L x 2^L hexes x 6 tets, FP64, "
+                        "10 calls each", "levels": rows,
+            "paper": "MATLAB R2021a on an M1 MacBook Air (Sec. 7.3); other hardware, context only"}
 
 
 def run_minimize(args, device):
@@ -653,6 +701,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-budget-gb", type=int, default=8)
     ap.add_argument("--minimize", action="store_true", help="also run the L-BFGS minimisation (64^3 x 6)")
+    ap.add_argument("--paper-tables", action="store_true",
+                    help="also time the energy and both gradients on the twisted bar, levels 1-5 (Tables 2 and 3)")
     ap.add_argument("--minimize-n", type=int, default=64)
     ap.add_argument("--minimize-iters", type=int, default=20000)
     args = ap.parse_args()
