@@ -71,13 +71,13 @@ __device__ __forceinline__ void finish_energy(double block_total, double* partia
 
 // ---- phi(x) = x - log(1 + x), x > -1 --------------------------------------------------------
 //
-// Breakpoints c_j = (j - FE_PHI_J0) / 256 with F_j = 1 + c_j (the table covers
-// [-76.5/256, 108.5/256); the kernels use it for |x| < 76.5/256): the nearest breakpoint
-// gives x = c_j + f with |f| <= 1/512 (exact: c_j is a multiple of 2^-8 within a factor 2
-// of x, Sterbenz' lemma), and with r = f / F_j
+// Breakpoints c_j = (j - FE_PHI_J0) / 1024 with F_j = 1 + c_j (the table covers
+// [-306/1024, 306/1024]; the kernels use it for |x| < 306/1024 = 76.5/256): the nearest
+// breakpoint gives x = c_j + f with |f| <= 1/2048 (exact: c_j is a multiple of 2^-10 within
+// a factor 2 of x, Sterbenz' lemma), and with r = f / F_j
 //   phi(x) = (c_j - ln F_j) + f (1 - 1/F_j) + (r - log1p(r)),
-//   r - log1p(r) = r^2 (1/2 - r/3 + r^2/4 - r^3/5 + r^4/6 - r^5/7 + r^6/8) + O(r^9),
-// |r| < 2.8e-3, so the truncation is below 2^-53 of the last term.  The three terms never
+//   r - log1p(r) = r^2 (1/2 - r/3 + r^2/4 - r^3/5 + r^4/6) + O(r^7),
+// |r| < 7.0e-4, so the truncation is below 2^-54 of r - log1p(r).  The three terms never
 // cancel by more than about a factor 4, the table holds c_j - ln F_j to twice double
 // precision (hi + lo), and there is no division.  Outside: x - log1p(x).
 #include "phi_table_f64.h"
@@ -103,7 +103,7 @@ struct PhiArg {
 };
 
 __device__ __forceinline__ PhiArg phi_arg(double x) {
-  // round(256 x) by the 1.5 * 2^52 shift: t = 1.5 * 2^52 + round(256 x) exactly
+  // round(FE_PHI_SCALE x) by the 1.5 * 2^52 shift: t = 1.5 * 2^52 + round(FE_PHI_SCALE x) exactly
   const double t = fma(x, (double)FE_PHI_SCALE, 0x1.8p52);
   int j = __double2loint(t) + FE_PHI_J0;
   j = min(max(j, 0), FE_PHI_N - 1);
@@ -118,9 +118,7 @@ __device__ __forceinline__ PhiArg phi_arg(double x) {
 
 __device__ __forceinline__ double phi_from(const PhiArg& a) {
   const double r = a.r;
-  double p = 1.0 / 8.0;
-  p = fma(p, r, -1.0 / 7.0);
-  p = fma(p, r, 1.0 / 6.0);
+  double p = 1.0 / 6.0;
   p = fma(p, r, -1.0 / 5.0);
   p = fma(p, r, 1.0 / 4.0);
   p = fma(p, r, -1.0 / 3.0);
@@ -135,13 +133,13 @@ __device__ __forceinline__ double phi_f64(double x) {
 }
 
 // 1/(1 + x) from the same row: inside the table 1 + x = F_j (1 + r), so
-// 1/(1 + x) = (1/F_j)(1 - r + r^2 - ... + r^6) (|r| < 2.8e-3: the next term is below
-// 2^-58 of the sum), which replaces a division.
+// 1/(1 + x) = (1/F_j)(1 - r + r^2 - ... - r^5) (|r| < 7.0e-4: the next term is below
+// 2^-62 of the sum), which replaces a division.
 __device__ __forceinline__ double rcp_from(const PhiArg& a) {
   const double r = a.r;
   double s = 1.0 - r;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) s = fma(-r, s, 1.0);
+  for (int k = 0; k < 4; ++k) s = fma(-r, s, 1.0);
   return a.BR.y * s;
 }
 

@@ -2,7 +2,7 @@
 """Writes phi_table_f64.h: the breakpoint table of phi(x) = x - log(1 + x) used by the FP64
 element kernels.
 
-Breakpoints c_j = (j - J0) / 256, j = 0 .. N - 1, cover x in [-76/256, 108/256].  For each
+Breakpoints c_j = (j - J0) / 1024, j = 0 .. N - 1, cover x in [-306/1024, 306/1024].  For each
 breakpoint, with F_j = 1 + c_j (exact dyadic rationals):
   A_j = c_j - ln(F_j)  (= phi(c_j))  as a pair of doubles hi + lo,
   B_j = c_j / F_j      (= 1 - 1/F_j) rounded to double,
@@ -15,9 +15,9 @@ from decimal import Decimal, getcontext
 
 getcontext().prec = 60
 
-SCALE = 256
-J0 = 76
-N = 185
+SCALE = 1024
+J0 = 306
+N = 613
 
 
 def split(d: Decimal):
