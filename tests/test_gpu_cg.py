@@ -161,3 +161,16 @@ def test_cached_products_equal_fe_hessian_vector(case):
     a = float(z[i] / (-g[i]))
     ref = a * gm.hessian_vector(v, -g)
     assert float((Hz - ref).abs().max()) <= 1e-14 * float(ref.abs().max()), name
+
+
+def test_device_cg_on_a_mesh_without_free_dofs():
+    """Every dof fixed: the gradient is 0, so the solve stops before any product."""
+    fem = _fem()
+    w = _lshape(1)
+    w.dirichlet[:] = 1
+    gm = fem.FEMesh.from_workload(w)
+    v = _dev(w.v)
+    _, g = gm.energy_gradient(v)
+    assert float(g.abs().max()) == 0.0
+    z, Hz, k, b = gm.cg_steihaug(v, g, 1.0, 0.0, 10)
+    assert (k, b) == (0, False) and float(z.abs().max()) == 0.0

@@ -114,3 +114,18 @@ def test_step_equals_update_then_direction():
     assert torch.equal(da, db) and gda == gdb
     a.close()
     b.close()
+
+
+def test_smallest_memory_and_one_unknown():
+    """n = 1 and m = 1: on f(x) = a x^2 / 2 the memory holds the exact curvature, so the
+    direction from any gradient is the Newton step -g / a; a second pair replaces the first."""
+    fem = _fem()
+    mem = fem.LbfgsMemory(1, 1)
+    a = 3.0
+    x0, x1, x2 = (torch.tensor([t], dtype=torch.float64, device="cuda") for t in (1.0, 0.5, 0.25))
+    assert mem.update(x1, x0, a * x1, a * x0) > 0.0 and mem.pairs() == 1
+    assert mem.update(x2, x1, a * x2, a * x1) > 0.0 and mem.pairs() == 1
+    g = torch.tensor([0.7], dtype=torch.float64, device="cuda")
+    d, gd = mem.direction(g)
+    assert abs(float(d[0]) + 0.7 / a) <= 1e-15 and abs(gd + 0.49 / a) <= 1e-15
+    mem.close()
