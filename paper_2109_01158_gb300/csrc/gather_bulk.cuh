@@ -14,7 +14,7 @@
 
 namespace fe {
 
-constexpr int kGatherWarps = 8;
+constexpr int kGatherWarps = 11;  // 11 x 20 KB = 220 KB of shared memory: one block per SM
 constexpr int kGatherCap = 20480;   // bytes of shared memory per warp
 constexpr int kGatherSmem = kGatherWarps * kGatherCap;
 
@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
   }
 }
 
-// Launch on the context stream: one block of 8 warps per SM (160 KB of shared memory each).
+// Launch on the context stream: one block of 11 warps per SM (220 KB of shared memory each;
+// 8 warps, 160 KB, were measured 13% slower on the FP64 gather of 128^3 x 6).
 // b: the load vector subtracted from the sums (the context's b unless given; nullptr = 0).
 // skip: nullptr, or a device flag; the launch does nothing when it is nonzero.
 template <int D, class Acc>
