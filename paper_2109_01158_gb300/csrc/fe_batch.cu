@@ -153,10 +153,11 @@ __global__ void __launch_bounds__(kBT) k_batch_elem(const BItem* __restrict__ it
 template <int D>
 __device__ __forceinline__ void gather_node(const BItem& it, int64_t i) {
   df s[D];
+  const int32_t q0 = it.row_ptr[i], q1 = it.row_ptr[i + 1];
+  // the first slot starts the sum (adding it to {0, 0} would return it unchanged)
 #pragma unroll
-  for (int j = 0; j < D; ++j) s[j] = {0.f, 0.f};
-  const int32_t q1 = it.row_ptr[i + 1];
-  for (int32_t q = it.row_ptr[i]; q < q1; ++q)
+  for (int j = 0; j < D; ++j) s[j] = (q1 > q0) ? ld_df(it.r, (int64_t)q0 * D + j) : df{0.f, 0.f};
+  for (int32_t q = q0 + 1; q < q1; ++q)
 #pragma unroll
     for (int j = 0; j < D; ++j) s[j] = df_add(s[j], ld_df(it.r, (int64_t)q * D + j));
   const int64_t dst = it.perm ? (int64_t)it.perm[i] : i;

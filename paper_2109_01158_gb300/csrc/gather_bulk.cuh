@@ -22,6 +22,7 @@ constexpr int kGatherSmem = kGatherWarps * kGatherCap;
 struct AccF64 {
   using T = double;
   double s = 0.0;
+  __device__ __forceinline__ void set(double x) { s = x; }
   __device__ __forceinline__ void add(double x) { s += x; }
   __device__ __forceinline__ double value() const { return s; }
 };
@@ -30,6 +31,7 @@ struct AccF64 {
 struct AccDF {
   using T = float2;
   df s = {0.f, 0.f};
+  __device__ __forceinline__ void set(float2 x) { s = df{x.x, x.y}; }
   __device__ __forceinline__ void add(float2 x) { s = df_add(s, df{x.x, x.y}); }
   __device__ __forceinline__ double value() const { return df_to_double(s); }
 };
@@ -38,6 +40,7 @@ struct AccDF {
 struct AccF32 {
   using T = float;
   float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void set(float x) { hi = x; }
   __device__ __forceinline__ void add(float x) {
     const df t = two_sum(hi, x);
     hi = t.hi;
@@ -109,13 +112,19 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
         for (int32_t t = 0; t < len; ++t) {
           const int64_t q = (int64_t)q0 + pos;
 #pragma unroll
-          for (int j = 0; j < D; ++j) acc[j].add(sbuf[q * D + j]);
+          for (int j = 0; j < D; ++j) {
+            if (t == 0) acc[j].set(sbuf[q * D + j]);   // (adding it to zero would return it unchanged)
+            else acc[j].add(sbuf[q * D + j]);
+          }
           pos = (pos + 1 == len) ? 0 : pos + 1;
         }
       } else {
         for (int32_t q = q0; q < q1; ++q)
 #pragma unroll
-          for (int j = 0; j < D; ++j) acc[j].add(__ldg(r + (int64_t)q * D + j));
+          for (int j = 0; j < D; ++j) {
+            if (q == q0) acc[j].set(__ldg(r + (int64_t)q * D + j));
+            else acc[j].add(__ldg(r + (int64_t)q * D + j));
+          }
       }
       const int64_t dst = perm ? (int64_t)__ldg(perm + i) : i;
 #pragma unroll
