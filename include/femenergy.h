@@ -76,6 +76,12 @@ typedef enum { FE_ORDER_NONE = 0, FE_ORDER_MORTON = 1 } fe_order;
  * precision instead of being rounded to the spacing of doubles near X. */
 typedef enum { FE_INPUT_DEFORMATION = 0, FE_INPUT_DISPLACEMENT = 1 } fe_input;
 
+/* Numbering of the dof vectors of the evaluation calls.  FE_VECTORS_CALLER (default): the
+ * caller's node numbering.  FE_VECTORS_DEVICE: the library's internal numbering (the Morton
+ * renumbering of FE_ORDER_MORTON; the same as the caller's with FE_ORDER_NONE), which skips
+ * the permutation on input and output -- for iterates that stay on the device. */
+typedef enum { FE_VECTORS_CALLER = 0, FE_VECTORS_DEVICE = 1 } fe_vector_order;
+
 /* Library version (major*10000 + minor*100 + patch). */
 int fe_version(void);
 
@@ -137,6 +143,19 @@ fe_status fe_set_precision(fe_ctx* ctx, int precision);
  * J = sum |T| W(I + grad u) - b.(X + u), with b.X formed once per load (Neumaier sum) and
  * b.u summed per call.  Any time after fe_create; FE_EINVAL for another value. */
 fe_status fe_set_input(fe_ctx* ctx, int input);
+
+/* Order of the dof vectors (fe_vector_order) of fe_energy, fe_gradient_exact,
+ * fe_energy_gradient, fe_energy_gradient_host, fe_gradient_fd (also of its dof subset),
+ * fe_hessian_vector and fe_cg_steihaug.  The batched calls and the server always use the
+ * caller's order.  Any time after fe_create; FE_EINVAL for another value. */
+fe_status fe_set_vector_order(fe_ctx* ctx, int order);
+
+/* Permute a dof vector between the caller's numbering (x_dev) and the device numbering
+ * (y_dev): y[d*i + j] = x[d*perm(i) + j] with perm the device -> caller node map of the
+ * uploaded mesh.  n_nodes*d doubles each, device memory, on the context's stream; the two
+ * must not overlap (FE_EINVAL if they are the same pointer).  Needs a mesh. */
+fe_status fe_to_device_order(fe_ctx* ctx, const double* x_dev, double* y_dev);
+fe_status fe_from_device_order(fe_ctx* ctx, const double* y_dev, double* x_dev);
 
 /* Device bytes held by the context (mesh, precompute and work buffers). */
 fe_status fe_footprint(const fe_ctx* ctx, size_t* bytes);

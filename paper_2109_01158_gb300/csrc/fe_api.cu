@@ -497,6 +497,50 @@ fe_status fe_hessian_vector(fe_ctx* c, const double* v, const double* w, double*
   return launch_hvp_f64(c, v, w, Hw);
 }
 
+namespace fe {
+namespace {
+// Dof vectors between the caller's numbering and the device numbering (perm: device -> caller).
+__global__ void __launch_bounds__(kThreads) k_permute_dofs(int64_t nn, int d, const int32_t* __restrict__ perm,
+                                                           const double* __restrict__ in, double* __restrict__ out,
+                                                           bool to_device) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
+    const int64_t p = perm[i];
+    for (int j = 0; j < d; ++j) {
+      if (to_device) out[i * d + j] = in[p * d + j];
+      else out[p * d + j] = in[i * d + j];
+    }
+  }
+}
+}  // namespace
+}  // namespace fe
+
+fe_status fe_set_vector_order(fe_ctx* c, int order) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  if (order != FE_VECTORS_CALLER && order != FE_VECTORS_DEVICE) return set_error(FE_EINVAL, "unknown vector order");
+  c->vector_order = order;
+  return FE_OK;
+}
+
+static fe_status permute_dofs(fe_ctx* c, const double* in, double* out, bool to_device) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  if (!c->have_mesh) return set_error(FE_EINVAL, "no mesh uploaded");
+  if (!in || !out) return set_error(FE_EINVAL, "null vector");
+  if (in == out) return set_error(FE_EINVAL, "the two vectors must not overlap");
+  DeviceGuard g(c->device);
+  const int64_t n = c->nn * c->d;
+  if (!c->perm)
+    return cuda_check(cudaMemcpyAsync(out, in, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, c->stream),
+                      "vector copy");
+  k_permute_dofs<<<grid_for(c->nn, kMaxNodeBlocks), kThreads, 0, c->stream>>>(c->nn, c->d, c->perm, in, out,
+                                                                                 to_device);
+  c->launches++;
+  return cuda_check(cudaGetLastError(), "vector permutation");
+}
+
+fe_status fe_to_device_order(fe_ctx* c, const double* x, double* y) { return permute_dofs(c, x, y, true); }
+fe_status fe_from_device_order(fe_ctx* c, const double* y, double* x) { return permute_dofs(c, y, x, false); }
+
 fe_status fe_cg_steihaug(fe_ctx* c, const double* v, const double* g, double radius, double tol, int max_cg,
                          double* z, double* Hz, int* iters, int* boundary) {
   fe_status st = check_ready(c);

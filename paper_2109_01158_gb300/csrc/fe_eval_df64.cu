@@ -180,7 +180,7 @@ fe_status evaldf_t(fe_ctx* c, const double* v, double* J, double* dens, double* 
   const int nb_elem = grid_for(c->ne, kMaxElemBlocks);
   double* node_partials = c->partials + kMaxElemBlocks;
   prof_begin(c, kStagePrep);
-  k_node_prep_df<D, MODEL == FE_NEOHOOKE, DIM><<<nb_node, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b,
+  k_node_prep_df<D, MODEL == FE_NEOHOOKE, DIM><<<nb_node, kThreads, 0, s>>>(c->nn, v, c->X, io_perm(c), c->b,
                                                                             c->u_df, node_partials, input_is_disp(c),
                                                                             input_is_disp(c) ? c->bX : 0.0);
   prof_end(c, kStagePrep);

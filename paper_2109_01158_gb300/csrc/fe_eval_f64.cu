@@ -689,7 +689,7 @@ fe_status eval_t(fe_ctx* c, const double* v, double* J, double* dens, double* g,
   const int nb_elem = grid_for(c->ne, kMaxElemBlocks);
   double* node_partials = c->partials + kMaxElemBlocks;
   prof_begin(c, kStagePrep);
-  k_node_prep<D, MODEL == FE_NEOHOOKE, DIM><<<nb_node, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b,
+  k_node_prep<D, MODEL == FE_NEOHOOKE, DIM><<<nb_node, kThreads, 0, s>>>(c->nn, v, c->X, io_perm(c), c->b,
                                                                          c->u, node_partials, input_is_disp(c),
                                                                          input_is_disp(c) ? c->bX : 0.0);
   prof_end(c, kStagePrep);
@@ -730,7 +730,7 @@ fe_status fd_t(fe_ctx* c, const double* v, double eps, double* g, const int64_t*
   const int nb_node = grid_for(c->nn, kMaxNodeBlocks);
   prof_begin(c, kStagePrep);
   k_node_prep<D, MODEL == FE_NEOHOOKE, DIM><<<nb_node, kThreads, 0, s>>>(
-      c->nn, v, c->X, c->perm, c->b, c->u, c->partials + kMaxElemBlocks, input_is_disp(c),
+      c->nn, v, c->X, io_perm(c), c->b, c->u, c->partials + kMaxElemBlocks, input_is_disp(c),
       input_is_disp(c) ? c->bX : 0.0);
   prof_end(c, kStagePrep);
   c->launches++;
@@ -767,7 +767,7 @@ fe_status fd_t(fe_ctx* c, const double* v, double eps, double* g, const int64_t*
     }
     prof_begin(c, kStageFdGather);
     k_gather_fd<D><<<grid_for(c->nn, 4 * kMaxNodeBlocks), kThreads, 0, s>>>(
-        c->nn, c->row_ptr, rfd, rfd + nslot, eps, c->b, c->dir, c->perm, g);
+        c->nn, c->row_ptr, rfd, rfd + nslot, eps, c->b, c->dir, io_perm(c), g);
     prof_end(c, kStageFdGather);
     c->launches++;
   }
@@ -810,11 +810,11 @@ fe_status launch_node_prep_f64(fe_ctx* c, const double* v) {
   const double sh = disp ? c->bX : 0.0;
   cudaStream_t s = c->stream;
   if (c->model == FE_NEOHOOKE) {
-    if (c->dim == 2) k_node_prep<2, true, 2><<<nb, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b, c->u, np, disp, sh);
-    else k_node_prep<3, true, 3><<<nb, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b, c->u, np, disp, sh);
+    if (c->dim == 2) k_node_prep<2, true, 2><<<nb, kThreads, 0, s>>>(c->nn, v, c->X, io_perm(c), c->b, c->u, np, disp, sh);
+    else k_node_prep<3, true, 3><<<nb, kThreads, 0, s>>>(c->nn, v, c->X, io_perm(c), c->b, c->u, np, disp, sh);
   } else {
-    if (c->dim == 2) k_node_prep<1, false, 2><<<nb, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b, c->u, np, false, 0.0);
-    else k_node_prep<1, false, 3><<<nb, kThreads, 0, s>>>(c->nn, v, c->X, c->perm, c->b, c->u, np, false, 0.0);
+    if (c->dim == 2) k_node_prep<1, false, 2><<<nb, kThreads, 0, s>>>(c->nn, v, c->X, io_perm(c), c->b, c->u, np, false, 0.0);
+    else k_node_prep<1, false, 3><<<nb, kThreads, 0, s>>>(c->nn, v, c->X, io_perm(c), c->b, c->u, np, false, 0.0);
   }
   c->launches++;
   return cuda_check(cudaGetLastError(), "node preparation");
@@ -829,7 +829,7 @@ fe_status launch_fd_f64(fe_ctx* c, const double* v, double eps, double* g, const
   if (!dofs && c->model != FE_NEOHOOKE) {
     const size_t bytes = sizeof(double) * 2 * (size_t)c->ne * (c->dim + 1) * c->d;
     if ((st = cuda_check(cudaMallocAsync((void**)&rfd, bytes > 0 ? bytes : 8, s), "alloc fd"))) return st;
-  } else if (c->perm) {
+  } else if (io_perm(c)) {
     if ((st = cuda_check(cudaMallocAsync((void**)&iperm, sizeof(int32_t) * c->nn, s), "alloc iperm")))
       return st;
     std::vector<int32_t> ip(c->nn);

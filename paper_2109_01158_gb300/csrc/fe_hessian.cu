@@ -456,7 +456,7 @@ fe_status hvp_prepare_t(fe_ctx* c, const double* v) {
 template <int DIM, int D, int MODEL>
 fe_status hvp_cached_t(fe_ctx* c, const double* w, double* Hw, const int* skip) {
   cudaStream_t s = c->stream;
-  k_w_prep<D><<<grid_for(c->nn, kMaxNodeBlocks), kThreads, 0, s>>>(c->nn, w, c->perm, c->dir, c->w_hvp, skip);
+  k_w_prep<D><<<grid_for(c->nn, kMaxNodeBlocks), kThreads, 0, s>>>(c->nn, w, io_perm(c), c->dir, c->w_hvp, skip);
   c->launches++;
   if (c->ne > 0) {
     k_hvp_cached_f64<DIM, D, MODEL><<<grid_for(c->ne, kMaxElemBlocks), kThreads, 0, s>>>(
@@ -474,7 +474,7 @@ fe_status hvp_dir_t(fe_ctx* c, const double* w, double* Hw, const int* skip) {
   cudaStream_t s = c->stream;
   const ModelParams mp = model_params(c);
   const int nb_node = grid_for(c->nn, kMaxNodeBlocks);
-  k_w_prep<D><<<nb_node, kThreads, 0, s>>>(c->nn, w, c->perm, c->dir, c->w_hvp, skip);
+  k_w_prep<D><<<nb_node, kThreads, 0, s>>>(c->nn, w, io_perm(c), c->dir, c->w_hvp, skip);
   c->launches++;
   if (c->ne > 0) {
     k_hvp_f64<DIM, D, MODEL><<<grid_for(c->ne, kMaxElemBlocks), kThreads, 0, s>>>(

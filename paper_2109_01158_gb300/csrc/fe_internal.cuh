@@ -73,6 +73,7 @@ struct fe_ctx {
   double p = 2.0, C1 = 0.0, D1 = 0.0;
   bool model_set = false;
   int input = FE_INPUT_DEFORMATION;  // meaning of the v argument of the evaluation calls
+  int vector_order = FE_VECTORS_CALLER;  // numbering of the dof vectors of the evaluation calls
   double bX = 0.0;              // b.X (Neo-Hookean), added to b.u when v is a displacement
   std::vector<double> f_host;   // load in the caller's dof order (empty = 0)
   std::vector<int32_t> perm_h;  // device node -> caller node (empty = identity)
@@ -130,6 +131,12 @@ struct fe_ctx {
 // True when the v argument of an evaluation is the Neo-Hookean displacement u = v - X.
 inline bool input_is_disp(const fe_ctx* c) {
   return c->model == FE_NEOHOOKE && c->input == FE_INPUT_DISPLACEMENT;
+}
+
+// The permutation (device node -> caller node) applied to the dof vectors of the evaluation
+// calls: the mesh's, or none when the caller works in the device numbering.
+inline const int32_t* io_perm(const fe_ctx* c) {
+  return c->vector_order == FE_VECTORS_DEVICE ? nullptr : c->perm;
 }
 
 

@@ -158,7 +158,7 @@ inline fe_status launch_gather_bulk(fe_ctx* c, const typename Acc::T* r, double*
   if (blocks > sms) blocks = sms;
   if (blocks < 1) blocks = 1;
   k_gather_bulk<D, Acc><<<(unsigned)blocks, kGatherWarps * 32, kGatherSmem, c->stream>>>(
-      c->nn, c->row_ptr, r, b, c->dir, c->perm, g, c->status, skip);
+      c->nn, c->row_ptr, r, b, c->dir, io_perm(c), g, c->status, skip);
   return cuda_check(cudaGetLastError(), "gather launch");
 }
 

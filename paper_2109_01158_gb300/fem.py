@@ -22,6 +22,7 @@ FE_PLAPLACE, FE_NEOHOOKE, FE_PLAPLACE_LP = 0, 1, 2
 FE_F64, FE_F32_COMP, FE_DF64 = 0, 1, 2
 FE_ORDER_NONE, FE_ORDER_MORTON = 0, 1
 FE_INPUT_DEFORMATION, FE_INPUT_DISPLACEMENT = 0, 1
+FE_VECTORS_CALLER, FE_VECTORS_DEVICE = 0, 1
 
 _STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "FE_EDOMAIN",
                  5: "FE_ETIMEOUT", 6: "FE_EBUSY"}
@@ -53,6 +54,9 @@ _SIGNATURES = {
     "fe_precompute": [_vp, ctypes.c_uint],
     "fe_set_precision": [_vp, _int],
     "fe_set_input": [_vp, _int],
+    "fe_set_vector_order": [_vp, _int],
+    "fe_to_device_order": [_vp, _vp, _vp],
+    "fe_from_device_order": [_vp, _vp, _vp],
     "fe_footprint": [_vp, _vp],
     "fe_energy": [_vp, _vp, _vp, _vp],
     "fe_gradient_exact": [_vp, _vp, _vp],
@@ -147,6 +151,9 @@ fe_set_load = _checked("fe_set_load")
 fe_precompute = _checked("fe_precompute")
 fe_set_precision = _checked("fe_set_precision")
 fe_set_input = _checked("fe_set_input")
+fe_set_vector_order = _checked("fe_set_vector_order")
+fe_to_device_order = _checked("fe_to_device_order")
+fe_from_device_order = _checked("fe_from_device_order")
 fe_footprint = _checked("fe_footprint")
 fe_energy = _checked("fe_energy")
 fe_gradient_exact = _checked("fe_gradient_exact")
@@ -454,6 +461,28 @@ class FEMesh:
     def set_precision(self, prec):
         fe_set_precision(self.ctx, int(prec))
         self.precision = int(prec)
+
+    def set_vector_order(self, order):
+        """FE_VECTORS_CALLER (default) or FE_VECTORS_DEVICE: the numbering of the dof vectors of
+        the evaluation, Hessian-vector, CG and central-difference calls."""
+        fe_set_vector_order(self.ctx, int(order))
+        self.vector_order = int(order)
+
+    def to_device_order(self, x, out=None):
+        """A dof vector in the caller's numbering -> the device numbering."""
+        x = self._vec(x)
+        self._sync_stream()
+        y = out if out is not None else torch.empty_like(x)
+        fe_to_device_order(self.ctx, _ptr(x), _ptr(y))
+        return y
+
+    def from_device_order(self, y, out=None):
+        """A dof vector in the device numbering -> the caller's numbering."""
+        y = self._vec(y)
+        self._sync_stream()
+        x = out if out is not None else torch.empty_like(y)
+        fe_from_device_order(self.ctx, _ptr(y), _ptr(x))
+        return x
 
     def set_input(self, kind):
         """FE_INPUT_DEFORMATION (v = X + u, default) or FE_INPUT_DISPLACEMENT (v = u)."""
