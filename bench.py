@@ -409,6 +409,22 @@ def run_ours(args, rank, world, local):
     hms = e0.elapsed_time(e1) / nh
     variants["f64_hessian_vector"] = {"value": w.ne / (hms / 1e3) / 1e9, "unit": "Gelem/s", "ms_per_call": hms}
 
+    # the energy alone (the forward of the autograd function; Table 2 times this), FP64
+    if gm.precision != fem.FE_F64:
+        gm.set_precision(fem.FE_F64)
+    for _ in range(3):
+        gm.energy(v)
+    ne_steps = max(5, args.steps // 4)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(ne_steps):
+        gm.energy(v)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ems = e0.elapsed_time(e1) / ne_steps
+    variants["f64_energy"] = {"value": w.ne / (ems / 1e3) / 1e9, "unit": "Gelem/s", "ms_per_call": ems}
+    gm.set_precision(code[prec])
+
     # one trust-region Newton step's inner solve: 50 Steihaug CG steps on the device (products
     # from the per-solve cache of the Hessian terms at v), FP64
     _, gv = gm.energy_gradient(v)
