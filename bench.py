@@ -54,6 +54,7 @@ F64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 # DRAM traffic of the element kernels per launch, from an ncu capture (profiles/): valid only
 # while the kernel's sources hash to the value recorded with the capture.
+ORDER_NAMES = {0: "as generated", 1: "Morton", 2: "reverse Cuthill-McKee"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 L2_BYTES = 129 << 20        # GB300 L2 (for the flush decision)
 FLUSH_BYTES = 256 << 20     # a write of this size evicts L2
@@ -464,7 +465,7 @@ def run_ours(args, rank, world, local):
         "metric": "energy+grad throughput", "value": value, "unit": "Gelem/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
-        "config": dict(workload_config(w, prec), node_order="Morton" if args.order == 1 else "as generated",
+        "config": dict(workload_config(w, prec), node_order=ORDER_NAMES[args.order],
                        **({"l2": "L2 evicted before every timed step (256 MB write, not timed)"} if flush else {})),
         "roofline": roof,
         "step_hbm": {"algorithmic_bytes": step_bytes,
@@ -706,7 +707,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="C3")
     ap.add_argument("--precision", choices=["f64", "f32", "df64"], default="f64")
-    ap.add_argument("--order", type=int, default=0, help="0 generator order, 1 Morton")
+    ap.add_argument("--order", type=int, default=0, choices=(0, 1, 2),
+                    help="internal node order: 0 as generated, 1 Morton, 2 reverse Cuthill-McKee")
     ap.add_argument("--flush-l2", action="store_true",
                     help="evict L2 before every timed step (automatic when a step's inputs are < 2 x L2)")
     ap.add_argument("--shuffle-nodes", action="store_true",

@@ -66,8 +66,12 @@ typedef enum { FE_PLAPLACE = 0, FE_NEOHOOKE = 1, FE_PLAPLACE_LP = 2 } fe_model;
  * for values within about 1e-30..1e30 in magnitude. */
 typedef enum { FE_F64 = 0, FE_F32_COMP = 1, FE_DF64 = 2 } fe_precision;
 
-/* Internal node/element numbering used for the device layout (invisible to callers). */
-typedef enum { FE_ORDER_NONE = 0, FE_ORDER_MORTON = 1 } fe_order;
+/* Internal node/element numbering used for the device layout (invisible to callers).
+ * FE_ORDER_MORTON sorts nodes along a Morton (Z-order) curve of their coordinates;
+ * FE_ORDER_RCM is the reverse Cuthill-McKee numbering of the node graph (nodes adjacent when
+ * they share an element), which keeps the index distance between neighbours small.  Both
+ * then sort the elements by their least renumbered node. */
+typedef enum { FE_ORDER_NONE = 0, FE_ORDER_MORTON = 1, FE_ORDER_RCM = 2 } fe_order;
 
 /* Meaning of the vector v passed to the evaluation calls.  FE_INPUT_DEFORMATION: v is the
  * deformation (the paper's unknown, Sec. 3), v = X + u for the Neo-Hookean model.
@@ -77,8 +81,9 @@ typedef enum { FE_ORDER_NONE = 0, FE_ORDER_MORTON = 1 } fe_order;
 typedef enum { FE_INPUT_DEFORMATION = 0, FE_INPUT_DISPLACEMENT = 1 } fe_input;
 
 /* Numbering of the dof vectors of the evaluation calls.  FE_VECTORS_CALLER (default): the
- * caller's node numbering.  FE_VECTORS_DEVICE: the library's internal numbering (the Morton
- * renumbering of FE_ORDER_MORTON; the same as the caller's with FE_ORDER_NONE), which skips
+ * caller's node numbering.  FE_VECTORS_DEVICE: the library's internal numbering (the
+ * renumbering of FE_ORDER_MORTON or FE_ORDER_RCM; the same as the caller's with
+ * FE_ORDER_NONE), which skips
  * the permutation on input and output -- for iterates that stay on the device. */
 typedef enum { FE_VECTORS_CALLER = 0, FE_VECTORS_DEVICE = 1 } fe_vector_order;
 
@@ -87,6 +92,13 @@ int fe_version(void);
 
 /* Message describing the last failing call on this thread (owned by the library). */
 const char* fe_last_error(void);
+
+/* The node renumbering that fe_mesh_upload applies for `order`, computed on the host
+ * (no context, no device work).  The mesh arguments are those of fe_mesh_upload and are
+ * validated the same way.  perm_out (n_nodes int32, caller-owned) receives perm[new] = old:
+ * the identity for FE_ORDER_NONE.  FE_EINVAL on a malformed mesh or a bad order. */
+fe_status fe_node_order(int dim, int64_t n_nodes, const double* coords_host, int64_t n_elems,
+                        const int32_t* elems_host, int order, int32_t* perm_out);
 
 /* Create a context on CUDA device `device` that enqueues all work on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  *out receives the context. */
@@ -105,9 +117,9 @@ fe_status fe_set_stream(fe_ctx* ctx, void* cuda_stream);
  *   n_elems    |T|;  elems_host:  n_elems*(dim+1) int32 node ids in [0, n_nodes)
  *   dirichlet_host: n_nodes*d bytes, 1 = fixed dof (dofsDirichlet), 0 = free (dofsMinim);
  *                   NULL = every dof free
- *   order      FE_ORDER_NONE keeps the caller's numbering; FE_ORDER_MORTON renumbers nodes
- *              along a Morton curve and sorts elements by their first renumbered node so
- *              that the gathers of v hit L2
+ *   order      FE_ORDER_NONE keeps the caller's numbering; FE_ORDER_MORTON (Morton curve) and
+ *              FE_ORDER_RCM (reverse Cuthill-McKee) renumber the nodes and sort elements by
+ *              their first renumbered node so that the gathers of v hit L2
  * Validates ids and sizes (n_elems*(dim+1) < 2^31).  Replaces any previous mesh and
  * invalidates the precompute.  FE_EINVAL on a malformed mesh. */
 fe_status fe_mesh_upload(fe_ctx* ctx, int dim, int d, int64_t n_nodes,

@@ -163,6 +163,146 @@ std::vector<int32_t> morton_order(int dim, int64_t nn, const double* X) {
   return perm;
 }
 
+// Node adjacency of a P1 mesh (two nodes are adjacent when they share an element), as a
+// CSR whose rows are sorted and free of duplicates.
+void node_graph(int k, int64_t nn, int64_t ne, const int32_t* elems, std::vector<int64_t>& ptr,
+                std::vector<int32_t>& adj) {
+  ptr.assign(nn + 1, 0);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int l = 0; l < k; ++l) ptr[elems[e * k + l] + 1] += k - 1;
+  for (int64_t i = 0; i < nn; ++i) ptr[i + 1] += ptr[i];
+  adj.resize(ptr[nn]);
+  std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int l = 0; l < k; ++l)
+      for (int m = 0; m < k; ++m)
+        if (m != l) adj[fill[elems[e * k + l]]++] = elems[e * k + m];
+  // sort and deduplicate each row, compacting in place
+  int64_t out = 0;
+  for (int64_t i = 0; i < nn; ++i) {
+    const int64_t b = ptr[i], end = ptr[i + 1];
+    std::sort(adj.begin() + b, adj.begin() + end);
+    const int64_t start = out;
+    for (int64_t q = b; q < end; ++q)
+      if (q == b || adj[q] != adj[q - 1]) adj[out++] = adj[q];
+    ptr[i] = start;
+  }
+  ptr[nn] = out;
+  adj.resize(out);
+}
+
+// Reverse Cuthill-McKee renumbering of the node graph (Cuthill & McKee 1969; reversed as
+// proposed by George 1971); perm[new] = old.  Each connected component is numbered from a
+// pseudo-peripheral node (George & Liu: restart the level structure from a node of least
+// degree in its last level while its depth grows), visiting the unnumbered neighbours of
+// each node in order of increasing degree (ties by id); the whole sequence is then reversed.
+// Components are taken in order of their least-degree, least-id node.
+std::vector<int32_t> rcm_order(int k, int64_t nn, int64_t ne, const int32_t* elems) {
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> adj;
+  node_graph(k, nn, ne, elems, ptr, adj);
+  auto deg = [&](int32_t i) { return ptr[i + 1] - ptr[i]; };
+  auto by_degree = [&](int32_t a, int32_t b) {
+    return deg(a) != deg(b) ? deg(a) < deg(b) : a < b;
+  };
+  std::vector<int32_t> seeds(nn);
+  std::iota(seeds.begin(), seeds.end(), 0);
+  std::stable_sort(seeds.begin(), seeds.end(), by_degree);
+
+  std::vector<int32_t> order;
+  order.reserve(nn);
+  std::vector<uint8_t> numbered(nn, 0);
+  std::vector<int32_t> stamp(nn, -1), queue;
+  int32_t bfs_id = 0;
+  // Level structure rooted at r within r's component: returns its depth and a node of
+  // least degree (then least id) in its last level.
+  auto levels = [&](int32_t r, int32_t* last_min) {
+    ++bfs_id;
+    queue.assign(1, r);
+    stamp[r] = bfs_id;
+    int depth = 0;
+    size_t head = 0;
+    while (true) {
+      const size_t level_end = queue.size();
+      int32_t best = queue[head];
+      for (size_t q = head; q < level_end; ++q) {
+        if (by_degree(queue[q], best)) best = queue[q];
+        const int32_t u = queue[q];
+        for (int64_t a = ptr[u]; a < ptr[u + 1]; ++a)
+          if (stamp[adj[a]] != bfs_id) {
+            stamp[adj[a]] = bfs_id;
+            queue.push_back(adj[a]);
+          }
+      }
+      if (queue.size() == level_end) {
+        *last_min = best;
+        return depth;
+      }
+      head = level_end;
+      ++depth;
+    }
+  };
+  std::vector<int32_t> nb;
+  for (int32_t s0 : seeds) {
+    if (numbered[s0]) continue;
+    int32_t root = s0, cand;
+    int depth = levels(root, &cand);
+    for (int it = 0; it < 16 && cand != root; ++it) {
+      int32_t next;
+      const int dc = levels(cand, &next);
+      if (dc <= depth) break;
+      root = cand;
+      depth = dc;
+      cand = next;
+    }
+    size_t head = order.size();
+    order.push_back(root);
+    numbered[root] = 1;
+    while (head < order.size()) {
+      const int32_t u = order[head++];
+      nb.clear();
+      for (int64_t a = ptr[u]; a < ptr[u + 1]; ++a)
+        if (!numbered[adj[a]]) {
+          numbered[adj[a]] = 1;
+          nb.push_back(adj[a]);
+        }
+      std::sort(nb.begin(), nb.end(), by_degree);
+      order.insert(order.end(), nb.begin(), nb.end());
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  return order;
+}
+
+// Checks shared by fe_mesh_upload and fe_node_order.
+fe_status check_mesh(int dim, int64_t nn, const double* coords, int64_t ne, const int32_t* elems,
+                     int order) {
+  if (dim != 2 && dim != 3) return set_error(FE_EINVAL, "dim must be 2 or 3");
+  if (nn < 0 || ne < 0) return set_error(FE_EINVAL, "negative size");
+  if (nn >= (int64_t)1 << 31 || ne * (dim + 1) >= (int64_t)1 << 31)
+    return set_error(FE_EINVAL, "mesh too large: n_nodes and n_elems*(dim+1) must be < 2^31");
+  if ((nn > 0 && !coords) || (ne > 0 && !elems)) return set_error(FE_EINVAL, "null mesh array");
+  if (order != FE_ORDER_NONE && order != FE_ORDER_MORTON && order != FE_ORDER_RCM)
+    return set_error(FE_EINVAL, "bad order");
+  const int k = dim + 1;
+  for (int64_t e = 0; e < ne; ++e)
+    for (int l = 0; l < k; ++l) {
+      int32_t i = elems[e * k + l];
+      if (i < 0 || i >= nn) return set_error(FE_EINVAL, "element node id out of range");
+      for (int l2 = 0; l2 < l; ++l2)
+        if (elems[e * k + l2] == i) return set_error(FE_EINVAL, "repeated node in an element");
+    }
+  return FE_OK;
+}
+
+// The node renumbering of `order` (perm[new] = old); empty for FE_ORDER_NONE.
+std::vector<int32_t> node_order(int dim, int64_t nn, const double* coords, int64_t ne,
+                                const int32_t* elems, int order) {
+  if (order == FE_ORDER_MORTON) return morton_order(dim, nn, coords);
+  if (order == FE_ORDER_RCM) return rcm_order(dim + 1, nn, ne, elems);
+  return {};
+}
+
 fe_status check_ready(fe_ctx* c, bool need_model = true) {
   if (!c) return set_error(FE_EINVAL, "null context");
   if (!c->have_mesh) return set_error(FE_EINVAL, "no mesh uploaded");
@@ -188,6 +328,20 @@ using namespace fe;
 extern "C" {
 
 int fe_version(void) { return 10000; }
+
+fe_status fe_node_order(int dim, int64_t nn, const double* coords, int64_t ne,
+                        const int32_t* elems, int order, int32_t* perm) {
+  fe_status st = check_mesh(dim, nn, coords, ne, elems, order);
+  if (st) return st;
+  if (nn > 0 && !perm) return set_error(FE_EINVAL, "perm is null");
+  std::vector<int32_t> p = node_order(dim, nn, coords, ne, elems, order);
+  if (p.empty()) {
+    for (int64_t i = 0; i < nn; ++i) perm[i] = (int32_t)i;
+  } else {
+    std::copy(p.begin(), p.end(), perm);
+  }
+  return FE_OK;
+}
 
 const char* fe_last_error(void) { return g_err.c_str(); }
 
@@ -251,21 +405,10 @@ fe_status fe_set_stream(fe_ctx* c, void* cuda_stream) {
 fe_status fe_mesh_upload(fe_ctx* c, int dim, int d, int64_t nn, const double* coords, int64_t ne,
                          const int32_t* elems, const uint8_t* dirichlet, int order) {
   if (!c) return set_error(FE_EINVAL, "null context");
-  if (dim != 2 && dim != 3) return set_error(FE_EINVAL, "dim must be 2 or 3");
   if (d != 1 && d != dim) return set_error(FE_EINVAL, "d must be 1 or dim");
-  if (nn < 0 || ne < 0) return set_error(FE_EINVAL, "negative size");
-  if (nn >= (int64_t)1 << 31 || ne * (dim + 1) >= (int64_t)1 << 31)
-    return set_error(FE_EINVAL, "mesh too large: n_nodes and n_elems*(dim+1) must be < 2^31");
-  if ((nn > 0 && !coords) || (ne > 0 && !elems)) return set_error(FE_EINVAL, "null mesh array");
-  if (order != FE_ORDER_NONE && order != FE_ORDER_MORTON) return set_error(FE_EINVAL, "bad order");
+  fe_status st0 = check_mesh(dim, nn, coords, ne, elems, order);
+  if (st0) return st0;
   const int k = dim + 1;
-  for (int64_t e = 0; e < ne; ++e)
-    for (int l = 0; l < k; ++l) {
-      int32_t i = elems[e * k + l];
-      if (i < 0 || i >= nn) return set_error(FE_EINVAL, "element node id out of range");
-      for (int l2 = 0; l2 < l; ++l2)
-        if (elems[e * k + l2] == i) return set_error(FE_EINVAL, "repeated node in an element");
-    }
   DeviceGuard g(c->device);
   if (!g.ok) return set_error(FE_ECUDA, "cudaSetDevice failed");
   cudaStreamSynchronize(c->stream);
@@ -278,8 +421,8 @@ fe_status fe_mesh_upload(fe_ctx* c, int dim, int d, int64_t nn, const double* co
 
   // internal numbering
   std::vector<int32_t> iperm;  // caller node -> device node
-  if (order == FE_ORDER_MORTON && nn > 0) {
-    c->perm_h = morton_order(dim, nn, coords);
+  if (order != FE_ORDER_NONE && nn > 0) {
+    c->perm_h = node_order(dim, nn, coords, ne, elems, order);
     iperm.resize(nn);
     for (int64_t i = 0; i < nn; ++i) iperm[c->perm_h[i]] = (int32_t)i;
     std::vector<int32_t> minnode(ne);

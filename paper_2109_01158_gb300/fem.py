@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libfemenergy.so")
 FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_EDOMAIN, FE_ETIMEOUT, FE_EBUSY = range(7)
 FE_PLAPLACE, FE_NEOHOOKE, FE_PLAPLACE_LP = 0, 1, 2
 FE_F64, FE_F32_COMP, FE_DF64 = 0, 1, 2
-FE_ORDER_NONE, FE_ORDER_MORTON = 0, 1
+FE_ORDER_NONE, FE_ORDER_MORTON, FE_ORDER_RCM = 0, 1, 2
 FE_INPUT_DEFORMATION, FE_INPUT_DISPLACEMENT = 0, 1
 FE_VECTORS_CALLER, FE_VECTORS_DEVICE = 0, 1
 
@@ -45,6 +45,7 @@ _dbl = ctypes.c_double
 _SIGNATURES = {
     "fe_version": [],
     "fe_last_error": [],
+    "fe_node_order": [_int, _i64, _vp, _i64, _vp, _int, _vp],
     "fe_create": [_vp, _int, _vp],
     "fe_destroy": [_vp],
     "fe_set_stream": [_vp, _vp],
@@ -155,6 +156,7 @@ fe_set_vector_order = _checked("fe_set_vector_order")
 fe_to_device_order = _checked("fe_to_device_order")
 fe_from_device_order = _checked("fe_from_device_order")
 fe_footprint = _checked("fe_footprint")
+fe_node_order = _checked("fe_node_order")
 fe_energy = _checked("fe_energy")
 fe_gradient_exact = _checked("fe_gradient_exact")
 fe_energy_gradient = _checked("fe_energy_gradient")
@@ -399,6 +401,18 @@ def _ptr(a) -> int | None:
     if isinstance(a, torch.Tensor):
         return a.data_ptr()
     return a.ctypes.data
+
+
+def node_order(coords, elems, order):
+    """The node renumbering fe_mesh_upload applies for `order` (host only, no GPU):
+    perm[new] = old as an int32 array.  coords: (n_nodes, dim) floats; elems:
+    (n_elems, dim+1) node ids."""
+    X = np.ascontiguousarray(coords, dtype=np.float64)
+    E = np.ascontiguousarray(elems, dtype=np.int32)
+    nn, dim = X.shape
+    perm = np.empty(nn, dtype=np.int32)
+    fe_node_order(int(dim), nn, _ptr(X), E.shape[0], _ptr(E), int(order), _ptr(perm))
+    return perm
 
 
 class FEMesh:

@@ -124,6 +124,7 @@ def test_shuffled_nodes_3d(precision):
     w = mg.shuffle_nodes(mg.neohooke_cube3d(9), seed=4)
     _parity(w, order=0, precision=precision)
     _parity(w, order=1, precision=precision)
+    _parity(w, order=2, precision=precision)
 
 
 @pytest.mark.parametrize("precision", [0, 2], ids=["f64", "df64"])

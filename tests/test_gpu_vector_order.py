@@ -26,12 +26,13 @@ def _dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
+@pytest.mark.parametrize("order", [1, 2], ids=["morton", "rcm"])
 @pytest.mark.parametrize("dim,model", [(3, mg.MODEL_NEOHOOKE), (2, mg.MODEL_PLAPLACE)])
 @pytest.mark.parametrize("precision", [0, 2], ids=["f64", "df64"])
-def test_device_order_is_the_permuted_caller_order(dim, model, precision):
+def test_device_order_is_the_permuted_caller_order(dim, model, precision, order):
     fem = _fem()
     w = mg.shuffle_nodes(mg.random_small(71 + dim, dim, model, *((6, 5, 4) if dim == 3 else (19, 17))))
-    gm = fem.FEMesh.from_workload(w, order=fem.FE_ORDER_MORTON, precisions=(precision, fem.FE_F64))
+    gm = fem.FEMesh.from_workload(w, order=order, precisions=(precision, fem.FE_F64))
     v = _dev(w.v)
     x = _dev(mg.uniform(5, np.arange(w.ndof), -1.0, 1.0))
     J, g = gm.energy_gradient(v)
@@ -42,6 +43,10 @@ def test_device_order_is_the_permuted_caller_order(dim, model, precision):
     vd, xd = gm.to_device_order(v), gm.to_device_order(x)
     assert not torch.equal(vd, v)                       # the numbering really differs
     assert torch.equal(gm.from_device_order(vd), v)     # exact inverse
+    # the device numbering is the host-side renumbering fe_node_order reports
+    perm = torch.from_numpy(fem.node_order(w.coords, w.elems, order).astype(np.int64)).cuda()
+    d = w.ndof // w.nn
+    assert torch.equal(vd.view(-1, d), v.view(-1, d)[perm])
     gm.set_vector_order(fem.FE_VECTORS_DEVICE)
     Jd, gd = gm.energy_gradient(vd)
     assert float(Jd) == float(J)
