@@ -272,6 +272,23 @@ fe_status fe_gradient_fd(fe_ctx* ctx, const double* v_dev, double eps, double* g
 fe_status fe_energy_gradient_host(fe_ctx* ctx, const double* v_host, double* J_host,
                                   double* g_host);
 
+/* Pipelined form of fe_energy_gradient_host for a sequence of evaluations: enqueues the
+ * copy of v_host into one of two device slots (on a copy-in stream), the evaluation of J and
+ * the exact gradient (on the context's stream) and the copies of J and g back to J_host and
+ * g_host (on a copy-out stream), and returns without waiting.  Successive calls alternate
+ * between the slots, so the copies of evaluation k + 1 in and of evaluation k - 1 out overlap
+ * evaluation k.  Arguments as for fe_energy_gradient_host; the copies overlap only when the
+ * host buffers are page-locked.  The caller keeps v_host unchanged, and reads J_host and
+ * g_host, only after fe_host_wait.  The slots hold 2 (2 n_nodes d + 1) doubles of device
+ * memory until the next fe_precompute, fe_mesh_upload or fe_destroy. */
+fe_status fe_energy_gradient_host_async(fe_ctx* ctx, const double* v_host, double* J_host,
+                                        double* g_host);
+
+/* Wait until every evaluation enqueued by fe_energy_gradient_host_async has been copied
+ * back; then as fe_sync_status (FE_EDOMAIN if any of them, or any other call since the last
+ * status read, met det F <= 0). */
+fe_status fe_host_wait(fe_ctx* ctx);
+
 /* Synchronise the stream and return (and clear) the device-side status of the calls
  * since the last fe_sync_status: FE_EDOMAIN if an element had det F <= 0, else FE_OK. */
 fe_status fe_sync_status(fe_ctx* ctx);

@@ -86,6 +86,20 @@ void dev_free(fe_ctx* c, T** p, size_t count) {
   *p = nullptr;
 }
 
+// Release the slots of the pipelined host evaluations (after their copies have drained);
+// the streams and events stay until fe_destroy.
+void pipe_free(fe_ctx* c) {
+  if (c->pipe_in) cudaStreamSynchronize(c->pipe_in);
+  if (c->pipe_out) cudaStreamSynchronize(c->pipe_out);
+  const size_t n = (size_t)c->nn * c->d;
+  for (int s = 0; s < 2; ++s) {
+    dev_free(c, &c->pipe_v[s], n);
+    dev_free(c, &c->pipe_g[s], n);
+  }
+  dev_free(c, &c->pipe_J, 2);
+  c->pipe_k = 0;
+}
+
 void free_precompute(fe_ctx* c) {
   const size_t ne = (size_t)c->ne, nn = (size_t)c->nn, k = (size_t)c->dim + 1;
   dev_free(c, &c->dphi, ne * c->dim * c->dim);
@@ -107,6 +121,7 @@ void free_precompute(fe_ctx* c) {
   dev_free(c, &c->r32, ne * k * c->d);
   dev_free(c, &c->stage_v, nn * c->d);
   dev_free(c, &c->stage_g, nn * c->d);
+  pipe_free(c);
   dev_free(c, &c->cg_vec, 3 * nn * c->d);
   dev_free(c, &c->hvp_cache, hvp_cache_doubles(c));
   c->have_pre = false;
@@ -388,6 +403,11 @@ fe_status fe_destroy(fe_ctx* c) {
   dev_free(c, &c->counter, 1);
   dev_free(c, &c->status, 1);
   dev_free(c, &c->stage_J, 1);
+  if (c->pipe_in) cudaStreamDestroy(c->pipe_in);
+  if (c->pipe_out) cudaStreamDestroy(c->pipe_out);
+  for (auto& pair : c->pipe_ev)
+    for (cudaEvent_t e : pair)
+      if (e) cudaEventDestroy(e);
   dev_free(c, &c->cg_part, 2 * kMaxNodeBlocks);
   dev_free(c, &c->cg_ticket, 1);
   dev_free(c, &c->cg_state, 1);
@@ -756,6 +776,62 @@ fe_status fe_energy_gradient_host(fe_ctx* c, const double* v_host, double* J_hos
   if ((st = eval(c, vin, c->stage_J, nullptr, gout ? gout : c->stage_g, true, true))) return st;
   cudaMemcpyAsync(J_host, c->stage_J, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (!gout) cudaMemcpyAsync(g_host, c->stage_g, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+  return fe_sync_status(c);
+}
+
+fe_status fe_energy_gradient_host_async(fe_ctx* c, const double* v_host, double* J_host, double* g_host) {
+  fe_status st = check_ready(c);
+  if (st) return st;
+  if (!v_host || !J_host || !g_host) return set_error(FE_EINVAL, "null argument");
+  DeviceGuard g(c->device);
+  const size_t n = (size_t)c->nn * c->d;
+  if (!c->pipe_in) {
+    if ((st = cuda_check(cudaStreamCreateWithFlags(&c->pipe_in, cudaStreamNonBlocking), "copy stream")) ||
+        (st = cuda_check(cudaStreamCreateWithFlags(&c->pipe_out, cudaStreamNonBlocking), "copy stream")))
+      return st;
+    for (auto& pair : c->pipe_ev)
+      for (cudaEvent_t& e : pair)
+        if ((st = cuda_check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event"))) return st;
+  }
+  if (!c->pipe_J) {
+    for (int s = 0; s < 2; ++s)
+      if ((st = dev_alloc(c, &c->pipe_v[s], n)) || (st = dev_alloc(c, &c->pipe_g[s], n))) {
+        pipe_free(c);
+        return st;
+      }
+    if ((st = dev_alloc(c, &c->pipe_J, 2))) {
+      pipe_free(c);
+      return st;
+    }
+    c->pipe_k = 0;
+  }
+  const int s = (int)(c->pipe_k & 1);
+  cudaEvent_t in_done = c->pipe_ev[0][s], eval_done = c->pipe_ev[1][s], out_done = c->pipe_ev[2][s];
+  const bool reuse = c->pipe_k >= 2;   // slot s held evaluation k - 2
+  // v into slot s once evaluation k - 2 has finished reading it
+  if (reuse) cudaStreamWaitEvent(c->pipe_in, eval_done, 0);
+  cudaMemcpyAsync(c->pipe_v[s], v_host, sizeof(double) * n, cudaMemcpyHostToDevice, c->pipe_in);
+  cudaEventRecord(in_done, c->pipe_in);
+  // evaluate once v has arrived and the slot's previous J and g have been copied out
+  cudaStreamWaitEvent(c->stream, in_done, 0);
+  if (reuse) cudaStreamWaitEvent(c->stream, out_done, 0);
+  if ((st = eval(c, c->pipe_v[s], c->pipe_J + s, nullptr, c->pipe_g[s], true, true))) return st;
+  cudaEventRecord(eval_done, c->stream);
+  cudaStreamWaitEvent(c->pipe_out, eval_done, 0);
+  cudaMemcpyAsync(J_host, c->pipe_J + s, sizeof(double), cudaMemcpyDeviceToHost, c->pipe_out);
+  cudaMemcpyAsync(g_host, c->pipe_g[s], sizeof(double) * n, cudaMemcpyDeviceToHost, c->pipe_out);
+  cudaEventRecord(out_done, c->pipe_out);
+  ++c->pipe_k;
+  return cuda_check(cudaGetLastError(), "fe_energy_gradient_host_async");
+}
+
+fe_status fe_host_wait(fe_ctx* c) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  DeviceGuard g(c->device);
+  if (c->pipe_out) {
+    fe_status st = cuda_check(cudaStreamSynchronize(c->pipe_out), "copy stream");
+    if (st) return st;
+  }
   return fe_sync_status(c);
 }
 

@@ -112,6 +112,14 @@ struct fe_ctx {
   double* stage_v = nullptr;   // staging for the *_host call
   double* stage_g = nullptr;
   double* stage_J = nullptr;
+  // pipelined host evaluations (fe_energy_gradient_host_async): two device slots, a copy-in
+  // and a copy-out stream, and per slot the events "copied in", "evaluated", "copied out"
+  double* pipe_v[2] = {nullptr, nullptr};
+  double* pipe_g[2] = {nullptr, nullptr};
+  double* pipe_J = nullptr;    // 2 doubles, one per slot
+  cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+  cudaEvent_t pipe_ev[3][2] = {};
+  int64_t pipe_k = 0;          // evaluations enqueued since the slots were allocated
   double* hvp_cache = nullptr; // per-element terms of the Hessian at the CG solver's point
   double* cg_vec = nullptr;    // 3*nn*d: residual, direction and H direction of the CG solver
   double* cg_part = nullptr;   // 2*kMaxNodeBlocks partial sums of the CG solver

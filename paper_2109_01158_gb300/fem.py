@@ -73,6 +73,8 @@ _SIGNATURES = {
     "fe_lbfgs_direction": [_vp, _vp, _vp, _vp],
     "fe_lbfgs_step": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "fe_energy_gradient_host": [_vp, _vp, _vp, _vp],
+    "fe_energy_gradient_host_async": [_vp, _vp, _vp, _vp],
+    "fe_host_wait": [_vp],
     "fe_sync_status": [_vp],
     "fe_get_shape_gradients": [_vp, _vp, _vp],
     "fe_get_patches": [_vp, _vp, _vp],
@@ -236,6 +238,7 @@ class LbfgsMemory:
         except Exception:
             pass
 fe_energy_gradient_host = _checked("fe_energy_gradient_host")
+fe_energy_gradient_host_async = _checked("fe_energy_gradient_host_async")
 fe_get_shape_gradients = _checked("fe_get_shape_gradients")
 fe_get_patches = _checked("fe_get_patches")
 fe_get_load_vector = _checked("fe_get_load_vector")
@@ -392,6 +395,14 @@ def fe_sync_status(ctx) -> int:
     st = load_library().fe_sync_status(ctx)
     if st not in (FE_OK, FE_EDOMAIN):
         raise FEError(st, "fe_sync_status", fe_last_error())
+    return st
+
+
+def fe_host_wait(ctx) -> int:
+    """Returns FE_OK or FE_EDOMAIN; raises on other errors."""
+    st = load_library().fe_host_wait(ctx)
+    if st not in (FE_OK, FE_EDOMAIN):
+        raise FEError(st, "fe_host_wait", fe_last_error())
     return st
 
 
@@ -569,6 +580,20 @@ class FEMesh:
         if st not in (FE_OK, FE_EDOMAIN):
             raise FEError(st, "fe_energy_gradient_host", fe_last_error())
         return J.value, g_host, st
+
+    def energy_gradient_host_async(self, v_host, J_host, g_host):
+        """Pipelined end-to-end call (fe_energy_gradient_host_async): enqueues the evaluation
+        of v_host with J and g copied back into J_host (one float64) and g_host (ndof
+        float64), and returns at once.  Use page-locked arrays (e.g. a pinned torch tensor's
+        .numpy()) for the copies to overlap; read the outputs after host_wait()."""
+        for a, n in ((v_host, self.ndof), (J_host, 1), (g_host, self.ndof)):
+            if a.dtype != np.float64 or a.size < n or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host buffers must be C-contiguous float64 of the mesh's size")
+        fe_energy_gradient_host_async(self.ctx, _ptr(v_host), _ptr(J_host), _ptr(g_host))
+
+    def host_wait(self) -> int:
+        """Wait for the pipelined evaluations; FE_OK or FE_EDOMAIN (raises on other errors)."""
+        return fe_host_wait(self.ctx)
 
     def sync_status(self) -> int:
         return fe_sync_status(self.ctx)
