@@ -32,7 +32,12 @@ def test_bench_json_line_on_a_small_workload():
     e2e = d["e2e"]
     assert e2e["h2d_bytes_per_step"] == 8 * d["config"]["dofs"]
     assert e2e["d2h_bytes_per_step"] == 8 * d["config"]["dofs"] + 8
-    assert 0 < e2e["value"] <= d["value"] * 1.05
+    if "l2" in e2e:
+        # inputs that fit in L2: value evicts L2 before every step, the host-buffer steps run
+        # back to back, so the two are not comparable
+        assert e2e["value"] > 0 and "l2" in d["config"]
+    else:
+        assert 0 < e2e["value"] <= d["value"] * 1.05
     assert d["gpu_launches"] == 3 * d["steps"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0
