@@ -148,7 +148,10 @@ uint64_t spread_bits(uint64_t x, int bits, int stride) {
   return r;
 }
 
-// Morton (Z-order) renumbering of the nodes; perm[new] = old.
+// Morton (Z-order) renumbering of the nodes; perm[new] = old.  Every axis is quantised on
+// the scale of the largest extent of the bounding box, so that the key follows distance in
+// space also on elongated domains (a per-axis scale would stretch the short axis to full
+// range and let its bits dominate the key).
 std::vector<int32_t> morton_order(int dim, int64_t nn, const double* X) {
   std::vector<double> lo(dim, 0.0), hi(dim, 0.0);
   for (int m = 0; m < dim; ++m) {
@@ -161,11 +164,12 @@ std::vector<int32_t> morton_order(int dim, int64_t nn, const double* X) {
     }
   const int bits = dim == 3 ? 21 : 31;
   const double scale = (double)((1ull << bits) - 1);
+  double ext = 0.0;
+  for (int m = 0; m < dim; ++m) ext = std::max(ext, hi[m] - lo[m]);
   std::vector<uint64_t> key(nn);
   for (int64_t i = 0; i < nn; ++i) {
     uint64_t k = 0;
     for (int m = 0; m < dim; ++m) {
-      double ext = hi[m] - lo[m];
       double t = ext > 0 ? (X[i * dim + m] - lo[m]) / ext : 0.0;
       uint64_t q = (uint64_t)(t * scale);
       k |= spread_bits(q, bits, dim) << m;

@@ -17,11 +17,11 @@ SRC = os.path.join(ROOT, "tests", "c", "host_call.c")
 PKG = os.path.join(ROOT, "paper_2109_01158_gb300")
 
 
-def _compile(out, link=True):
+def _compile(out, link=True, src=SRC):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    cmd = [cc, "-std=c99", "-O2", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), SRC, "-o", out]
+    cmd = [cc, "-std=c99", "-O2", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), src, "-o", out]
     if link:
         cmd += ["-L", PKG, "-lfemenergy", "-Wl,-rpath," + PKG]
     else:
@@ -32,6 +32,22 @@ def _compile(out, link=True):
 
 def test_c_caller_compiles_against_the_header(tmp_path):
     _compile(str(tmp_path / "host_call.o"), link=False)
+
+
+def test_c_caller_of_the_host_side_node_order(tmp_path):
+    """tests/c/node_order.c links libfemenergy.so and calls fe_node_order, which needs no
+    device.  The strip is numbered row by row, so its natural bandwidth is n + 2.  Reverse
+    Cuthill-McKee brings it to 2, the least any numbering of the strip has.  The Morton
+    curve, on one scale for both axes, keeps neighbours a few indices apart."""
+    from paper_2109_01158_gb300 import build
+    if not os.path.exists(os.path.join(PKG, "libfemenergy.so")):
+        build.build()
+    exe = str(tmp_path / "node_order")
+    _compile(exe, src=os.path.join(ROOT, "tests", "c", "node_order.c"))
+    res = subprocess.run([exe], capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    bw = dict(line.split()[1::2] for line in res.stdout.splitlines())
+    assert bw["0"] == "42" and bw["2"] == "2" and int(bw["1"]) < 8
 
 
 def _write_input(path, w):
