@@ -231,8 +231,9 @@ std::vector<int32_t> rcm_order(int k, int64_t nn, int64_t ne, const int32_t* ele
   std::vector<int32_t> order;
   order.reserve(nn);
   std::vector<uint8_t> numbered(nn, 0);
-  std::vector<int32_t> stamp(nn, -1), queue;
-  int32_t bfs_id = 0;
+  std::vector<int64_t> stamp(nn, -1);   // the last search that reached each node
+  std::vector<int32_t> queue;
+  int64_t bfs_id = 0;
   // Level structure rooted at r within r's component: returns its depth and a node of
   // least degree (then least id) in its last level.
   auto levels = [&](int32_t r, int32_t* last_min) {
