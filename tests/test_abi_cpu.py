@@ -42,8 +42,44 @@ def test_library_exports_every_declared_symbol(libpath):
 
 
 def test_library_built_for_sm103a(libpath):
-    out = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True).stdout
-    assert "sm_103a" in out
+    """Every translation unit is compiled with one -gencode, for sm_103a only."""
+    from paper_2109_01158_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.getmtime(libpath) >= max(os.path.getmtime(os.path.join(build.CSRC, f))
+                                            for f in os.listdir(build.CSRC) if f.endswith((".cu", ".cuh", ".h")))
+
+
+# Every entry point whose first argument is the context, with the number of arguments after it.
+_CTX_CALLS = {
+    "fe_destroy": 0, "fe_set_stream": 1, "fe_mesh_upload": 8, "fe_set_model": 4, "fe_set_load": 1,
+    "fe_precompute": 1, "fe_set_precision": 1, "fe_set_input": 1, "fe_set_vector_order": 1,
+    "fe_to_device_order": 2, "fe_from_device_order": 2, "fe_footprint": 1, "fe_energy": 3,
+    "fe_gradient_exact": 2, "fe_energy_gradient": 3, "fe_hessian_vector": 3, "fe_cg_steihaug": 9,
+    "fe_gradient_fd": 5, "fe_energy_gradient_host": 3, "fe_energy_gradient_host_async": 3, "fe_host_wait": 0,
+    "fe_sync_status": 0, "fe_get_shape_gradients": 2, "fe_get_patches": 2, "fe_get_load_vector": 1,
+}
+
+
+def test_null_context_is_rejected(libpath):
+    """Each call on a NULL context returns FE_EINVAL (fe_destroy: FE_OK) without touching the
+    device.  Run in a child process, so that a crash fails the test instead of the session."""
+    code = "\n".join([
+        "import ctypes, sys",
+        f"lib = ctypes.CDLL({libpath!r})",
+        "bad = []",
+        f"for name, n in {_CTX_CALLS!r}.items():",
+        "    fn = getattr(lib, name)",
+        "    fn.restype = ctypes.c_int",
+        "    fn.argtypes = [ctypes.c_void_p] * (n + 1)",
+        "    st = fn(*([None] * (n + 1)))",
+        "    want = 0 if name == 'fe_destroy' else 1",
+        "    if st != want: bad.append((name, st))",
+        "print(bad)",
+        "sys.exit(1 if bad else 0)",
+    ])
+    import sys
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0, (res.stdout, res.stderr)
 
 
 def test_binding_names_match_abi(libpath):
