@@ -153,3 +153,21 @@ def test_node_order_rejects_bad_input():
     bad[0, 0] = X.shape[0]
     with pytest.raises(fem.FEError, match="out of range"):
         fem.node_order(X, bad, fem.FE_ORDER_RCM)
+
+
+def test_size_limits_and_empty_meshes():
+    """The size checks fe_mesh_upload shares with fe_node_order reject n_nodes >= 2^31 and
+    n_elems*(dim+1) >= 2^31 before reading any array; an empty mesh is accepted, and nodes
+    that belong to no element are still numbered (each is its own component)."""
+    lib = fem.load_library()   # argument types set by the binding
+    X = np.zeros((4, 3))
+    E = np.zeros((1, 4), dtype=np.int32)
+    perm = np.empty(4, dtype=np.int32)
+    call = lib.fe_node_order
+    assert call(3, 1 << 31, X.ctypes.data, 0, None, fem.FE_ORDER_RCM, perm.ctypes.data) == fem.FE_EINVAL
+    assert "too large" in fem.fe_last_error()
+    assert call(3, 4, X.ctypes.data, 1 << 29, E.ctypes.data, fem.FE_ORDER_RCM, perm.ctypes.data) == fem.FE_EINVAL
+    assert call(3, 0, None, 0, None, fem.FE_ORDER_RCM, None) == fem.FE_OK
+    for order in (fem.FE_ORDER_MORTON, fem.FE_ORDER_RCM):
+        p = fem.node_order(np.random.default_rng(1).random((7, 2)), np.zeros((0, 3), np.int32), order)
+        assert np.array_equal(np.sort(p), np.arange(7))
