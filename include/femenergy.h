@@ -289,6 +289,15 @@ fe_status fe_energy_gradient_host_async(fe_ctx* ctx, const double* v_host, doubl
  * status read, met det F <= 0). */
 fe_status fe_host_wait(fe_ctx* ctx);
 
+/* Watchdog of the device waits (failure detection; not in the paper).  The kernels that
+ * stage data with bulk asynchronous copies wait for each copy at most `cycles` SM clocks
+ * (0 = the default, 2e9, about one second) before they give up: the kernel then records
+ * FE_ETIMEOUT (returned by the next fe_sync_status), waits with the default limit for the
+ * copies it has in flight, and returns without finishing its outputs.  A short limit makes
+ * that path run on purpose (tests of failure detection); the context stays usable and the
+ * next call with the default limit is correct.  FE_EINVAL for cycles < 0. */
+fe_status fe_set_wait_limit(fe_ctx* ctx, int64_t cycles);
+
 /* Synchronise the stream and return (and clear) the device-side status of the calls
  * since the last fe_sync_status: FE_EDOMAIN if an element had det F <= 0, else FE_OK. */
 fe_status fe_sync_status(fe_ctx* ctx);
@@ -404,22 +413,27 @@ fe_status fe_server_reset_stats(fe_server* s);
  * callers that cannot let this library allocate device memory -- a host program whose GPU
  * memory is owned entirely by its own pool allocator, or one whose time-critical loop must
  * not call cudaMalloc, which can synchronise the device).  It evaluates the same
- * J = sum_k |T_k| W(F_k) - b.v as fe_energy, needs no context and no fe_precompute, and
- * calls no cudaMalloc, cudaFree or other allocating routine.
+ * J = sum_k |T_k| W(F_k) - b.v as fe_energy, with W in the same displacement form as the
+ * context kernels (full relative accuracy near F = I), needs no context and no
+ * fe_precompute, and calls no cudaMalloc, cudaFree or other allocating routine.
  *   device, cuda_stream   the device holding every array, and the stream to enqueue on
- *   dim, d, model, p, C1, D1   as in fe_mesh_upload / fe_set_model
- *   coords_dev  n_nodes*dim doubles;  elems_dev  n_elems*(dim+1) int32 (caller layouts of
- *               fe_mesh_upload, on the device)
+ *   dim, d, model, p, C1, D1   as in fe_mesh_upload / fe_set_model: FE_NEOHOOKE (d = dim),
+ *               FE_PLAPLACE or FE_PLAPLACE_LP (d = 1, p > 1); anything else is FE_EINVAL
+ *   coords_dev  n_nodes*dim doubles;  elems_dev  n_elems*(dim+1) int32 node ids, each in
+ *               [0, n_nodes) (caller layouts of fe_mesh_upload, on the device)
  *   dphi_dev    n_elems*(dim+1)*dim doubles, vol_dev n_elems doubles: the shape gradients
  *               and volumes in the layout fe_get_shape_gradients returns
- *   b_dev       NULL or n_nodes*d doubles (b = M f);  v_dev  n_nodes*d doubles
- *   J_dev       one double receiving J (+Inf if some det F <= 0)
- * Its only scratch (block partial sums and a ticket, 19,472 bytes) is a static device array
- * that every GPU loading the library keeps until the process exits.  The first call on a
- * device looks up that array's address; make it before any stream capture.  All calls
- * share the array: calls that overlap on the GPU race and must be serialised by the
- * caller.  Sizes beyond the maximum (n_elems*(dim+1) >= 2^31 or n_nodes*d >= 2^31) are
- * rejected with FE_EINVAL. */
+ *   b_dev       NULL (no load) or n_nodes*d doubles (b = M f);  v_dev  n_nodes*d doubles
+ *   J_dev       one double receiving J: +Inf if some det F <= 0 (whatever the element's
+ *               volume); NaN if some element names a node outside [0, n_nodes) (such an
+ *               element is skipped without reading memory through its ids)
+ * The arrays are only checked on the device, so those two outcomes arrive in J_dev, not in
+ * the return status.  Its only scratch (block partial sums, a ticket and a flag word,
+ * 19,472 bytes) is a static device array that every GPU loading the library keeps until the
+ * process exits.  The first call on a device looks up that array's address; make it before
+ * any stream capture.  All calls share the array: calls that overlap on the GPU race and
+ * must be serialised by the caller.  Sizes beyond the maximum (n_elems*(dim+1) >= 2^31 or
+ * n_nodes*d >= 2^31) and a device index that does not exist are rejected with FE_EINVAL. */
 fe_status fe_energy_noalloc(int device, void* cuda_stream, int dim, int d, int model, double p,
                             double C1, double D1, int64_t n_nodes, const double* coords_dev,
                             int64_t n_elems, const int32_t* elems_dev, const double* dphi_dev,

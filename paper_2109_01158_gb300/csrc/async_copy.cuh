@@ -57,14 +57,39 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
   return ok != 0;
 }
 
-// Wait for the phase with parity `phase` to complete; false if it did not within the limit.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
-  if (mbar_try_wait(bar, phase)) return true;
+// Non-suspending test of the phase with parity `phase`.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase with parity `phase` to complete; false if it did not within `limit` SM
+// clocks.  try_wait may suspend the thread for a while inside the hardware, longer than a
+// short limit, so a limit below the default is checked with the non-suspending test.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, long long limit = kWaitCycles) {
+  const bool poll = limit < kWaitCycles;
+  if (poll ? mbar_test_wait(bar, phase) : mbar_try_wait(bar, phase)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, phase)) {
-    if (clock64() - t0 > kWaitCycles) return false;
+  while (!(poll ? mbar_test_wait(bar, phase) : mbar_try_wait(bar, phase))) {
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }
+
+// Per-thread asynchronous copy of 8 bytes from global to shared memory (both 8-byte aligned);
+// the thread waits for its own copies with cp_async_wait_all (completion does not depend on
+// any other thread).
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 }  // namespace fe

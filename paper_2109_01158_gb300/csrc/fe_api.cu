@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "async_copy.cuh"  // kWaitCycles
 #include "fe_internal.cuh"
 
 namespace fe {
@@ -22,6 +23,18 @@ fe_status cuda_check(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return FE_OK;
   g_err = std::string(what) + ": " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA;
+}
+
+int sm_count(int device) {
+  static std::atomic<int> cache[64];
+  if (device >= 0 && device < 64) {
+    const int v = cache[device].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1) sms = 1;
+  if (device >= 0 && device < 64) cache[device].store(sms, std::memory_order_relaxed);
+  return sms;
 }
 
 void prof_begin(fe_ctx* c, int stage) {
@@ -60,32 +73,6 @@ struct DeviceGuard {
   }
 };
 
-// Device allocation rounded up to 256 bytes plus 256 bytes of slack: bulk copies read whole
-// 16-byte units, so a range that ends inside the last unit of a buffer stays in bounds.
-inline size_t alloc_bytes(size_t bytes) { return ((bytes + 255) / 256) * 256 + 256; }
-
-template <typename T>
-fe_status dev_alloc(fe_ctx* c, T** p, size_t count) {
-  size_t bytes = alloc_bytes(sizeof(T) * (count > 0 ? count : 1));
-  cudaError_t e = cudaMalloc((void**)p, bytes);
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    return cuda_check(e, "cudaMalloc");
-  }
-  c->bytes += bytes;
-  return FE_OK;
-}
-
-template <typename T>
-void dev_free(fe_ctx* c, T** p, size_t count) {
-  if (*p) {
-    cudaFree(*p);
-    size_t bytes = alloc_bytes(sizeof(T) * (count > 0 ? count : 1));
-    c->bytes = c->bytes >= bytes ? c->bytes - bytes : 0;
-  }
-  *p = nullptr;
-}
-
 // Release the slots of the pipelined host evaluations (after their copies have drained);
 // the streams and events stay until fe_destroy.
 void pipe_free(fe_ctx* c) {
@@ -108,8 +95,8 @@ void free_precompute(fe_ctx* c) {
   dev_free(c, &c->ent, ne * k);
   dev_free(c, &c->slot, ne * k);
   dev_free(c, &c->b, nn * c->d);
-  dev_free(c, &c->dphi32, ne * c->dim * c->dim);
-  dev_free(c, &c->vol32, ne);
+  dev_free(c, &c->dphi32, padded_ne(ne) * c->dim * c->dim);
+  dev_free(c, &c->vol32, padded_ne(ne));
   dev_free(c, &c->dphi_df, ne * c->dim * c->dim);
   dev_free(c, &c->vol_df, ne);
   dev_free(c, &c->log_tab, kLogTable);
@@ -118,7 +105,7 @@ void free_precompute(fe_ctx* c) {
   dev_free(c, &c->u, nn * padded_d(c->d));
   dev_free(c, &c->w_hvp, nn * padded_d(c->d));
   dev_free(c, &c->r, ne * k * c->d);
-  dev_free(c, &c->r32, ne * k * c->d);
+  free_tiles(c);
   dev_free(c, &c->stage_v, nn * c->d);
   dev_free(c, &c->stage_g, nn * c->d);
   pipe_free(c);
@@ -179,6 +166,44 @@ std::vector<int32_t> morton_order(int dim, int64_t nn, const double* X) {
   std::vector<int32_t> perm(nn);
   std::iota(perm.begin(), perm.end(), 0);
   std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  return perm;
+}
+
+// Device order of the elements (eperm[new] = old): stable sort by the Morton key of the
+// centroid, quantised like morton_order's keys (the largest extent of the bounding box of the
+// nodes).  Empty when that order is the identity.
+std::vector<int32_t> element_order(int dim, int64_t nn, const double* X, int64_t ne, const int32_t* elems) {
+  if (ne <= 1 || nn <= 0) return {};
+  const int k = dim + 1;
+  std::vector<double> lo(dim), hi(dim);
+  for (int m = 0; m < dim; ++m) lo[m] = hi[m] = X[m];
+  for (int64_t i = 0; i < nn; ++i)
+    for (int m = 0; m < dim; ++m) {
+      lo[m] = std::min(lo[m], X[i * dim + m]);
+      hi[m] = std::max(hi[m], X[i * dim + m]);
+    }
+  const int bits = dim == 3 ? 21 : 31;
+  const double scale = (double)((1ull << bits) - 1);
+  double ext = 0.0;
+  for (int m = 0; m < dim; ++m) ext = std::max(ext, hi[m] - lo[m]);
+  std::vector<uint64_t> key(ne);
+  for (int64_t e = 0; e < ne; ++e) {
+    uint64_t kk = 0;
+    for (int m = 0; m < dim; ++m) {
+      double cm = 0.0;
+      for (int l = 0; l < k; ++l) cm += X[(int64_t)elems[e * k + l] * dim + m];
+      const double t = ext > 0 ? (cm / k - lo[m]) / ext : 0.0;
+      const double tq = std::min(std::max(t, 0.0), 1.0);
+      kk |= spread_bits((uint64_t)(tq * scale), bits, dim) << m;
+    }
+    key[e] = kk;
+  }
+  std::vector<int32_t> perm(ne);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  bool id = true;
+  for (int64_t e = 0; e < ne && id; ++e) id = perm[e] == (int32_t)e;
+  if (id) return {};
   return perm;
 }
 
@@ -444,24 +469,18 @@ fe_status fe_mesh_upload(fe_ctx* c, int dim, int d, int64_t nn, const double* co
   c->ne = ne;
   c->order = order;
 
-  // internal numbering
+  // internal numbering: nodes as `order` asks; elements always along the Morton curve of
+  // their centroids, so that a contiguous range of elements is a compact piece of the mesh
+  // (the tiles of the fused element + patch kernels are such ranges)
   std::vector<int32_t> iperm;  // caller node -> device node
   if (order != FE_ORDER_NONE && nn > 0) {
     c->perm_h = node_order(dim, nn, coords, ne, elems, order);
     iperm.resize(nn);
     for (int64_t i = 0; i < nn; ++i) iperm[c->perm_h[i]] = (int32_t)i;
-    std::vector<int32_t> minnode(ne);
-    for (int64_t e = 0; e < ne; ++e) {
-      int32_t m = iperm[elems[e * k]];
-      for (int l = 1; l < k; ++l) m = std::min(m, iperm[elems[e * k + l]]);
-      minnode[e] = m;
-    }
-    c->eperm_h.resize(ne);
-    std::iota(c->eperm_h.begin(), c->eperm_h.end(), 0);
-    std::stable_sort(c->eperm_h.begin(), c->eperm_h.end(),
-                     [&](int32_t a, int32_t b) { return minnode[a] < minnode[b]; });
   }
+  c->eperm_h = element_order(dim, nn, coords, ne, elems);
   const bool ident = c->perm_h.empty();
+  const bool eident = c->eperm_h.empty();
   std::vector<double> Xd(nn * dim);
   std::vector<uint8_t> dd(nn * d, 0);
   for (int64_t i = 0; i < nn; ++i) {
@@ -472,7 +491,7 @@ fe_status fe_mesh_upload(fe_ctx* c, int dim, int d, int64_t nn, const double* co
   }
   std::vector<int32_t> Ed(ne * k);
   for (int64_t e = 0; e < ne; ++e) {
-    const int64_t src = ident ? e : c->eperm_h[e];
+    const int64_t src = eident ? e : c->eperm_h[e];
     for (int l = 0; l < k; ++l) {
       int32_t n = elems[src * k + l];
       Ed[(int64_t)l * ne + e] = ident ? n : iperm[n];
@@ -488,11 +507,17 @@ fe_status fe_mesh_upload(fe_ctx* c, int dim, int d, int64_t nn, const double* co
   cudaMemcpy(c->elems, Ed.data(), sizeof(int32_t) * ne * k, cudaMemcpyHostToDevice);
   cudaMemcpy(c->dir, dd.data(), nn * d, cudaMemcpyHostToDevice);
   if (!ident) {
-    if ((st = dev_alloc(c, &c->perm, nn)) || (st = dev_alloc(c, &c->eperm, ne))) {
+    if ((st = dev_alloc(c, &c->perm, nn))) {
       free_mesh(c);
       return st;
     }
     cudaMemcpy(c->perm, c->perm_h.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice);
+  }
+  if (!eident) {
+    if ((st = dev_alloc(c, &c->eperm, ne))) {
+      free_mesh(c);
+      return st;
+    }
     cudaMemcpy(c->eperm, c->eperm_h.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice);
   }
   if ((st = cuda_check(cudaDeviceSynchronize(), "mesh upload"))) {
@@ -567,13 +592,13 @@ fe_status fe_precompute(fe_ctx* c, unsigned precisions) {
     }
   }
   if (precisions & (1u << FE_F32_COMP)) {
-    if ((st = dev_alloc(c, &c->dphi32, ne * c->dim * c->dim)) || (st = dev_alloc(c, &c->vol32, ne)) ||
-        (st = dev_alloc(c, &c->r32, ne * k * c->d))) {
+    if ((st = dev_alloc(c, &c->dphi32, padded_ne(ne) * c->dim * c->dim)) || (st = dev_alloc(c, &c->vol32, padded_ne(ne))) ||
+        (st = build_tiles(c))) {
       free_precompute(c);
       return st;
     }
   }
-  if ((precisions & ((1u << FE_DF64) | (1u << FE_F32_COMP))) && (st = dev_alloc(c, &c->u_df, nn * dp))) {
+  if ((precisions & (1u << FE_DF64)) && (st = dev_alloc(c, &c->u_df, nn * dp))) {
     free_precompute(c);
     return st;
   }
@@ -840,6 +865,13 @@ fe_status fe_host_wait(fe_ctx* c) {
   return fe_sync_status(c);
 }
 
+fe_status fe_set_wait_limit(fe_ctx* c, int64_t cycles) {
+  if (!c) return set_error(FE_EINVAL, "null context");
+  if (cycles < 0) return set_error(FE_EINVAL, "negative wait limit");
+  c->wait_limit = cycles > 0 ? (long long)cycles : kWaitCycles;
+  return FE_OK;
+}
+
 fe_status fe_sync_status(fe_ctx* c) {
   if (!c) return set_error(FE_EINVAL, "null context");
   DeviceGuard g(c->device);
@@ -890,14 +922,15 @@ fe_status fe_get_patches(fe_ctx* c, int64_t* row_ptr_host, int64_t* ent_host) {
   if (ne > 0)
     cudaMemcpyAsync(en.data(), c->ent, sizeof(int32_t) * ne * k, cudaMemcpyDeviceToHost, c->stream);
   if ((st = cuda_check(cudaStreamSynchronize(c->stream), "read back"))) return st;
-  if (c->perm_h.empty()) {
+  if (c->perm_h.empty() && c->eperm_h.empty()) {
     for (int64_t i = 0; i <= nn; ++i) row_ptr_host[i] = rp[i];
     for (int64_t q = 0; q < ne * k; ++q) ent_host[q] = en[q];
     return FE_OK;
   }
-  // translate to the caller's numbering: caller node iu is device node iperm[iu]
+  // translate to the caller's numbering: caller node iu is device node iperm[iu], device
+  // element e is caller element eperm[e]; rows are listed in caller element order
   std::vector<int32_t> iperm(nn);
-  for (int64_t i = 0; i < nn; ++i) iperm[c->perm_h[i]] = (int32_t)i;
+  for (int64_t i = 0; i < nn; ++i) iperm[c->perm_h.empty() ? i : c->perm_h[i]] = (int32_t)i;
   row_ptr_host[0] = 0;
   for (int64_t iu = 0; iu < nn; ++iu) {
     const int32_t i = iperm[iu];
@@ -905,7 +938,7 @@ fe_status fe_get_patches(fe_ctx* c, int64_t* row_ptr_host, int64_t* ent_host) {
     int64_t* out = ent_host + row_ptr_host[iu];
     for (int64_t t = 0; t < len; ++t) {
       const int32_t v = en[rp[i] + t];
-      out[t] = (int64_t)c->eperm_h[v / k] * k + v % k;
+      out[t] = (int64_t)(c->eperm_h.empty() ? v / k : c->eperm_h[v / k]) * k + v % k;
     }
     std::sort(out, out + len);
     row_ptr_host[iu + 1] = row_ptr_host[iu] + len;

@@ -6,6 +6,7 @@
 #include <math_constants.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -38,6 +39,18 @@ inline int grid_for(int64_t n, int max_blocks) {
   if (b < 1) b = 1;
   return (int)(b < max_blocks ? b : max_blocks);
 }
+
+// Element tiles of the fused element + patch kernels (fe_tiles.cu): a tile is a contiguous
+// range of at most kTileElems device-order elements together with the nodes they touch (at
+// most tile_max_nodes(dim)); one block of kTileThreads threads evaluates one tile.
+constexpr int kTileElems = 768;      // 128 hexahedra of six tetrahedra: one octree cell
+constexpr int kTileThreads = 768;    // one thread per element of a tile
+constexpr int tile_max_nodes(int dim) { return dim == 3 ? 256 : 512; }
+// Tiles start on multiples of kTileAlign elements, and the element arrays the tile kernels
+// stage (dphi32, vol32, ...) use the padded stride padded_ne(ne): every staged range then
+// starts 16-byte aligned.
+constexpr int kTileAlign = 4;
+inline int64_t padded_ne(int64_t ne) { return (ne + kTileAlign - 1) / kTileAlign * kTileAlign; }
 
 // Padded stride (in components) of the per-node displacement buffer: 1, 2 or 4.
 inline int padded_d(int d) { return d == 3 ? 4 : d; }
@@ -93,8 +106,8 @@ struct fe_ctx {
   int32_t* ent = nullptr;      // ne*(dim+1): e*(dim+1)+l, rows in increasing element order
   int32_t* slot = nullptr;     // (dim+1) SoA arrays of ne: CSR position of (e, l)
   double* b = nullptr;         // nn*d, device order
-  float* dphi32 = nullptr;     // FP32 copy of dphi
-  float* vol32 = nullptr;      // FP32 copy of vol
+  float* dphi32 = nullptr;     // FP32 copy of dphi (array stride padded_ne(ne))
+  float* vol32 = nullptr;      // FP32 copy of vol (padded_ne(ne) entries)
   float2* dphi_df = nullptr;   // double-float copy of dphi (hi, lo)
   float2* vol_df = nullptr;    // double-float copy of vol
   fe::LogEntry* log_tab = nullptr;  // table of the double-float logarithm
@@ -103,8 +116,7 @@ struct fe_ctx {
   double* u = nullptr;         // nn*padded_d(d): displacement (Neo-Hookean) or v
   double* w_hvp = nullptr;     // nn*padded_d(d): direction of a Hessian-vector product
   double* r = nullptr;         // ne*(dim+1)*d slot-ordered local forces (x2 for FD)
-  float* r32 = nullptr;        // ne*(dim+1)*d, FP32 local forces
-  float2* u_df = nullptr;      // nn*padded_d(d) double-float displacement (FE_DF64, FE_F32_COMP)
+  float2* u_df = nullptr;      // nn*padded_d(d) double-float displacement (FE_DF64)
   float2* r_df = nullptr;      // ne*(dim+1)*d double-float local forces
   double* partials = nullptr;  // element partials [kMaxElemBlocks] then node partials
   unsigned* counter = nullptr; // last-block ticket
@@ -126,6 +138,30 @@ struct fe_ctx {
   unsigned* cg_ticket = nullptr;  // last-block ticket of the CG solver
   fe::CgState* cg_state = nullptr;  // device scalars of the CG solver
   fe::CgState* cg_host = nullptr;   // page-locked host copy of them
+
+  // device: element tiles (fe_tiles.cu).  Tile t holds the elements [tile_ebeg[t],
+  // tile_ebeg[t+1]) and the tile nodes [tile_nbeg[t], tile_nbeg[t+1]) (sorted by node id).
+  // tile_node[k] = {device node id i, caller node id perm[i], first local slot | slot count
+  // << 16, (partial slot + 1) << 1 | owner}: partial slot -1 when every element of the node's
+  // patch is in this tile, owner = 1 when this tile adds the node's b_i v_i;
+  // tile_elem[e] = local node ids and local slots of element e (16 bits each: ids in .x/.y,
+  // slots in .z/.w).  A node whose patch spans several tiles ("shared") receives one partial
+  // sum per tile: the s-th shared node tile_snode[s] has the partial slots
+  // tile_spart[tile_sbeg[s] .. tile_sbeg[s+1]) of tile_part.
+  int64_t n_tiles = 0, n_tnodes = 0, n_shared = 0, n_tpart = 0;
+  int32_t* tile_ebeg = nullptr;   // n_tiles + 1
+  int32_t* tile_nbeg = nullptr;   // n_tiles + 1
+  int4* tile_node = nullptr;      // n_tnodes
+  uint4* tile_elem = nullptr;     // ne
+  int32_t* tile_snode = nullptr;  // n_shared
+  int32_t* tile_sbeg = nullptr;   // n_shared + 1
+  int32_t* tile_spart = nullptr;  // n_tpart: partial slots of each shared node, in tile order
+  float2* tile_part = nullptr;    // n_tpart * d: partial patch sums of the shared nodes
+  double* tile_epart = nullptr;   // 2 * n_tiles: per-tile sums of |T| W and of b.v
+
+  // SM clocks a bulk-copy kernel waits for its first copy before it gives up and reports
+  // FE_ETIMEOUT (fe_set_wait_limit); the drain after giving up always waits the full default
+  long long wait_limit = 2000000000LL;
 
   int64_t launches = 0;
   size_t bytes = 0;
@@ -199,6 +235,52 @@ fe_status launch_eval_f32(fe_ctx* c, const double* v, double* J, double* dens, d
                           bool want_energy, bool want_grad);
 
 ModelParams model_params(const fe_ctx* c);
+
+// Device allocation rounded up to 256 bytes plus 256 bytes of slack: bulk copies read whole
+// 16-byte units, so a range that ends inside the last unit of a buffer stays in bounds.
+inline size_t alloc_bytes(size_t bytes) { return ((bytes + 255) / 256) * 256 + 256; }
+
+template <typename T>
+fe_status dev_alloc(fe_ctx* c, T** p, size_t count) {
+  size_t bytes = alloc_bytes(sizeof(T) * (count > 0 ? count : 1));
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_check(e, "cudaMalloc");
+  }
+  c->bytes += bytes;
+  return FE_OK;
+}
+
+template <typename T>
+void dev_free(fe_ctx* c, T** p, size_t count) {
+  if (*p) {
+    cudaFree(*p);
+    size_t bytes = alloc_bytes(sizeof(T) * (count > 0 ? count : 1));
+    c->bytes = c->bytes >= bytes ? c->bytes - bytes : 0;
+  }
+  *p = nullptr;
+}
+
+// Raise the dynamic shared-memory limit of kernel `func` to `bytes` on `device`, once per
+// device (the attribute is per device); `done` is the caller's per-kernel bit mask of devices.
+// Thread-safe: two threads may both set it, which is harmless.
+inline fe_status ensure_smem(const void* func, int device, int bytes, std::atomic<uint64_t>& done) {
+  const uint64_t bit = (device >= 0 && device < 64) ? (1ull << device) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return FE_OK;
+  const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return cuda_check(e, "kernel shared-memory attribute");
+  if (bit) done.fetch_or(bit, std::memory_order_release);
+  return FE_OK;
+}
+
+// Number of SMs of `device`, queried once per device.
+int sm_count(int device);
+
+// fe_tiles.cu: the element tiles of the fused element + patch kernels (built from the
+// device-order mesh; freed with the precompute).
+fe_status build_tiles(fe_ctx* c);
+void free_tiles(fe_ctx* c);
 
 // Bracket a launch with profiling events when timing is enabled (no-op otherwise).
 enum Stage { kStagePrep = 0, kStageElem = 1, kStageGather = 2, kStageFdElem = 3, kStageFdGather = 4 };

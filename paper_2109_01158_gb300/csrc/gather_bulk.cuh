@@ -36,21 +36,8 @@ struct AccDF {
   __device__ __forceinline__ double value() const { return df_to_double(s); }
 };
 
-// Float slots, float-pair (TwoSum) sums.
-struct AccF32 {
-  using T = float;
-  float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void set(float x) { hi = x; }
-  __device__ __forceinline__ void add(float x) {
-    const df t = two_sum(hi, x);
-    hi = t.hi;
-    lo = fadd(lo, t.lo);
-  }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-
 // The kernel and its launcher have internal linkage: every translation unit that uses them
-// compiles its own copy of the kernel, and the launcher's once-per-device attribute flag must
+// compiles its own copy of the kernel, and the launcher's once-per-device attribute mask must
 // belong to that copy.
 namespace {
 
@@ -58,7 +45,7 @@ template <int D, class Acc>
 __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
     int64_t nn, const int32_t* __restrict__ row_ptr, const typename Acc::T* __restrict__ r,
     const double* __restrict__ b, const uint8_t* __restrict__ dir, const int32_t* __restrict__ perm,
-    double* __restrict__ g, int* status, const int* skip) {
+    double* __restrict__ g, int* status, const int* skip, long long wait_limit) {
   using T = typename Acc::T;
   if (skip && *skip) return;  // a solver loop enqueued this launch after it had finished
   extern __shared__ __align__(128) unsigned char gsmem[];
@@ -87,9 +74,10 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
         mbar_arrive_expect_tx(bar, (uint32_t)(a1 - a0));
         bulk_g2s(buf, reinterpret_cast<const unsigned char*>(r) + a0, (uint32_t)(a1 - a0), bar);
       }
-      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, phase));
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, phase, wait_limit));
       if (!ok) {
-        // give up: record it, wait (bounded) for the copy still in flight, and stop
+        // give up: record it, wait (with the full limit) for the copy still in flight, so
+        // that nothing is written to shared memory after the block has left, and stop
         if (lane == 0) atomicOr(status, kStatusTimeout);
         mbar_wait_bounded(bar, phase);
         return;
@@ -144,21 +132,16 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
 template <int D, class Acc>
 inline fe_status launch_gather_bulk(fe_ctx* c, const typename Acc::T* r, double* g, const double* b,
                                     const int* skip = nullptr) {
-  static bool configured[64] = {false};
-  if (c->device < 0 || c->device >= 64 || !configured[c->device]) {
-    cudaError_t e = cudaFuncSetAttribute(k_gather_bulk<D, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kGatherSmem);
-    if (e != cudaSuccess) return cuda_check(e, "gather smem attribute");
-    if (c->device >= 0 && c->device < 64) configured[c->device] = true;
-  }
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  static std::atomic<uint64_t> smem_set{0};
+  fe_status st = ensure_smem((const void*)k_gather_bulk<D, Acc>, c->device, kGatherSmem, smem_set);
+  if (st) return st;
+  const int sms = sm_count(c->device);
   const int64_t nchunks = (c->nn + 31) / 32;
   int64_t blocks = (nchunks + kGatherWarps - 1) / kGatherWarps;
   if (blocks > sms) blocks = sms;
   if (blocks < 1) blocks = 1;
   k_gather_bulk<D, Acc><<<(unsigned)blocks, kGatherWarps * 32, kGatherSmem, c->stream>>>(
-      c->nn, c->row_ptr, r, b, c->dir, io_perm(c), g, c->status, skip);
+      c->nn, c->row_ptr, r, b, c->dir, io_perm(c), g, c->status, skip, c->wait_limit);
   return cuda_check(cudaGetLastError(), "gather launch");
 }
 

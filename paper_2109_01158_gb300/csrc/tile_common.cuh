@@ -1,0 +1,201 @@
+// tile_common.cuh -- pieces shared by the fused element + patch kernels of every precision
+// (see fe_tiles.cu for the tile structure): the shared-memory layout of the tile pipeline, the
+// asynchronous copies that fill it, the per-tile energy partials and their final sum, and the
+// kernel that completes the gradient of the shared nodes.
+//
+// The fused kernels run one persistent block per SM; block b takes the tiles b, b + G,
+// b + 2G, ... (G blocks).  While it computes tile t it already has in flight:
+//   - bulk asynchronous copies (TMA) of the element arrays and node records of the tile after
+//     next (two element stages, three record buffers: the current tile's records are still
+//     read while those of the next two tiles arrive), and
+//   - per-thread asynchronous copies of the nodal values (v, X, b) of the next tile,
+// so that its arithmetic overlaps the HBM traffic of the following tiles.
+#pragma once
+
+#include "async_copy.cuh"
+#include "df64.cuh"
+#include "fe_internal.cuh"
+
+namespace fe {
+namespace {
+
+// Shared-memory layout of the pipeline of one block.
+//   E[2]  element stages: DIM*DIM shape-gradient arrays and the volume (EB bytes per element
+//         each), then the local ids / local slots (16 bytes per element); tiles start on
+//         multiples of kTileAlign elements and the arrays use the padded stride, so every
+//         copied range starts 16-byte aligned;
+//   V     nodal values of the next tile as copied from global memory: per node D values of v,
+//         D of X and D of b (doubles);
+//   U     per-node records of the current tile (NU bytes each), built from V;
+//   Rs    the local forces of the current tile, RB bytes per slot.
+template <int DIM, int D, int EB, int NU, int RB>
+struct TilePipe {
+  static constexpr int kNodes = tile_max_nodes(DIM);
+  static constexpr int kSlots = (DIM + 1) * kTileElems;
+  static constexpr int kArrays = DIM * DIM + 1;
+  static constexpr int kArrayBytes = (kTileElems * EB + 15) / 16 * 16;
+  static_assert(kTileElems % kTileAlign == 0, "tiles hold whole groups of kTileAlign elements");
+  static constexpr int kElemOff = kArrays * kArrayBytes;          // uint4 per element
+  static constexpr int kEBytes = kElemOff + kTileElems * 16;
+  static constexpr int kVPerNode = 3 * D;                         // doubles
+  static constexpr int kE = 0;
+  static constexpr int kV = kE + 2 * kEBytes;
+  static constexpr int kU = kV + kNodes * kVPerNode * 8;
+  static constexpr int kRs = kU + kNodes * NU;
+  static constexpr int kBytes = kRs + kSlots * RB;
+  static_assert(kEBytes % 16 == 0 && kU % 16 == 0 && kRs % 16 == 0, "alignment");
+};
+
+// The tile structure and element arrays of one precision (structure of arrays, stride ne).
+struct TileArgs {
+  const int32_t* ebeg;         // ntiles + 1
+  const int32_t* nbeg;         // ntiles + 1
+  const int4* node;            // node records
+  const unsigned char* dphi;   // DIM*DIM arrays of `stride` entries of EB bytes
+  const unsigned char* vol;    // `stride` entries of EB bytes
+  const uint4* elem;           // local ids / slots
+  int64_t ntiles;
+  int64_t stride;              // padded_ne(ne)
+  long long wait_limit;
+};
+
+// Thread 0: bulk copies of the element arrays of elements [e0, e1) into the stage at `st`,
+// completing on `bar` (one arrival; an empty range completes the phase at once).
+template <class S, int EB>
+__device__ __forceinline__ void pipe_issue_elems(unsigned char* st, const TileArgs& A, int e0, int e1,
+                                                 uint64_t* bar) {
+  const int n = e1 - e0;
+  const uint32_t bytes = ((uint32_t)n * EB + 15u) & ~15u;
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(bar, S::kArrays * bytes + (uint32_t)n * 16u);
+  if (n > 0) {
+#pragma unroll
+    for (int a = 0; a < S::kArrays; ++a) {
+      const unsigned char* p = (a < S::kArrays - 1 ? A.dphi + (int64_t)a * A.stride * EB : A.vol) + (int64_t)e0 * EB;
+      bulk_g2s(st + a * S::kArrayBytes, p, bytes, bar);
+    }
+    bulk_g2s(st + S::kElemOff, A.elem + e0, (uint32_t)n * 16u, bar);
+  }
+}
+
+// Thread 0: bulk copy of the node records [k0, k0 + nt) into `rb`, completing on `bar`.
+__device__ __forceinline__ void pipe_issue_recs(int4* rb, const TileArgs& A, int k0, int nt, uint64_t* bar) {
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(bar, (uint32_t)nt * 16u);
+  if (nt > 0) bulk_g2s(rb, A.node + k0, (uint32_t)nt * 16u, bar);
+}
+
+// One thread per tile node: per-thread asynchronous copies of the node's v (at its caller or
+// device index), X (Neo-Hookean deformation input) and b (when a load is given) into V.
+template <int DIM, int D, int MODEL>
+__device__ __forceinline__ void pipe_gather_nodes(double* V, const int4* rec, int nt, const double* v,
+                                                  const double* X, const double* b, bool caller_order, bool disp) {
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+    const int4 r = rec[k];
+    const int64_t i = r.x, src = caller_order ? r.y : r.x;
+    double* o = V + k * 3 * D;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      cp_async8(o + j, v + src * D + j);
+      if (MODEL == FE_NEOHOOKE && !disp) cp_async8(o + D + j, X + i * DIM + j);
+      if (b && (r.w & 1)) cp_async8(o + 2 * D + j, b + i * D + j);
+    }
+  }
+  cp_async_commit();
+}
+
+__device__ __forceinline__ double pipe_warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// One warp: the sums of red[0][0..n) and red[1][0..n) in a fixed order (valid in lane 0).
+__device__ __forceinline__ void pipe_warp_pair_sum(const double* r0, const double* r1, int n, double* s0,
+                                                   double* s1) {
+  const int lane = threadIdx.x & 31;
+  double a = 0.0, b = 0.0;
+  for (int k = lane; k < n; k += 32) {
+    a += r0[k];
+    b += r1[k];
+  }
+  *s0 = pipe_warp_sum(a);
+  *s1 = pipe_warp_sum(b);
+}
+
+// After every block has written its tiles' partials epart[t] (sum |T| W) and epart[ntiles + t]
+// (b.v): the block that arrives last adds them over the tiles in a fixed order and writes
+// J = sum |T| W - (b.v + shift) (shift = b.X when the caller passes displacements).  `red`
+// holds 2 * blockDim.x doubles of shared memory.
+__device__ __forceinline__ void pipe_finish_energy(const double* epart, int64_t ntiles, double shift,
+                                                   unsigned* counter, double* J, double* red) {
+  __shared__ bool am_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    am_last = atomicAdd(counter, 1u) == gridDim.x - 1u;
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  double s = 0.0, b = 0.0;
+  for (int64_t k = threadIdx.x; k < ntiles; k += blockDim.x) {
+    s += __ldcg(epart + k);
+    b += __ldcg(epart + ntiles + k);
+  }
+  red[threadIdx.x] = s;
+  red[blockDim.x + threadIdx.x] = b;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double ts, tb;
+    pipe_warp_pair_sum(red, red + blockDim.x, blockDim.x, &ts, &tb);
+    if (threadIdx.x == 0) {
+      *J = ts - (tb + shift);
+      *counter = 0u;
+    }
+  }
+}
+
+// Accumulator of a shared node's partial sums (one per tile, in tile order).
+struct PartF32 {
+  using T = float;
+  float s = 0.f;
+  __device__ __forceinline__ void add(float x, bool first) { s = first ? x : __fadd_rn(s, x); }
+  __device__ __forceinline__ double value() const { return (double)s; }
+};
+
+struct PartDF {
+  using T = float2;
+  df s = {0.f, 0.f};
+  __device__ __forceinline__ void add(float2 x, bool first) { s = first ? df{x.x, x.y} : df_add(s, df{x.x, x.y}); }
+  __device__ __forceinline__ double value() const { return df_to_double(s); }
+};
+
+// Gradient of the shared nodes: g_i = sum of the node's tile partials - b_i, 0 on Dirichlet
+// dofs; written at the caller's index perm[i] (perm null = identity).  One thread per
+// (node, component).
+template <int D, class Acc>
+__global__ void __launch_bounds__(kThreads) k_tile_shared(int64_t nshared, const int32_t* __restrict__ snode,
+                                                          const int32_t* __restrict__ sbeg,
+                                                          const int32_t* __restrict__ spart,
+                                                          const typename Acc::T* __restrict__ part,
+                                                          const double* __restrict__ b,
+                                                          const uint8_t* __restrict__ dir,
+                                                          const int32_t* __restrict__ perm, double* __restrict__ g) {
+  const int64_t n = nshared * D;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n; w += stride) {
+    const int64_t s = w / D;
+    const int j = (int)(w - s * D);
+    const int64_t i = __ldg(snode + s);
+    const int32_t p0 = __ldg(sbeg + s), p1 = __ldg(sbeg + s + 1);
+    Acc acc;
+    for (int32_t p = p0; p < p1; ++p) acc.add(__ldg(part + (int64_t)__ldg(spart + p) * D + j), p == p0);
+    const int64_t dst = perm ? (int64_t)__ldg(perm + i) : i;
+    const double bj = b ? __ldg(b + i * D + j) : 0.0;
+    g[dst * D + j] = __ldg(dir + i * D + j) ? 0.0 : acc.value() - bj;
+  }
+}
+
+}  // namespace
+}  // namespace fe

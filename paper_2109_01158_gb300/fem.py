@@ -76,6 +76,7 @@ _SIGNATURES = {
     "fe_energy_gradient_host_async": [_vp, _vp, _vp, _vp],
     "fe_host_wait": [_vp],
     "fe_sync_status": [_vp],
+    "fe_set_wait_limit": [_vp, _i64],
     "fe_get_shape_gradients": [_vp, _vp, _vp],
     "fe_get_patches": [_vp, _vp, _vp],
     "fe_get_load_vector": [_vp, _vp],
@@ -246,6 +247,7 @@ fe_launch_count = _checked("fe_launch_count")
 fe_profile_enable = _checked("fe_profile_enable")
 fe_profile_read = _checked("fe_profile_read")
 fe_energy_noalloc = _checked("fe_energy_noalloc")
+fe_set_wait_limit = _checked("fe_set_wait_limit")
 fe_diag_df64_log = _checked("fe_diag_df64_log")
 fe_batch_work_bytes = _checked("fe_batch_work_bytes")
 fe_batch_create = _checked("fe_batch_create")
@@ -597,6 +599,10 @@ class FEMesh:
 
     def sync_status(self) -> int:
         return fe_sync_status(self.ctx)
+
+    def set_wait_limit(self, cycles: int = 0):
+        """SM clocks a kernel waits for a bulk copy before it reports FE_ETIMEOUT (0 = default)."""
+        fe_set_wait_limit(self.ctx, int(cycles))
 
     # -- inspection ----------------------------------------------------------------------
     def shape_gradients(self):

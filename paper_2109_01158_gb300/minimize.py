@@ -327,9 +327,10 @@ def _to_boundary(z, d, radius):
     return (-zd + math.sqrt(disc)) / max(dd, 1e-300)
 
 
-def _cg_steihaug(g, hv, radius, tol, max_cg):
+def _cg_steihaug(g, hv, radius, tol, max_cg, history=None):
     """Steihaug's truncated CG (Nocedal & Wright, Alg. 7.2) for min g.z + z.Hz/2 within
-    ||z|| <= radius.  Returns (z, Hz, iterations, hit_boundary)."""
+    ||z|| <= radius.  Returns (z, Hz, iterations, hit_boundary); `history`, when a list, gets
+    the residual norm after every step."""
     z = torch.zeros_like(g)
     Hz = torch.zeros_like(g)
     r = g.clone()
@@ -351,6 +352,8 @@ def _cg_steihaug(g, hv, radius, tol, max_cg):
         z, Hz = z_new, Hz + alpha * Hd
         r = r + alpha * Hd
         rr_new = float(torch.dot(r, r).item())
+        if history is not None:
+            history.append(math.sqrt(rr_new))
         if math.sqrt(rr_new) <= tol:
             return z, Hz, k, False
         d = -r + (rr_new / rr) * d

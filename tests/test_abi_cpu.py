@@ -56,7 +56,7 @@ _CTX_CALLS = {
     "fe_to_device_order": 2, "fe_from_device_order": 2, "fe_footprint": 1, "fe_energy": 3,
     "fe_gradient_exact": 2, "fe_energy_gradient": 3, "fe_hessian_vector": 3, "fe_cg_steihaug": 9,
     "fe_gradient_fd": 5, "fe_energy_gradient_host": 3, "fe_energy_gradient_host_async": 3, "fe_host_wait": 0,
-    "fe_sync_status": 0, "fe_get_shape_gradients": 2, "fe_get_patches": 2, "fe_get_load_vector": 1,
+    "fe_sync_status": 0, "fe_set_wait_limit": 1, "fe_get_shape_gradients": 2, "fe_get_patches": 2, "fe_get_load_vector": 1,
 }
 
 
