@@ -3,8 +3,8 @@
 // arithmetic in float (elem_f32.cuh) and FP64 energy sums, in one fused persistent launch per
 // call plus a small completion launch for the gradient of nodes on tile boundaries.
 //
-// One persistent block per SM walks its element tiles (fe_tiles.cu, tile_common.cuh).  Per
-// tile:
+// Persistent blocks (kTileBlocksPerSM per SM) walk their element tiles (fe_tiles.cu,
+// tile_common.cuh).  Per tile:
 //   B  one thread per element: H from float-pair differences of u, W and |T| dW/dF in float,
 //      and the local forces r_{T,l} = |T| dW/dF grad(phi_l) written to the element's local
 //      slots in shared memory;
@@ -53,8 +53,9 @@ __device__ __forceinline__ void load_pairs(const float2* us, int k, float2 (&w)[
 }
 
 // d as the pair hi + lo of floats: hi = d with its significand cut to 24 bits, lo = the rest
-// rounded to float (|hi + lo - d| <= 2^-48 |d|), from the bits of d with integer operations
-// only.  Outside 2^-60 <= |d| < 2^61 (and for 0, subnormals, Inf, NaN) it rounds in FP64.
+// cut to 24 bits (|hi + lo - d| < 2^-47 |d|), from the bits of d with integer operations only
+// (the conversion instructions run at a low rate on the FP64 unit of this GPU).  Outside
+// 2^-60 <= |d| < 2^61 (and for 0, subnormals, Inf, NaN) it rounds in FP64.
 __device__ __forceinline__ float2 split_double(double d) {
   const long long bits = __double_as_longlong(d);
   const unsigned hw = (unsigned)(bits >> 32);
@@ -66,55 +67,54 @@ __device__ __forceinline__ float2 split_double(double d) {
   const unsigned sign = hw & 0x80000000u;
   // hi: sign | float exponent | the top 23 stored significand bits
   const float hi = __uint_as_float(sign | ((ex - 896u) << 23) | ((unsigned)(bits >> 29) & 0x7fffffu));
-  // lo: the low 29 significand bits times 2^(ex - 1075), rounded once
+  // lo: the low 29 significand bits, worth rest * 2^(ex - 1075), normalised to a float with
+  // its top 24 bits (nb significant bits: exponent nb - 1 + ex - 1075, at least 2^-112)
   const unsigned rest = (unsigned)bits & 0x1fffffffu;
-  const float scale = __uint_as_float((ex - 948u) << 23);   // 2^(ex - 1075) (ex >= 963: normal)
-  const float lo = __fmul_rn(__uint2float_rn(rest), scale);
-  return make_float2(hi, sign ? -lo : lo);
+  if (rest == 0u) return make_float2(hi, 0.f);
+  const int nb = 32 - __clz(rest);
+  const unsigned m = nb > 24 ? rest >> (nb - 24) : rest << (24 - nb);
+  const float lo = __uint_as_float(sign | ((unsigned)(nb + (int)ex - 949) << 23) | (m & 0x7fffffu));
+  return make_float2(hi, lo);
 }
 
-// N: the float-pair records of the tile's nodes from the copied values V; returns this
-// thread's b_i v_i over the nodes the tile owns.
+// N: the float-pair records of a tile's nodes from the copied values V, as (node, component)
+// items over the compute threads; returns this thread's b_i v_i over the nodes the tile owns.
 template <int DIM, int D, int MODEL>
 __device__ __forceinline__ double nodes_to_pairs(const double* V, const int4* rec, int nt, float2* us, bool with_b,
-                                                 bool disp) {
+                                                 bool disp, int nthreads) {
   constexpr int DP = Pipe32<DIM, D>::DP;
   double bv = 0.0;
-  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+  for (int w = threadIdx.x; w < nt * D; w += nthreads) {
+    const int k = w / D, j = w - k * D;
     const double* o = V + k * 3 * D;
-    const bool own = with_b && (rec[k].w & 1);
-    float2 w[DP];
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      const double vj = o[j];
-      w[j] = split_double((MODEL == FE_NEOHOOKE && !disp) ? vj - o[D + j] : vj);
-      if (own) bv = fma(o[2 * D + j], vj, bv);
-    }
-    if constexpr (DP == 1) {
-      us[k] = w[0];
-    } else if constexpr (DP == 2) {
-      reinterpret_cast<float4*>(us)[k] = make_float4(w[0].x, w[0].y, w[1].x, w[1].y);
-    } else {
-      float4* q = reinterpret_cast<float4*>(us) + 2 * k;
-      q[0] = make_float4(w[0].x, w[0].y, w[1].x, w[1].y);
-      q[1] = make_float4(w[2].x, w[2].y, 0.f, 0.f);
-    }
+    const double vj = o[j];
+    us[k * DP + j] = split_double((MODEL == FE_NEOHOOKE && !disp) ? vj - o[D + j] : vj);
+    if (with_b && (rec[k].w & 1)) bv = fma(o[2 * D + j], vj, bv);
   }
   return bv;
 }
 
+// The block: warps 0 .. kTileElems/32 - 1 compute (one thread per element of a tile, and the
+// node work as (node, component) items); the last warp is the producer: its lane 0 issues and
+// waits for every bulk copy and loads the tiles' ranges, and the warp adds each tile's energy
+// partial.  No compute thread waits on a copy barrier.
 template <int DIM, int D, int MODEL, bool ENERGY, bool GRAD, bool DENS>
-__global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
+__global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_f32(
     TileArgs ta, const double* __restrict__ v, const double* __restrict__ X, const double* __restrict__ b,
     const uint8_t* __restrict__ dir, const int32_t* __restrict__ eperm, ModelParams mp, bool caller_order,
     bool disp, double shift, double* __restrict__ g, float* __restrict__ part, double* __restrict__ dens,
     double* epart, unsigned* counter, double* J, int* status) {
   using P = Pipe32<DIM, D>;
   using S = typename P::S;
-  constexpr int K = DIM + 1, NXY = P::NXY;
+  constexpr int K = DIM + 1, NXY = P::NXY, DP = P::DP;
+  constexpr int NC = kTileElems;         // compute threads
+  constexpr int NCW = NC / 32;           // compute warps
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t barE[2], barR[3];
   __shared__ __align__(16) int4 recs[3][S::kNodes];
+  __shared__ int4 info[3];               // {e0, e1, k0, nt} of the tile in each record slot
+  __shared__ float ews[NC];               // |T| W of the tile's elements
+  __shared__ double wbv[NCW];            // per compute warp: its b.v of the tile
   __shared__ double red[2 * kTileThreads];
   __shared__ int abort_flag;
   float2* us = reinterpret_cast<float2*>(smem + S::kU);
@@ -122,22 +122,23 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
   float2* rxy = reinterpret_cast<float2*>(smem + S::kRs);
   float* rz = reinterpret_cast<float*>(smem + S::kRs + NXY * 4 * S::kSlots);
   const int G = gridDim.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool compute = tid < NC, producer = warp == NCW, issuer = tid == NC;
   const int64_t ntiles = ta.ntiles;
   const bool with_b = ENERGY && b != nullptr;
-  // thread 0's view of the copy pipeline: completed phases and copies in flight per buffer
+  // the issuer's view of the copy pipeline: completed phases and copies in flight per buffer
   uint32_t phE[2] = {0u, 0u}, phR[3] = {0u, 0u, 0u};
   bool pendE[2] = {false, false}, pendR[3] = {false, false, false};
-  auto issue_tile = [&](int64_t tq, int eb, int rb, bool elems, bool records) {
-    if (elems) {
-      pipe_issue_elems<S, 4>(smem + S::kE + eb * S::kEBytes, ta, __ldg(ta.ebeg + tq), __ldg(ta.ebeg + tq + 1),
-                             &barE[eb]);
-      pendE[eb] = true;
-    }
-    if (records) {
-      const int k0 = __ldg(ta.nbeg + tq);
-      pipe_issue_recs(recs[rb], ta, k0, __ldg(ta.nbeg + tq + 1) - k0, &barR[rb]);
-      pendR[rb] = true;
-    }
+  auto issue_records = [&](int64_t tq, int slot) {
+    const int e0 = __ldg(ta.ebeg + tq), e1 = __ldg(ta.ebeg + tq + 1);
+    const int k0 = __ldg(ta.nbeg + tq), nt = __ldg(ta.nbeg + tq + 1) - k0;
+    info[slot] = make_int4(e0, e1, k0, nt);
+    pipe_issue_recs(recs[slot], ta, k0, nt, &barR[slot]);
+    pendR[slot] = true;
+  };
+  auto issue_elems = [&](int slot, int eb) {
+    const int4 in = info[slot];
+    pipe_issue_elems<S, 4>(smem + S::kE + eb * S::kEBytes, ta, in.x, in.y, &barE[eb]);
+    pendE[eb] = true;
   };
   auto wait_e = [&](int eb) {
     const bool ok = mbar_wait_bounded(&barE[eb], phE[eb] & 1u, ta.wait_limit);
@@ -151,24 +152,29 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
   };
 
   int64_t t = blockIdx.x;
-  if (tid == 0) {
+  if (issuer) {
     abort_flag = 0;
     for (int q = 0; q < 2; ++q) mbar_init(&barE[q], 1);
     for (int q = 0; q < 3; ++q) mbar_init(&barR[q], 1);
     mbar_init_fence();
-    issue_tile(t, 0, 0, true, true);
-    if (t + G < ntiles) issue_tile(t + G, 1, 1, true, true);
+    issue_records(t, 0);
+    issue_elems(0, 0);
+    if (t + G < ntiles) {
+      issue_records(t + G, 1);
+      issue_elems(1, 1);
+    }
     if (!wait_r(0)) abort_flag = 1;
   }
   __syncthreads();
   double bv = 0.0;   // this thread's b_i v_i of the current tile
   if (!abort_flag) {
-    const int nt = __ldg(ta.nbeg + t + 1) - __ldg(ta.nbeg + t);
-    pipe_gather_nodes<DIM, D, MODEL>(V, recs[0], nt, v, X, with_b ? b : nullptr, caller_order, disp);
-    cp_async_wait_all();
+    if (compute) {
+      pipe_gather_nodes<DIM, D, MODEL>(V, recs[0], info[0].w, v, X, with_b ? b : nullptr, caller_order, disp, NC);
+      cp_async_wait_all();
+    }
     __syncthreads();
-    bv = nodes_to_pairs<DIM, D, MODEL>(V, recs[0], nt, us, with_b, disp);
-    if (tid == 0) {
+    if (compute) bv = nodes_to_pairs<DIM, D, MODEL>(V, recs[0], info[0].w, us, with_b, disp, NC);
+    if (issuer) {
       bool ok = wait_e(0);
       if (ok && t + G < ntiles) ok = wait_r(1);
       if (!ok) abort_flag = 1;
@@ -181,23 +187,27 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
   int it = 0;
   for (; t < ntiles && !abort_flag; t += G, ++it) {
     const int eb = it & 1, rb = it % 3, rn = (it + 1) % 3, r2 = (it + 2) % 3;
-    const int64_t tn = t + G, t2 = t + 2 * (int64_t)G;
-    const int e0 = __ldg(ta.ebeg + t), e1 = __ldg(ta.ebeg + t + 1);
-    const int nt = __ldg(ta.nbeg + t + 1) - __ldg(ta.nbeg + t);
-    const int ntn = tn < ntiles ? __ldg(ta.nbeg + tn + 1) - __ldg(ta.nbeg + tn) : 0;
+    const bool has_next = t + G < ntiles, has_t2 = t + 2 * (int64_t)G < ntiles;
+    const int4 in = info[rb];
+    const int e0 = in.x, e1 = in.y, nt = in.w;
+    const int ntn = has_next ? info[rn].w : 0;
     const int4* R = recs[rb];
     const unsigned char* E = smem + S::kE + eb * S::kEBytes;
 
-    // the next tile's nodal values start copying
-    if (tn < ntiles) pipe_gather_nodes<DIM, D, MODEL>(V, recs[rn], ntn, v, X, with_b ? b : nullptr, caller_order, disp);
+    if (producer) {
+      // the records of the tile after next (slot r2 held the previous tile's)
+      if (issuer && has_t2) issue_records(t + 2 * (int64_t)G, r2);
+    } else {
+      // the next tile's nodal values start copying
+      if (has_next)
+        pipe_gather_nodes<DIM, D, MODEL>(V, recs[rn], ntn, v, X, with_b ? b : nullptr, caller_order, disp, NC);
 
-    // B: one thread per element
-    float ew = 0.f;   // this thread's |T| W
-    {
-      const uint4* se = reinterpret_cast<const uint4*>(E + S::kElemOff);
-      for (int e = e0 + tid; e < e1; e += blockDim.x) {
-        const int el = e - e0;
-        const uint4 le = se[el];
+      // B: one thread per element
+      float ew = 0.f;   // this thread's |T| W
+      const int e = e0 + tid;
+      if (e < e1) {
+        const int el = tid;
+        const uint4 le = reinterpret_cast<const uint4*>(E + S::kElemOff)[el];
         const int lid[4] = {(int)(le.x & 0xffffu), (int)(le.x >> 16), (int)(le.y & 0xffffu), (int)(le.y >> 16)};
         float2 u0[D], ul[D];
         load_pairs<D>(us, lid[0], u0);
@@ -212,14 +222,11 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
 #pragma unroll
         for (int l = 0; l < DIM; ++l)
 #pragma unroll
-          for (int m = 0; m < DIM; ++m) {
-            const int ar = l * DIM + m;
-            gg[l][m] = reinterpret_cast<const float*>(E + ar * S::kArrayBytes)[el];
-          }
+          for (int m = 0; m < DIM; ++m) gg[l][m] = reinterpret_cast<const float*>(E + (l * DIM + m) * S::kArrayBytes)[el];
         const float vT = reinterpret_cast<const float*>(E + DIM * DIM * S::kArrayBytes)[el];
         float Pm[D][DIM];
         const float W = elem_f32<DIM, D, MODEL, ENERGY || DENS, GRAD>(a, gg, vT, C1, D1, mp, Pm, bad);
-        if (ENERGY) ew = fmaf(vT, W, ew);
+        if (ENERGY) ew = __fmul_rn(vT, W);
         if (DENS) dens[eperm ? (int64_t)__ldg(eperm + e) : (int64_t)e] = (double)W;
         if (GRAD) {
           const int sl[4] = {(int)(le.z & 0xffffu), (int)(le.z >> 16), (int)(le.w & 0xffffu), (int)(le.w >> 16)};
@@ -242,75 +249,84 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
           if constexpr (D != 2) rz[sl[0]] = r0[D - 1];
         }
       }
-    }
-    if (ENERGY) {
-      red[tid] = (double)ew;
-      red[blockDim.x + tid] = bv;
-    }
-    __syncthreads();
-    // the element stage of this tile is free: the copies of the tile after next
-    if (tid == 0 && t2 < ntiles) issue_tile(t2, eb, r2, true, true);
-    // the tile's energy partial (the last warp, which has no node work below)
-    if (ENERGY && warp == (int)(blockDim.x >> 5) - 1) {
-      double s, sb;
-      pipe_warp_pair_sum(red, red + blockDim.x, blockDim.x, &s, &sb);
-      if (lane == 0) {
-        epart[t] = s;
-        epart[ntiles + t] = sb;
-        __threadfence();
+      if (ENERGY) {
+        ews[tid] = ew;
+        if (with_b) {
+          const double wb = pipe_warp_sum(bv);
+          if (lane == 0) wbv[warp] = wb;
+        }
       }
     }
+    __syncthreads();
 
-    // C: patch sums, one thread per tile node
-    if (GRAD) {
-      for (int k = tid; k < nt; k += blockDim.x) {
-        const int4 rec = R[k];
-        const int beg = rec.z & 0xffff, cnt = (int)((unsigned)rec.z >> 16);
-        // walk the node's slots from position k mod cnt, wrapping around: consecutive nodes
-        // then start on different shared-memory banks; the order is fixed by the mesh alone
-        float s[D];
-#pragma unroll
-        for (int j = 0; j < D; ++j) s[j] = 0.f;
-        if (cnt > 0) {
-          const int p = (int)((unsigned)k % (unsigned)cnt);
-          int q = beg + p;
-          const int qend = beg + cnt;
-#pragma unroll 4
-          for (int n = 0; n < cnt; ++n) {
-            if constexpr (NXY) {
-              const float2 xy = rxy[q];
-              s[0] = n ? __fadd_rn(s[0], xy.x) : xy.x;
-              s[1] = n ? __fadd_rn(s[1], xy.y) : xy.y;
-            }
-            if constexpr (D != 2) s[D - 1] = n ? __fadd_rn(s[D - 1], rz[q]) : rz[q];
-            q = (q + 1 == qend) ? beg : q + 1;
-          }
-        }
-        const int dst = (rec.w >> 1) - 1;
-        const int64_t i = rec.x;
-        if (dst < 0) {
-          const int64_t o = caller_order ? (int64_t)rec.y : i;
-#pragma unroll
-          for (int j = 0; j < D; ++j) {
-            const double bj = b ? __ldg(b + i * D + j) : 0.0;
-            g[o * D + j] = __ldg(dir + i * D + j) ? 0.0 : (double)s[j] - bj;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < D; ++j) part[(int64_t)dst * D + j] = s[j];
+    if (producer) {
+      // the element stage of this tile is free: the element copies of the tile after next
+      if (issuer && has_t2) issue_elems(r2, eb);
+      // the tile's energy partial, in FP64 from the compute warps' float pairs
+      if (ENERGY) {
+        const double x = pipe_warp_sum_floats(ews, NC);
+        double xb = 0.0;
+        if (with_b) xb = pipe_warp_sum(lane < NCW ? wbv[lane] : 0.0);
+        if (lane == 0) {
+          epart[t] = x;
+          epart[ntiles + t] = xb;
         }
       }
+    } else {
+      // C: patch sums, one thread per tile node
+      if (GRAD) {
+        for (int k = tid; k < nt; k += NC) {
+          const int4 rec = R[k];
+          const int beg = rec.z & 0xffff, cnt = (int)((unsigned)rec.z >> 16);
+          // walk the node's slots from position k mod cnt, wrapping around: consecutive nodes
+          // then start on different shared-memory banks; the order is fixed by the mesh alone
+          float s[D];
+#pragma unroll
+          for (int j = 0; j < D; ++j) s[j] = 0.f;
+          if (cnt > 0) {
+            const int p = (int)((unsigned)k % (unsigned)cnt);
+            auto add = [&](int q, bool first) {
+              if constexpr (NXY) {
+                const float2 xy = rxy[q];
+                s[0] = first ? xy.x : __fadd_rn(s[0], xy.x);
+                s[1] = first ? xy.y : __fadd_rn(s[1], xy.y);
+              }
+              if constexpr (D != 2) s[D - 1] = first ? rz[q] : __fadd_rn(s[D - 1], rz[q]);
+            };
+            add(beg + p, true);
+#pragma unroll 4
+            for (int q = beg + p + 1; q < beg + cnt; ++q) add(q, false);
+#pragma unroll 4
+            for (int q = beg; q < beg + p; ++q) add(q, false);
+          }
+          const int dst = (rec.w >> 1) - 1;
+          const int64_t i = rec.x;
+          if (dst < 0) {
+            const int64_t o = caller_order ? (int64_t)rec.y : i;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+              const double sj = f2d_bits(s[j]);
+              g[o * D + j] = __ldg(dir + i * D + j) ? 0.0 : (b ? sj - __ldg(b + i * D + j) : sj);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < D; ++j) part[(int64_t)dst * D + j] = s[j];
+          }
+        }
+      }
+      cp_async_wait_all();
     }
-    cp_async_wait_all();
     __syncthreads();
-    // N: the next tile's elements and records have arrived (thread 0 waits), and its nodes
-    if (tn < ntiles) {
-      if (tid == 0) {
+
+    // N: the next tile's nodes; the issuer waits for the next tile's elements and for the
+    // records of the tile after next
+    if (has_next) {
+      if (issuer) {
         bool ok = wait_e(eb ^ 1);
-        if (ok && t2 < ntiles) ok = wait_r(r2);
+        if (ok && has_t2) ok = wait_r(r2);
         if (!ok) abort_flag = 1;
       }
-      bv = nodes_to_pairs<DIM, D, MODEL>(V, recs[rn], ntn, us, with_b, disp);
+      if (compute) bv = nodes_to_pairs<DIM, D, MODEL>(V, recs[rn], ntn, us, with_b, disp, NC);
     }
     __syncthreads();
   }
@@ -319,19 +335,20 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
     // a copy did not arrive in time: record it, wait with the full limit for every copy still
     // in flight (nothing may land in shared memory after the block has left), and make J NaN
     cp_async_wait_all();
-    if (tid == 0) {
+    if (issuer) {
       atomicOr(status, kStatusTimeout);
       for (int q = 0; q < 2; ++q)
         if (pendE[q]) mbar_wait_bounded(&barE[q], phE[q] & 1u);
       for (int q = 0; q < 3; ++q)
         if (pendR[q]) mbar_wait_bounded(&barR[q], phR[q] & 1u);
-      if (ENERGY)
-        for (int64_t tq = t; tq < ntiles; tq += G) {
-          epart[tq] = CUDART_NAN;
-          epart[ntiles + tq] = 0.0;
-        }
     }
+    if (ENERGY && producer && lane == 0)
+      for (int64_t tq = t; tq < ntiles; tq += G) {
+        epart[tq] = CUDART_NAN;
+        epart[ntiles + tq] = 0.0;
+      }
   }
+  if (ENERGY && producer && lane == 0) __threadfence();   // this block's partials, before the ticket
   if (bad) atomicOr(status, kStatusDomain);
   if (ENERGY) pipe_finish_energy(epart, ntiles, shift, counter, J, red);
 }
@@ -348,7 +365,7 @@ fe_status launch_tile_f32(fe_ctx* c, const ModelParams& mp, const double* v, dou
               c->wait_limit};
   const bool disp = input_is_disp(c);
   const double* b = c->f_host.empty() ? nullptr : c->b;
-  const int64_t grid = std::min<int64_t>(c->n_tiles, sm_count(c->device));
+  const int64_t grid = std::min<int64_t>(c->n_tiles, (int64_t)kTileBlocksPerSM * sm_count(c->device));
   kern<<<(unsigned)grid, kTileThreads, S::kBytes, c->stream>>>(
       ta, v, c->X, b, c->dir, c->eperm, mp, io_perm(c) != nullptr, disp, disp ? c->bX : 0.0, g,
       reinterpret_cast<float*>(c->tile_part), dens, c->tile_epart, c->counter, J, c->status);

@@ -42,10 +42,11 @@ inline int grid_for(int64_t n, int max_blocks) {
 
 // Element tiles of the fused element + patch kernels (fe_tiles.cu): a tile is a contiguous
 // range of at most kTileElems device-order elements together with the nodes they touch (at
-// most tile_max_nodes(dim)); one block of kTileThreads threads evaluates one tile.
-constexpr int kTileElems = 768;      // 128 hexahedra of six tetrahedra: one octree cell
-constexpr int kTileThreads = 768;    // one thread per element of a tile
-constexpr int tile_max_nodes(int dim) { return dim == 3 ? 256 : 512; }
+// most tile_max_nodes(dim)); the fused kernels run blocks of kTileThreads threads.
+constexpr int kTileElems = 384;      // 64 hexahedra of six tetrahedra: one octree cell
+constexpr int kTileThreads = kTileElems + 32;   // one compute thread per element + a producer warp
+constexpr int kTileBlocksPerSM = 2;  // resident blocks per SM: one computes while the other gathers
+constexpr int tile_max_nodes(int dim) { return dim == 3 ? 160 : 256; }
 // Tiles start on multiples of kTileAlign elements, and the element arrays the tile kernels
 // stage (dphi32, vol32, ...) use the padded stride padded_ne(ne): every staged range then
 // starts 16-byte aligned.

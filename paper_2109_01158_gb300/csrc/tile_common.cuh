@@ -3,8 +3,9 @@
 // asynchronous copies that fill it, the per-tile energy partials and their final sum, and the
 // kernel that completes the gradient of the shared nodes.
 //
-// The fused kernels run one persistent block per SM; block b takes the tiles b, b + G,
-// b + 2G, ... (G blocks).  While it computes tile t it already has in flight:
+// The fused kernels run kTileBlocksPerSM persistent blocks per SM (while one block sums
+// patches or converts nodal values with a few warps, the other's warps compute elements);
+// block b takes the tiles b, b + G, b + 2G, ... (G blocks).  While it computes tile t it already has in flight:
 //   - bulk asynchronous copies (TMA) of the element arrays and node records of the tile after
 //     next (two element stages, three record buffers: the current tile's records are still
 //     read while those of the next two tiles arrive), and
@@ -18,6 +19,16 @@
 
 namespace fe {
 namespace {
+
+// float -> double from the bits (exact, like the conversion instruction, which runs at a low
+// rate on the FP64 unit of this GPU): sign, exponent rebiased by 1023 - 127, significand
+// shifted up by 29.  Zero, subnormals, Inf and NaN take the conversion instruction.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 255u) return (double)f;
+  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu)), (int)(u << 29));
+}
 
 // Shared-memory layout of the pipeline of one block.
 //   E[2]  element stages: DIM*DIM shape-gradient arrays and the volume (EB bytes per element
@@ -85,21 +96,22 @@ __device__ __forceinline__ void pipe_issue_recs(int4* rb, const TileArgs& A, int
   if (nt > 0) bulk_g2s(rb, A.node + k0, (uint32_t)nt * 16u, bar);
 }
 
-// One thread per tile node: per-thread asynchronous copies of the node's v (at its caller or
-// device index), X (Neo-Hookean deformation input) and b (when a load is given) into V.
+// Per-thread asynchronous copies of the nodal values of a tile's nodes into V, spread over
+// the first `nthreads` threads as (node, component) items: for node k and component j,
+// V[k][j] = v_j (at the node's caller or device index), V[k][D + j] = X_j (Neo-Hookean
+// deformation input) and V[k][2D + j] = b_j (when a load is given and the tile owns the
+// node's b_i v_i).
 template <int DIM, int D, int MODEL>
 __device__ __forceinline__ void pipe_gather_nodes(double* V, const int4* rec, int nt, const double* v,
-                                                  const double* X, const double* b, bool caller_order, bool disp) {
-  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+                                                  const double* X, const double* b, bool caller_order, bool disp,
+                                                  int nthreads) {
+  for (int w = threadIdx.x; w < nt * D; w += nthreads) {
+    const int k = w / D, j = w - k * D;
     const int4 r = rec[k];
-    const int64_t i = r.x, src = caller_order ? r.y : r.x;
-    double* o = V + k * 3 * D;
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      cp_async8(o + j, v + src * D + j);
-      if (MODEL == FE_NEOHOOKE && !disp) cp_async8(o + D + j, X + i * DIM + j);
-      if (b && (r.w & 1)) cp_async8(o + 2 * D + j, b + i * D + j);
-    }
+    double* o = V + k * 3 * D + j;
+    cp_async8(o, v + (int64_t)(caller_order ? r.y : r.x) * D + j);
+    if (MODEL == FE_NEOHOOKE && !disp) cp_async8(o + D, X + (int64_t)r.x * DIM + j);
+    if (b && (r.w & 1)) cp_async8(o + 2 * D, b + (int64_t)r.x * D + j);
   }
   cp_async_commit();
 }
@@ -108,6 +120,29 @@ __device__ __forceinline__ double pipe_warp_sum(double x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
   return x;
+}
+
+// One warp: the sum of the n floats x[0..n) as a float pair (TwoSum per addition: the pair
+// holds the exact sum to within a few units of 2^-48 of the terms' magnitudes), converted to
+// FP64 and added over the lanes in a fixed order; valid in lane 0.  An infinite term makes the
+// sum +Inf (TwoSum on Inf would give NaN).
+__device__ __forceinline__ double pipe_warp_sum_floats(const float* x, int n) {
+  const int lane = threadIdx.x & 31;
+  df s = {0.f, 0.f};
+  bool inf = false;
+  for (int k = lane; k < n; k += 32) {
+    const float y = x[k];
+    if (isinf(y)) {
+      inf = true;
+    } else {
+      const df t = two_sum(s.hi, y);
+      s = fast_two_sum(t.hi, __fadd_rn(t.lo, s.lo));
+    }
+  }
+  double d = f2d_bits(s.hi) + f2d_bits(s.lo);
+  d = pipe_warp_sum(d);
+  inf = __any_sync(0xffffffffu, inf);
+  return inf ? CUDART_INF : d;
 }
 
 // One warp: the sums of red[0][0..n) and red[1][0..n) in a fixed order (valid in lane 0).
@@ -124,9 +159,9 @@ __device__ __forceinline__ void pipe_warp_pair_sum(const double* r0, const doubl
 }
 
 // After every block has written its tiles' partials epart[t] (sum |T| W) and epart[ntiles + t]
-// (b.v): the block that arrives last adds them over the tiles in a fixed order and writes
-// J = sum |T| W - (b.v + shift) (shift = b.X when the caller passes displacements).  `red`
-// holds 2 * blockDim.x doubles of shared memory.
+// (b.v) and fenced them: the block that arrives last adds them over the tiles in a fixed order
+// and writes J = sum |T| W - (b.v + shift) (shift = b.X when the caller passes displacements).
+// `red` holds 2 * blockDim.x doubles of shared memory.
 __device__ __forceinline__ void pipe_finish_energy(const double* epart, int64_t ntiles, double shift,
                                                    unsigned* counter, double* J, double* red) {
   __shared__ bool am_last;
@@ -161,7 +196,7 @@ struct PartF32 {
   using T = float;
   float s = 0.f;
   __device__ __forceinline__ void add(float x, bool first) { s = first ? x : __fadd_rn(s, x); }
-  __device__ __forceinline__ double value() const { return (double)s; }
+  __device__ __forceinline__ double value() const { return f2d_bits(s); }
 };
 
 struct PartDF {
@@ -192,8 +227,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_shared(int64_t nshared, const
     Acc acc;
     for (int32_t p = p0; p < p1; ++p) acc.add(__ldg(part + (int64_t)__ldg(spart + p) * D + j), p == p0);
     const int64_t dst = perm ? (int64_t)__ldg(perm + i) : i;
-    const double bj = b ? __ldg(b + i * D + j) : 0.0;
-    g[dst * D + j] = __ldg(dir + i * D + j) ? 0.0 : acc.value() - bj;
+    g[dst * D + j] = __ldg(dir + i * D + j) ? 0.0 : (b ? acc.value() - __ldg(b + i * D + j) : acc.value());
   }
 }
 
