@@ -598,7 +598,7 @@ fe_status fe_precompute(fe_ctx* c, unsigned precisions) {
       return st;
     }
   }
-  if ((precisions & (1u << FE_DF64)) && (st = dev_alloc(c, &c->u_df, nn * dp))) {
+  if ((precisions & ((1u << FE_DF64) | (1u << FE_F32_COMP))) && (st = dev_alloc(c, &c->u_df, nn * dp))) {
     free_precompute(c);
     return st;
   }

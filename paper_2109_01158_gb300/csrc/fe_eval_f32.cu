@@ -1,25 +1,29 @@
 // fe_eval_f32.cu -- the FP32 path (FE_F32_COMP; a precision variant not in the paper): the
 // energy J(v) = sum |T| W(F_T) - b.v and its exact gradient (Sec. 5 and 6.2) with the element
-// arithmetic in float (elem_f32.cuh) and FP64 energy sums, in one fused persistent launch per
-// call plus a small completion launch for the gradient of nodes on tile boundaries.
+// arithmetic in float (elem_f32.cuh) and FP64 energy sums.
 //
-// Persistent blocks (kTileBlocksPerSM per SM) walk their element tiles (fe_tiles.cu,
-// tile_common.cuh).  Per tile:
-//   B  one thread per element: H from float-pair differences of u, W and |T| dW/dF in float,
-//      and the local forces r_{T,l} = |T| dW/dF grad(phi_l) written to the element's local
-//      slots in shared memory;
-//   C  one thread per tile node: the node's local slots summed in float in a fixed order; a
-//      node whose patch lies in the tile gets g_i = sum - b_i (0 on Dirichlet dofs), a shared
-//      node leaves its partial sum (slots of one tile are consecutive: coalesced writes);
-//   N  the next tile's nodes: u = v - X in FP64 (v in the caller's or the device numbering;
-//      u = v for the p-Laplacian or a displacement input), kept as float pairs (hi, lo) so that
-//      differences across an element round only once, and the b_i v_i of the nodes this tile
-//      owns;
-//   the tile's |T| W (summed per thread in float, then per tile in FP64) and b.v go to its
-//   energy partial; the last block adds the partials in tile order.
-// k_tile_shared adds the shared nodes' partials in tile order.  No intermediate leaves the
-// chip except those partials, and every sum has a fixed order (bitwise reproducible, whatever
-// the number of blocks).
+// Three launches per call:
+//   k_pairs32     one thread per node: u = v - X in FP64 (v in the caller's or the device
+//                 numbering; u = v for the p-Laplacian or a displacement input), stored as
+//                 float pairs (hi, lo) so that differences across an element round only once,
+//                 and the block partials of b.v;
+//   k_tile_f32    one persistent block per SM walks its element tiles (fe_tiles.cu,
+//                 tile_common.cuh) with specialised warps:
+//                   node warps copy the next tile's float pairs into shared memory;
+//                   element warps, one thread per element: H from float-pair differences of
+//                      u, W and |T| dW/dF in float, and the local forces
+//                      r_{T,l} = |T| dW/dF grad(phi_l) written to the element's local slots in
+//                      shared memory;
+//                   node warps then sum the patches, one thread per tile node: the node's
+//                      local slots summed in float in a fixed order; a node whose patch lies
+//                      in the tile gets g_i = sum - b_i (0 on Dirichlet dofs), a shared node
+//                      leaves its partial sum;
+//                   the producer warp issues the bulk copies and adds the tile's |T| W into its
+//                      energy partial (float pairs per lane, FP64 across lanes); the last block
+//                      adds the partials in tile order;
+//   k_tile_shared adds the shared nodes' partials in tile order.
+// The local forces never leave the chip (only the shared nodes' partials do), and every sum
+// has a fixed order: bitwise reproducible whatever the number of blocks.
 #include "elem_f32.cuh"
 #include "fe_internal.cuh"
 #include "tile_common.cuh"
@@ -31,21 +35,22 @@ template <int DIM, int D>
 struct Pipe32 {
   static constexpr int DP = D == 3 ? 4 : D;   // float pairs per node record (padded)
   static constexpr int NXY = D >= 2 ? 2 : 0;  // components of r kept as float2
-  // r: components 0 and 1 as float2 per slot (D >= 2), the last (D = 1 or 3) as float
+  // nodal values: DP float pairs per node; r: components 0 and 1 as float2 per slot (D >= 2),
+  // the last (D = 1 or 3) as float
   using S = TilePipe<DIM, D, 4, DP * 8, D * 4>;
 };
 
 template <int D>
-__device__ __forceinline__ void load_pairs(const float2* us, int k, float2 (&w)[D]) {
+__device__ __forceinline__ void load_pairs_g(const float2* __restrict__ u, int64_t n, float2 (&w)[D]) {
   if constexpr (D == 1) {
-    w[0] = us[k];
+    w[0] = __ldg(u + n);
   } else if constexpr (D == 2) {
-    const float4 a = reinterpret_cast<const float4*>(us)[k];
+    const float4 a = __ldg(reinterpret_cast<const float4*>(u) + n);
     w[0] = make_float2(a.x, a.y);
     w[1] = make_float2(a.z, a.w);
   } else {
-    const float4* p = reinterpret_cast<const float4*>(us) + 2 * k;
-    const float4 a = p[0], b = p[1];
+    const float4* p = reinterpret_cast<const float4*>(u) + 2 * n;
+    const float4 a = __ldg(p), b = __ldg(p + 1);
     w[0] = make_float2(a.x, a.y);
     w[1] = make_float2(a.z, a.w);
     w[2] = make_float2(b.x, b.y);
@@ -77,153 +82,230 @@ __device__ __forceinline__ float2 split_double(double d) {
   return make_float2(hi, lo);
 }
 
-// N: the float-pair records of a tile's nodes from the copied values V, as (node, component)
-// items over the compute threads; returns this thread's b_i v_i over the nodes the tile owns.
+// u (device order) as float pairs, DP pairs per node, one node per thread; block partials of
+// b.v (b in device order, v read at the caller's index when perm is given; the grid depends on
+// nn only, so the partials are the same on every run).
 template <int DIM, int D, int MODEL>
-__device__ __forceinline__ double nodes_to_pairs(const double* V, const int4* rec, int nt, float2* us, bool with_b,
-                                                 bool disp, int nthreads) {
+__global__ void __launch_bounds__(kThreads) k_pairs32(int64_t nn, const double* __restrict__ v,
+                                                      const double* __restrict__ X, const int32_t* __restrict__ perm,
+                                                      const double* __restrict__ b, float2* __restrict__ u, bool disp,
+                                                      double* __restrict__ bv_partials) {
   constexpr int DP = Pipe32<DIM, D>::DP;
-  double bv = 0.0;
-  for (int w = threadIdx.x; w < nt * D; w += nthreads) {
-    const int k = w / D, j = w - k * D;
-    const double* o = V + k * 3 * D;
-    const double vj = o[j];
-    us[k * DP + j] = split_double((MODEL == FE_NEOHOOKE && !disp) ? vj - o[D + j] : vj);
-    if (with_b && (rec[k].w & 1)) bv = fma(o[2 * D + j], vj, bv);
+  __shared__ double sh[kThreads / 32];
+  double dot = 0.0;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // one node per thread
+  if (i < nn) {
+    const int64_t src = perm ? (int64_t)__ldg(perm + i) : i;
+    float2 w[DP];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const double vj = __ldg(v + src * D + j);
+      w[j] = split_double((MODEL == FE_NEOHOOKE && !disp) ? vj - __ldg(X + i * DIM + j) : vj);
+      if (b) dot = fma(__ldg(b + i * D + j), vj, dot);
+    }
+    if constexpr (DP == 1) {
+      u[i] = w[0];
+    } else if constexpr (DP == 2) {
+      reinterpret_cast<float4*>(u)[i] = make_float4(w[0].x, w[0].y, w[1].x, w[1].y);
+    } else {
+      float4* o = reinterpret_cast<float4*>(u) + 2 * i;
+      o[0] = make_float4(w[0].x, w[0].y, w[1].x, w[1].y);
+      o[1] = make_float4(w[2].x, w[2].y, 0.f, 0.f);
+    }
   }
-  return bv;
+  if (b) {
+    // a fixed tree per block (the grid depends on nn only)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = dot;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      dot = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+      if (threadIdx.x == 0) bv_partials[blockIdx.x] = dot;
+    }
+  }
 }
 
-// The block: warps 0 .. kTileElems/32 - 1 compute (one thread per element of a tile, and the
-// node work as (node, component) items); the last warp is the producer: its lane 0 issues and
-// waits for every bulk copy and loads the tiles' ranges, and the warp adds each tile's energy
-// partial.  No compute thread waits on a copy barrier.
+// Barriers of the tile pipeline (index: buffer of the tile).
+struct PipeBars {
+  uint64_t e_full[2], e_empty[2];    // element stage: TMA landed / element warps done
+  uint64_t r_full[3], r_empty[3];    // node records: TMA landed / node warps done
+  uint64_t u_full[2], u_empty[2];    // nodal values: node warps wrote / element warps done
+  uint64_t rs_full[2], rs_empty[2];  // local forces and energies: element warps wrote / node
+                                     // warps and producer done
+};
+
+// The block: warps 0 .. kTileElems/32 - 1 are element warps (one thread per element of a
+// tile); the next kTileNodeWarps are node warps (they copy the next tile's nodal values into
+// shared memory, then sum the current tile's patches); the last warp is the producer (its lane
+// 0 issues every bulk copy; the warp adds each tile's energy partial).  The roles hand buffers
+// over through the mbarriers of PipeBars; every wait is bounded and gives up when another
+// thread has given up, so a lost copy ends the kernel with FE_ETIMEOUT instead of a hang.
 template <int DIM, int D, int MODEL, bool ENERGY, bool GRAD, bool DENS>
-__global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_f32(
-    TileArgs ta, const double* __restrict__ v, const double* __restrict__ X, const double* __restrict__ b,
-    const uint8_t* __restrict__ dir, const int32_t* __restrict__ eperm, ModelParams mp, bool caller_order,
-    bool disp, double shift, double* __restrict__ g, float* __restrict__ part, double* __restrict__ dens,
-    double* epart, unsigned* counter, double* J, int* status) {
+__global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
+    TileArgs ta, const float2* __restrict__ upairs, const double* __restrict__ b, const uint8_t* __restrict__ dir,
+    const int32_t* __restrict__ eperm, ModelParams mp, bool caller_order, double* __restrict__ g,
+    float* __restrict__ part, double* __restrict__ dens, double* epart, const double* bvp, int nbv, double shift,
+    unsigned* counter, double* J, int* status) {
   using P = Pipe32<DIM, D>;
   using S = typename P::S;
   constexpr int K = DIM + 1, NXY = P::NXY, DP = P::DP;
-  constexpr int NC = kTileElems;         // compute threads
-  constexpr int NCW = NC / 32;           // compute warps
+  constexpr int NE = kTileElems, NEW = NE / 32;              // element threads and warps
+  constexpr int NN = 32 * kTileNodeWarps;                    // node threads
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t barE[2], barR[3];
-  __shared__ __align__(16) int4 recs[3][S::kNodes];
-  __shared__ int4 info[3];               // {e0, e1, k0, nt} of the tile in each record slot
-  __shared__ float ews[NC];               // |T| W of the tile's elements
-  __shared__ double wbv[NCW];            // per compute warp: its b.v of the tile
-  __shared__ double red[2 * kTileThreads];
-  __shared__ int abort_flag;
-  float2* us = reinterpret_cast<float2*>(smem + S::kU);
-  double* V = reinterpret_cast<double*>(smem + S::kV);
-  float2* rxy = reinterpret_cast<float2*>(smem + S::kRs);
-  float* rz = reinterpret_cast<float*>(smem + S::kRs + NXY * 4 * S::kSlots);
+  __shared__ PipeBars bars;
+  __shared__ int4 info[3];        // {e0, e1, k0, nt} of the tile whose records are in R[slot]
+  __shared__ volatile int abort_flag;
   const int G = gridDim.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool compute = tid < NC, producer = warp == NCW, issuer = tid == NC;
+  const bool elem_warp = warp < NEW, node_warp = !elem_warp && warp < NEW + kTileNodeWarps;
+  const bool issuer = tid == NE + NN;
   const int64_t ntiles = ta.ntiles;
-  const bool with_b = ENERGY && b != nullptr;
-  // the issuer's view of the copy pipeline: completed phases and copies in flight per buffer
-  uint32_t phE[2] = {0u, 0u}, phR[3] = {0u, 0u, 0u};
-  bool pendE[2] = {false, false}, pendR[3] = {false, false, false};
-  auto issue_records = [&](int64_t tq, int slot) {
-    const int e0 = __ldg(ta.ebeg + tq), e1 = __ldg(ta.ebeg + tq + 1);
-    const int k0 = __ldg(ta.nbeg + tq), nt = __ldg(ta.nbeg + tq + 1) - k0;
-    info[slot] = make_int4(e0, e1, k0, nt);
-    pipe_issue_recs(recs[slot], ta, k0, nt, &barR[slot]);
-    pendR[slot] = true;
+  const int my_tiles = (int)((ntiles - blockIdx.x + G - 1) / G);   // tiles blockIdx.x + i G
+  auto tile_of = [&](int i) { return (int64_t)blockIdx.x + (int64_t)i * G; };
+  auto E = [&](int i) { return smem + S::kE + (i & 1) * S::kEBytes; };
+  auto R = [&](int i) { return reinterpret_cast<int4*>(smem + S::kR + (i % 3) * S::kRBytes); };
+  auto U = [&](int i) { return reinterpret_cast<float2*>(smem + S::kU + (i & 1) * S::kUBytes); };
+  auto RXY = [&](int i) { return reinterpret_cast<float2*>(smem + S::kRs + (i & 1) * S::kRsBytes); };
+  auto RZ = [&](int i) {
+    return reinterpret_cast<float*>(smem + S::kRs + (i & 1) * S::kRsBytes + NXY * 4 * S::kSlots);
   };
-  auto issue_elems = [&](int slot, int eb) {
-    const int4 in = info[slot];
-    pipe_issue_elems<S, 4>(smem + S::kE + eb * S::kEBytes, ta, in.x, in.y, &barE[eb]);
-    pendE[eb] = true;
-  };
-  auto wait_e = [&](int eb) {
-    const bool ok = mbar_wait_bounded(&barE[eb], phE[eb] & 1u, ta.wait_limit);
-    if (ok) { ++phE[eb]; pendE[eb] = false; }
+  auto EW = [&](int i) { return reinterpret_cast<float*>(smem + S::kEw + (i & 1) * S::kEwBytes); };
+  // every thread of a warp calls wait() together and gets the same answer (the warp leaves the
+  // pipeline as a whole, so no lane is left behind in a warp-wide operation)
+  bool ok = true;
+  auto wait = [&](uint64_t* bar, int use) {   // the use-th completion of `bar`
+    bool w = ok && mbar_wait_or_abort(bar, (uint32_t)use & 1u, ta.wait_limit, &abort_flag);
+    if (ok && !w && !abort_flag) {
+      abort_flag = 1;
+      atomicOr(status, kStatusTimeout);
+    }
+    ok = __all_sync(0xffffffffu, w);
     return ok;
   };
-  auto wait_r = [&](int rb) {
-    const bool ok = mbar_wait_bounded(&barR[rb], phR[rb] & 1u, ta.wait_limit);
-    if (ok) { ++phR[rb]; pendR[rb] = false; }
+  // the same for a wait done by lane 0 alone (the result is broadcast to the warp)
+  auto wait_lane0 = [&](uint64_t* bar, int use) {
+    bool w = true;
+    if (lane == 0) {
+      w = ok && mbar_wait_or_abort(bar, (uint32_t)use & 1u, ta.wait_limit, &abort_flag);
+      if (ok && !w && !abort_flag) {
+        abort_flag = 1;
+        atomicOr(status, kStatusTimeout);
+      }
+    }
+    ok = __shfl_sync(0xffffffffu, w, 0) && ok;
     return ok;
   };
-
-  int64_t t = blockIdx.x;
+  // the issuer's copies: how many were issued into each buffer (to drain them on abort)
+  int nE[2] = {0, 0}, nR[3] = {0, 0, 0};
+  auto issue_elems = [&](int i) {
+    const int4 in = info[i % 3];
+    pipe_issue_elems<S, 4>(E(i), ta, in.x, in.y, &bars.e_full[i & 1]);
+    ++nE[i & 1];
+  };
+  auto issue_recs = [&](int i) {
+    const int64_t tq = tile_of(i);
+    const int k0 = __ldg(ta.nbeg + tq);
+    info[i % 3] = make_int4(__ldg(ta.ebeg + tq), __ldg(ta.ebeg + tq + 1), k0, __ldg(ta.nbeg + tq + 1) - k0);
+    pipe_issue_recs(R(i), ta, k0, info[i % 3].w, &bars.r_full[i % 3]);
+    ++nR[i % 3];
+  };
+  if (tid == 0) abort_flag = 0;
   if (issuer) {
-    abort_flag = 0;
-    for (int q = 0; q < 2; ++q) mbar_init(&barE[q], 1);
-    for (int q = 0; q < 3; ++q) mbar_init(&barR[q], 1);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&bars.e_full[q], 1);
+      mbar_init(&bars.e_empty[q], NEW);
+      mbar_init(&bars.u_full[q], kTileNodeWarps);
+      mbar_init(&bars.u_empty[q], NEW);
+      mbar_init(&bars.rs_full[q], NEW);
+      mbar_init(&bars.rs_empty[q], NEW + 1);
+    }
+    for (int q = 0; q < 3; ++q) {
+      mbar_init(&bars.r_full[q], 1);
+      mbar_init(&bars.r_empty[q], NEW);
+    }
     mbar_init_fence();
-    issue_records(t, 0);
-    issue_elems(0, 0);
-    if (t + G < ntiles) {
-      issue_records(t + G, 1);
-      issue_elems(1, 1);
-    }
-    if (!wait_r(0)) abort_flag = 1;
-  }
-  __syncthreads();
-  double bv = 0.0;   // this thread's b_i v_i of the current tile
-  if (!abort_flag) {
-    if (compute) {
-      pipe_gather_nodes<DIM, D, MODEL>(V, recs[0], info[0].w, v, X, with_b ? b : nullptr, caller_order, disp, NC);
-      cp_async_wait_all();
-    }
-    __syncthreads();
-    if (compute) bv = nodes_to_pairs<DIM, D, MODEL>(V, recs[0], info[0].w, us, with_b, disp, NC);
-    if (issuer) {
-      bool ok = wait_e(0);
-      if (ok && t + G < ntiles) ok = wait_r(1);
-      if (!ok) abort_flag = 1;
-    }
   }
   __syncthreads();
 
   bool bad = false;
-  const float C1 = (float)mp.C1, D1 = (float)mp.D1;
-  int it = 0;
-  for (; t < ntiles && !abort_flag; t += G, ++it) {
-    const int eb = it & 1, rb = it % 3, rn = (it + 1) % 3, r2 = (it + 2) % 3;
-    const bool has_next = t + G < ntiles, has_t2 = t + 2 * (int64_t)G < ntiles;
-    const int4 in = info[rb];
-    const int e0 = in.x, e1 = in.y, nt = in.w;
-    const int ntn = has_next ? info[rn].w : 0;
-    const int4* R = recs[rb];
-    const unsigned char* E = smem + S::kE + eb * S::kEBytes;
-
-    if (producer) {
-      // the records of the tile after next (slot r2 held the previous tile's)
-      if (issuer && has_t2) issue_records(t + 2 * (int64_t)G, r2);
-    } else {
-      // the next tile's nodal values start copying
-      if (has_next)
-        pipe_gather_nodes<DIM, D, MODEL>(V, recs[rn], ntn, v, X, with_b ? b : nullptr, caller_order, disp, NC);
-
-      // B: one thread per element
-      float ew = 0.f;   // this thread's |T| W
-      const int e = e0 + tid;
-      if (e < e1) {
-        const int el = tid;
-        const uint4 le = reinterpret_cast<const uint4*>(E + S::kElemOff)[el];
+  if (warp == NEW + kTileNodeWarps) {
+    // producer warp: lane 0 issues the bulk copies; the warp adds the tiles' energy partials
+    if (issuer) {
+      // records of the first three tiles, elements of the first two
+      for (int i = 0; i < 3 && i < my_tiles; ++i) issue_recs(i);
+      for (int i = 0; i < 2 && i < my_tiles; ++i) issue_elems(i);
+    }
+    for (int i = 0; i < my_tiles; ++i) {
+      // the element stage of tile i is free once the element warps are done with it (the same
+      // moment as their forces and energies are complete)
+      if (i + 2 < my_tiles) {
+        if (!wait_lane0(&bars.e_empty[i & 1], i >> 1)) break;
+        if (issuer) issue_elems(i + 2);
+      }
+      if (!wait(&bars.rs_full[i & 1], i >> 1)) break;
+      if (ENERGY) {
+        const double x = pipe_warp_sum_floats(EW(i), NE);   // FP64 across lanes from float pairs
+        if (lane == 0) epart[tile_of(i)] = x;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars.rs_empty[i & 1]);
+      // the record slot of tile i is free once the node warps have summed its patches
+      if (i + 3 < my_tiles) {
+        if (!wait_lane0(&bars.r_empty[i % 3], i / 3)) break;
+        if (issuer) issue_recs(i + 3);
+      }
+    }
+  } else if (node_warp) {
+    const int ntid = tid - NE;
+    // the nodal values of tile i (its records must have landed) into U(i)
+    auto gather = [&](int i) {
+      if (!wait(&bars.r_full[i % 3], i / 3)) return false;
+      if (i >= 2 && !wait(&bars.u_empty[i & 1], (i >> 1) - 1)) return false;
+      const int4* rec = R(i);
+      float2* us = U(i);
+      const int nt = info[i % 3].w;
+      for (int k = ntid; k < nt; k += NN) {
+        float2 w[D];
+        load_pairs_g<D>(upairs, rec[k].x, w);
+#pragma unroll
+        for (int j = 0; j < D; ++j) us[k * DP + j] = w[j];
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars.u_full[i & 1]);
+      return true;
+    };
+    if (my_tiles > 0) gather(0);
+    for (int i = 1; i < my_tiles && ok; ++i)
+      if (!gather(i)) break;
+  } else if (elem_warp) {
+    // B: one thread per element of tile i
+    const float C1 = (float)mp.C1, D1 = (float)mp.D1;
+    for (int i = 0; i < my_tiles && ok; ++i) {
+      if (!wait(&bars.e_full[i & 1], i >> 1) || !wait(&bars.u_full[i & 1], i >> 1)) break;
+      if (i >= 2 && !wait(&bars.rs_empty[i & 1], (i >> 1) - 1)) break;
+      const int4 in = info[i % 3];
+      const unsigned char* St = E(i);
+      const float2* us = U(i);
+      float2* rxy = RXY(i);
+      float* rz = RZ(i);
+      float ew = 0.f;
+      const int e = in.x + tid;
+      if (e < in.y) {
+        const uint4 le = reinterpret_cast<const uint4*>(St + S::kElemOff)[tid];
         const int lid[4] = {(int)(le.x & 0xffffu), (int)(le.x >> 16), (int)(le.y & 0xffffu), (int)(le.y >> 16)};
-        float2 u0[D], ul[D];
-        load_pairs<D>(us, lid[0], u0);
         float a[DIM][D];
 #pragma unroll
-        for (int l = 1; l < K; ++l) {
-          load_pairs<D>(us, lid[l], ul);
+        for (int l = 1; l < K; ++l)
 #pragma unroll
-          for (int j = 0; j < D; ++j) a[l - 1][j] = pair_diff(ul[j], u0[j]);
-        }
+          for (int j = 0; j < D; ++j) a[l - 1][j] = pair_diff(us[lid[l] * DP + j], us[lid[0] * DP + j]);
         float gg[DIM][DIM];
 #pragma unroll
         for (int l = 0; l < DIM; ++l)
 #pragma unroll
-          for (int m = 0; m < DIM; ++m) gg[l][m] = reinterpret_cast<const float*>(E + (l * DIM + m) * S::kArrayBytes)[el];
-        const float vT = reinterpret_cast<const float*>(E + DIM * DIM * S::kArrayBytes)[el];
+          for (int m = 0; m < DIM; ++m) gg[l][m] = reinterpret_cast<const float*>(St + (l * DIM + m) * S::kArrayBytes)[tid];
+        const float vT = reinterpret_cast<const float*>(St + DIM * DIM * S::kArrayBytes)[tid];
         float Pm[D][DIM];
         const float W = elem_f32<DIM, D, MODEL, ENERGY || DENS, GRAD>(a, gg, vT, C1, D1, mp, Pm, bad);
         if (ENERGY) ew = __fmul_rn(vT, W);
@@ -249,112 +331,76 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_f32(
           if constexpr (D != 2) rz[sl[0]] = r0[D - 1];
         }
       }
-      if (ENERGY) {
-        ews[tid] = ew;
-        if (with_b) {
-          const double wb = pipe_warp_sum(bv);
-          if (lane == 0) wbv[warp] = wb;
-        }
+      if (ENERGY) EW(i)[tid] = ew;
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bars.e_empty[i & 1]);
+        mbar_arrive(&bars.u_empty[i & 1]);
+        mbar_arrive(&bars.rs_full[i & 1]);
       }
-    }
-    __syncthreads();
-
-    if (producer) {
-      // the element stage of this tile is free: the element copies of the tile after next
-      if (issuer && has_t2) issue_elems(r2, eb);
-      // the tile's energy partial, in FP64 from the compute warps' float pairs
-      if (ENERGY) {
-        const double x = pipe_warp_sum_floats(ews, NC);
-        double xb = 0.0;
-        if (with_b) xb = pipe_warp_sum(lane < NCW ? wbv[lane] : 0.0);
-        if (lane == 0) {
-          epart[t] = x;
-          epart[ntiles + t] = xb;
-        }
-      }
-    } else {
-      // C: patch sums, one thread per tile node
+      // C: patch sums of tile i once every element warp has written its forces, one thread
+      // per (tile node, component)
+      if (!wait(&bars.rs_full[i & 1], i >> 1)) break;
       if (GRAD) {
-        for (int k = tid; k < nt; k += NC) {
-          const int4 rec = R[k];
+        const int4* Rr = R(i);
+        const int nt = in.w;
+        for (int w = tid; w < nt * D; w += NE) {
+          const int k = w / D, j = w - k * D;
+          const int4 rec = Rr[k];
           const int beg = rec.z & 0xffff, cnt = (int)((unsigned)rec.z >> 16);
+          const float* col = (NXY && j < NXY) ? reinterpret_cast<const float*>(rxy) + j : rz;
+          const int str = (NXY && j < NXY) ? 2 : 1;
           // walk the node's slots from position k mod cnt, wrapping around: consecutive nodes
           // then start on different shared-memory banks; the order is fixed by the mesh alone
-          float s[D];
-#pragma unroll
-          for (int j = 0; j < D; ++j) s[j] = 0.f;
+          float sum = 0.f;
           if (cnt > 0) {
             const int p = (int)((unsigned)k % (unsigned)cnt);
-            auto add = [&](int q, bool first) {
-              if constexpr (NXY) {
-                const float2 xy = rxy[q];
-                s[0] = first ? xy.x : __fadd_rn(s[0], xy.x);
-                s[1] = first ? xy.y : __fadd_rn(s[1], xy.y);
-              }
-              if constexpr (D != 2) s[D - 1] = first ? rz[q] : __fadd_rn(s[D - 1], rz[q]);
-            };
-            add(beg + p, true);
+            sum = col[(beg + p) * str];
 #pragma unroll 4
-            for (int q = beg + p + 1; q < beg + cnt; ++q) add(q, false);
+            for (int q = beg + p + 1; q < beg + cnt; ++q) sum = __fadd_rn(sum, col[q * str]);
 #pragma unroll 4
-            for (int q = beg; q < beg + p; ++q) add(q, false);
+            for (int q = beg; q < beg + p; ++q) sum = __fadd_rn(sum, col[q * str]);
           }
           const int dst = (rec.w >> 1) - 1;
-          const int64_t i = rec.x;
+          const int64_t n = rec.x;
           if (dst < 0) {
-            const int64_t o = caller_order ? (int64_t)rec.y : i;
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-              const double sj = f2d_bits(s[j]);
-              g[o * D + j] = __ldg(dir + i * D + j) ? 0.0 : (b ? sj - __ldg(b + i * D + j) : sj);
-            }
+            const int64_t o = caller_order ? (int64_t)rec.y : n;
+            const double sj = f2d_bits(sum);
+            g[o * D + j] = __ldg(dir + n * D + j) ? 0.0 : (b ? sj - __ldg(b + n * D + j) : sj);
           } else {
-#pragma unroll
-            for (int j = 0; j < D; ++j) part[(int64_t)dst * D + j] = s[j];
+            part[(int64_t)dst * D + j] = sum;
           }
         }
       }
-      cp_async_wait_all();
-    }
-    __syncthreads();
-
-    // N: the next tile's nodes; the issuer waits for the next tile's elements and for the
-    // records of the tile after next
-    if (has_next) {
-      if (issuer) {
-        bool ok = wait_e(eb ^ 1);
-        if (ok && has_t2) ok = wait_r(r2);
-        if (!ok) abort_flag = 1;
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bars.rs_empty[i & 1]);
+        mbar_arrive(&bars.r_empty[i % 3]);
       }
-      if (compute) bv = nodes_to_pairs<DIM, D, MODEL>(V, recs[rn], ntn, us, with_b, disp, NC);
     }
-    __syncthreads();
   }
 
+  __syncthreads();
   if (abort_flag) {
-    // a copy did not arrive in time: record it, wait with the full limit for every copy still
-    // in flight (nothing may land in shared memory after the block has left), and make J NaN
-    cp_async_wait_all();
+    // a wait gave up: wait with the full limit for every bulk copy still in flight (nothing may
+    // land in shared memory after the block has left) and make J NaN
     if (issuer) {
-      atomicOr(status, kStatusTimeout);
       for (int q = 0; q < 2; ++q)
-        if (pendE[q]) mbar_wait_bounded(&barE[q], phE[q] & 1u);
+        if (nE[q] > 0) mbar_wait_bounded(&bars.e_full[q], (uint32_t)(nE[q] - 1) & 1u);
       for (int q = 0; q < 3; ++q)
-        if (pendR[q]) mbar_wait_bounded(&barR[q], phR[q] & 1u);
+        if (nR[q] > 0) mbar_wait_bounded(&bars.r_full[q], (uint32_t)(nR[q] - 1) & 1u);
+      if (ENERGY)
+        for (int i = 0; i < my_tiles; ++i) epart[tile_of(i)] = CUDART_NAN;
     }
-    if (ENERGY && producer && lane == 0)
-      for (int64_t tq = t; tq < ntiles; tq += G) {
-        epart[tq] = CUDART_NAN;
-        epart[ntiles + tq] = 0.0;
-      }
   }
-  if (ENERGY && producer && lane == 0) __threadfence();   // this block's partials, before the ticket
+  if (ENERGY && warp == NEW + kTileNodeWarps && lane == 0) __threadfence();   // partials before the ticket
   if (bad) atomicOr(status, kStatusDomain);
-  if (ENERGY) pipe_finish_energy(epart, ntiles, shift, counter, J, red);
+  if (ENERGY) pipe_finish_energy(epart, ntiles, bvp, nbv, shift, counter, J, reinterpret_cast<double*>(smem + S::kRs));
 }
 
 template <int DIM, int D, int MODEL, bool E, bool G, bool DN>
-fe_status launch_tile_f32(fe_ctx* c, const ModelParams& mp, const double* v, double* J, double* dens, double* g) {
+fe_status launch_tile_f32(fe_ctx* c, const ModelParams& mp, double* J, double* dens, double* g, const double* bvp,
+                          int nbv) {
   using S = typename Pipe32<DIM, D>::S;
   auto kern = k_tile_f32<DIM, D, MODEL, E, G, DN>;
   static std::atomic<uint64_t> smem_set{0};
@@ -365,10 +411,10 @@ fe_status launch_tile_f32(fe_ctx* c, const ModelParams& mp, const double* v, dou
               c->wait_limit};
   const bool disp = input_is_disp(c);
   const double* b = c->f_host.empty() ? nullptr : c->b;
-  const int64_t grid = std::min<int64_t>(c->n_tiles, (int64_t)kTileBlocksPerSM * sm_count(c->device));
+  const int64_t grid = std::min<int64_t>(c->n_tiles, sm_count(c->device));
   kern<<<(unsigned)grid, kTileThreads, S::kBytes, c->stream>>>(
-      ta, v, c->X, b, c->dir, c->eperm, mp, io_perm(c) != nullptr, disp, disp ? c->bX : 0.0, g,
-      reinterpret_cast<float*>(c->tile_part), dens, c->tile_epart, c->counter, J, c->status);
+      ta, c->u_df, b, c->dir, c->eperm, mp, io_perm(c) != nullptr, g, reinterpret_cast<float*>(c->tile_part), dens,
+      c->tile_epart, bvp, nbv, disp ? c->bX : 0.0, c->counter, J, c->status);
   return cuda_check(cudaGetLastError(), "f32 tile launch");
 }
 
@@ -377,21 +423,29 @@ fe_status eval32_t(fe_ctx* c, const double* v, double* J, double* dens, double* 
                    bool want_grad) {
   const ModelParams mp = model_params(c);
   const bool E = want_energy, G = want_grad, Dn = dens != nullptr;
+  const double* b = c->f_host.empty() ? nullptr : c->b;
+  const int nb_node = (int)std::max<int64_t>((c->nn + kThreads - 1) / kThreads, 1);
+  double* bvp = c->tile_bvp;
+  prof_begin(c, kStagePrep);
+  k_pairs32<DIM, D, MODEL><<<nb_node, kThreads, 0, c->stream>>>(c->nn, v, c->X, io_perm(c), E ? b : nullptr, c->u_df,
+                                                                 input_is_disp(c), bvp);
+  prof_end(c, kStagePrep);
+  c->launches++;
+  const double* bv_in = (E && b) ? bvp : nullptr;
   prof_begin(c, kStageElem);
   fe_status es;
-  if (E && G && Dn) es = launch_tile_f32<DIM, D, MODEL, true, true, true>(c, mp, v, J, dens, g);
-  else if (E && G) es = launch_tile_f32<DIM, D, MODEL, true, true, false>(c, mp, v, J, dens, g);
-  else if (E && Dn) es = launch_tile_f32<DIM, D, MODEL, true, false, true>(c, mp, v, J, dens, g);
-  else if (E) es = launch_tile_f32<DIM, D, MODEL, true, false, false>(c, mp, v, J, dens, g);
-  else if (G && Dn) es = launch_tile_f32<DIM, D, MODEL, false, true, true>(c, mp, v, J, dens, g);
-  else if (G) es = launch_tile_f32<DIM, D, MODEL, false, true, false>(c, mp, v, J, dens, g);
-  else es = launch_tile_f32<DIM, D, MODEL, false, false, true>(c, mp, v, J, dens, g);
+  if (E && G && Dn) es = launch_tile_f32<DIM, D, MODEL, true, true, true>(c, mp, J, dens, g, bv_in, nb_node);
+  else if (E && G) es = launch_tile_f32<DIM, D, MODEL, true, true, false>(c, mp, J, dens, g, bv_in, nb_node);
+  else if (E && Dn) es = launch_tile_f32<DIM, D, MODEL, true, false, true>(c, mp, J, dens, g, bv_in, nb_node);
+  else if (E) es = launch_tile_f32<DIM, D, MODEL, true, false, false>(c, mp, J, dens, g, bv_in, nb_node);
+  else if (G && Dn) es = launch_tile_f32<DIM, D, MODEL, false, true, true>(c, mp, J, dens, g, bv_in, nb_node);
+  else if (G) es = launch_tile_f32<DIM, D, MODEL, false, true, false>(c, mp, J, dens, g, bv_in, nb_node);
+  else es = launch_tile_f32<DIM, D, MODEL, false, false, true>(c, mp, J, dens, g, bv_in, nb_node);
   prof_end(c, kStageElem);
   if (es) return es;
   c->launches++;
   if (G && c->n_shared > 0) {
     prof_begin(c, kStageGather);
-    const double* b = c->f_host.empty() ? nullptr : c->b;
     k_tile_shared<D, PartF32><<<grid_for(c->n_shared * D, kMaxElemBlocks), kThreads, 0, c->stream>>>(
         c->n_shared, c->tile_snode, c->tile_sbeg, c->tile_spart, reinterpret_cast<const float*>(c->tile_part), b,
         c->dir, io_perm(c), g);

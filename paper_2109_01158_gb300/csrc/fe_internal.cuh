@@ -43,10 +43,10 @@ inline int grid_for(int64_t n, int max_blocks) {
 // Element tiles of the fused element + patch kernels (fe_tiles.cu): a tile is a contiguous
 // range of at most kTileElems device-order elements together with the nodes they touch (at
 // most tile_max_nodes(dim)); the fused kernels run blocks of kTileThreads threads.
-constexpr int kTileElems = 384;      // 64 hexahedra of six tetrahedra: one octree cell
-constexpr int kTileThreads = kTileElems + 32;   // one compute thread per element + a producer warp
-constexpr int kTileBlocksPerSM = 2;  // resident blocks per SM: one computes while the other gathers
-constexpr int tile_max_nodes(int dim) { return dim == 3 ? 160 : 256; }
+constexpr int kTileElems = 768;      // 128 hexahedra of six tetrahedra: one octree cell
+constexpr int kTileNodeWarps = 3;    // warps that gather nodal values and sum patches
+constexpr int kTileThreads = kTileElems + 32 * kTileNodeWarps + 32;   // + one producer warp
+constexpr int tile_max_nodes(int dim) { return dim == 3 ? 256 : 512; }
 // Tiles start on multiples of kTileAlign elements, and the element arrays the tile kernels
 // stage (dphi32, vol32, ...) use the padded stride padded_ne(ne): every staged range then
 // starts 16-byte aligned.
@@ -117,7 +117,7 @@ struct fe_ctx {
   double* u = nullptr;         // nn*padded_d(d): displacement (Neo-Hookean) or v
   double* w_hvp = nullptr;     // nn*padded_d(d): direction of a Hessian-vector product
   double* r = nullptr;         // ne*(dim+1)*d slot-ordered local forces (x2 for FD)
-  float2* u_df = nullptr;      // nn*padded_d(d) double-float displacement (FE_DF64)
+  float2* u_df = nullptr;      // nn*padded_d(d) displacement as float pairs (FE_DF64, FE_F32_COMP)
   float2* r_df = nullptr;      // ne*(dim+1)*d double-float local forces
   double* partials = nullptr;  // element partials [kMaxElemBlocks] then node partials
   unsigned* counter = nullptr; // last-block ticket
@@ -158,7 +158,8 @@ struct fe_ctx {
   int32_t* tile_sbeg = nullptr;   // n_shared + 1
   int32_t* tile_spart = nullptr;  // n_tpart: partial slots of each shared node, in tile order
   float2* tile_part = nullptr;    // n_tpart * d: partial patch sums of the shared nodes
-  double* tile_epart = nullptr;   // 2 * n_tiles: per-tile sums of |T| W and of b.v
+  double* tile_epart = nullptr;   // 2 * n_tiles: per-tile sums of |T| W (and of b.v)
+  double* tile_bvp = nullptr;     // ceil(nn / kThreads): block partials of b.v of the node prep
 
   // SM clocks a bulk-copy kernel waits for its first copy before it gives up and reports
   // FE_ETIMEOUT (fe_set_wait_limit); the drain after giving up always waits the full default

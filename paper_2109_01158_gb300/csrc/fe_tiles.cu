@@ -38,6 +38,7 @@ void free_tiles(fe_ctx* c) {
   dev_free(c, &c->tile_spart, (size_t)c->n_tpart);
   dev_free(c, &c->tile_part, (size_t)c->n_tpart * (c->d > 0 ? c->d : 1));
   dev_free(c, &c->tile_epart, 2 * (size_t)c->n_tiles);
+  dev_free(c, &c->tile_bvp, (size_t)(c->nn + kThreads - 1) / kThreads);
   c->n_tiles = c->n_tnodes = c->n_shared = c->n_tpart = 0;
 }
 
@@ -168,7 +169,8 @@ fe_status build_tiles(fe_ctx* c) {
       (st = dev_alloc(c, &c->tile_snode, (size_t)nshared)) || (st = dev_alloc(c, &c->tile_sbeg, (size_t)nshared + 1)) ||
       (st = dev_alloc(c, &c->tile_spart, (size_t)npart)) ||
       (st = dev_alloc(c, &c->tile_part, (size_t)npart * (c->d > 0 ? c->d : 1))) ||
-      (st = dev_alloc(c, &c->tile_epart, 2 * (size_t)ntiles))) {
+      (st = dev_alloc(c, &c->tile_epart, 2 * (size_t)ntiles)) ||
+      (st = dev_alloc(c, &c->tile_bvp, (size_t)(nn + kThreads - 1) / kThreads))) {
     c->n_tiles = ntiles;
     c->n_tnodes = ntn;
     c->n_shared = nshared;

@@ -3,14 +3,13 @@
 // asynchronous copies that fill it, the per-tile energy partials and their final sum, and the
 // kernel that completes the gradient of the shared nodes.
 //
-// The fused kernels run kTileBlocksPerSM persistent blocks per SM (while one block sums
-// patches or converts nodal values with a few warps, the other's warps compute elements);
-// block b takes the tiles b, b + G, b + 2G, ... (G blocks).  While it computes tile t it already has in flight:
-//   - bulk asynchronous copies (TMA) of the element arrays and node records of the tile after
-//     next (two element stages, three record buffers: the current tile's records are still
-//     read while those of the next two tiles arrive), and
-//   - per-thread asynchronous copies of the nodal values (v, X, b) of the next tile,
-// so that its arithmetic overlaps the HBM traffic of the following tiles.
+// The fused kernels run one persistent block per SM; block b takes the tiles b, b + G,
+// b + 2G, ... (G blocks).  Its warps are specialised: element warps (one thread per element of
+// a tile), node warps (the nodal values of the next tile, then the patch sums of the current
+// one) and a producer warp (bulk asynchronous copies (TMA) of the element arrays and node
+// records of the following tiles, and the tiles' energy partials).  They hand buffers to each
+// other through full/empty mbarriers, so the element arithmetic of one tile overlaps the patch
+// sums of the previous one and the HBM traffic of the next ones.
 #pragma once
 
 #include "async_copy.cuh"
@@ -30,15 +29,15 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu)), (int)(u << 29));
 }
 
-// Shared-memory layout of the pipeline of one block.
-//   E[2]  element stages: DIM*DIM shape-gradient arrays and the volume (EB bytes per element
-//         each), then the local ids / local slots (16 bytes per element); tiles start on
-//         multiples of kTileAlign elements and the arrays use the padded stride, so every
-//         copied range starts 16-byte aligned;
-//   V     nodal values of the next tile as copied from global memory: per node D values of v,
-//         D of X and D of b (doubles);
-//   U     per-node records of the current tile (NU bytes each), built from V;
-//   Rs    the local forces of the current tile, RB bytes per slot.
+// Shared-memory layout of the pipeline of one block (buffers of consecutive tiles alternate):
+//   E[2]   element stages: DIM*DIM shape-gradient arrays and the volume (EB bytes per element
+//          each), then the local ids / local slots (16 bytes per element); tiles start on
+//          multiples of kTileAlign elements and the arrays use the padded stride, so every
+//          copied range starts 16-byte aligned;
+//   R[3]   node records (int4 per tile node);
+//   U[2]   the tile's nodal values, NU bytes per node;
+//   Rs[2]  the tile's local forces, RB bytes per slot;
+//   Ew[2]  the tile's element energies |T| W (float per element).
 template <int DIM, int D, int EB, int NU, int RB>
 struct TilePipe {
   static constexpr int kNodes = tile_max_nodes(DIM);
@@ -48,13 +47,19 @@ struct TilePipe {
   static_assert(kTileElems % kTileAlign == 0, "tiles hold whole groups of kTileAlign elements");
   static constexpr int kElemOff = kArrays * kArrayBytes;          // uint4 per element
   static constexpr int kEBytes = kElemOff + kTileElems * 16;
-  static constexpr int kVPerNode = 3 * D;                         // doubles
+  static constexpr int kRBytes = kNodes * 16;
+  static constexpr int kUBytes = (kNodes * NU + 15) / 16 * 16;
+  static constexpr int kRsBytes = (kSlots * RB + 15) / 16 * 16;
+  static constexpr int kEwBytes = kTileElems * 4;
   static constexpr int kE = 0;
-  static constexpr int kV = kE + 2 * kEBytes;
-  static constexpr int kU = kV + kNodes * kVPerNode * 8;
-  static constexpr int kRs = kU + kNodes * NU;
-  static constexpr int kBytes = kRs + kSlots * RB;
-  static_assert(kEBytes % 16 == 0 && kU % 16 == 0 && kRs % 16 == 0, "alignment");
+  static constexpr int kR = kE + 2 * kEBytes;
+  static constexpr int kU = kR + 3 * kRBytes;
+  static constexpr int kRs = kU + 2 * kUBytes;
+  static constexpr int kEw = kRs + 2 * kRsBytes;
+  static constexpr int kBytes = kEw + 2 * kEwBytes;
+  static_assert(kEBytes % 16 == 0 && kRBytes % 16 == 0, "alignment");
+  static_assert(kTileElems % 128 == 0, "the energy sum reads the tile in rows of 128");
+  static_assert(2 * kRsBytes >= 2 * kTileThreads * 8, "the final reduction reuses Rs");
 };
 
 // The tile structure and element arrays of one precision (structure of arrays, stride ne).
@@ -96,56 +101,38 @@ __device__ __forceinline__ void pipe_issue_recs(int4* rb, const TileArgs& A, int
   if (nt > 0) bulk_g2s(rb, A.node + k0, (uint32_t)nt * 16u, bar);
 }
 
-// Per-thread asynchronous copies of the nodal values of a tile's nodes into V, spread over
-// the first `nthreads` threads as (node, component) items: for node k and component j,
-// V[k][j] = v_j (at the node's caller or device index), V[k][D + j] = X_j (Neo-Hookean
-// deformation input) and V[k][2D + j] = b_j (when a load is given and the tile owns the
-// node's b_i v_i).
-template <int DIM, int D, int MODEL>
-__device__ __forceinline__ void pipe_gather_nodes(double* V, const int4* rec, int nt, const double* v,
-                                                  const double* X, const double* b, bool caller_order, bool disp,
-                                                  int nthreads) {
-  for (int w = threadIdx.x; w < nt * D; w += nthreads) {
-    const int k = w / D, j = w - k * D;
-    const int4 r = rec[k];
-    double* o = V + k * 3 * D + j;
-    cp_async8(o, v + (int64_t)(caller_order ? r.y : r.x) * D + j);
-    if (MODEL == FE_NEOHOOKE && !disp) cp_async8(o + D, X + (int64_t)r.x * DIM + j);
-    if (b && (r.w & 1)) cp_async8(o + 2 * D, b + (int64_t)r.x * D + j);
-  }
-  cp_async_commit();
-}
-
 __device__ __forceinline__ double pipe_warp_sum(double x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
   return x;
 }
 
-// One warp: the sum of the n floats x[0..n) as a float pair (TwoSum per addition: the pair
-// holds the exact sum to within a few units of 2^-48 of the terms' magnitudes), converted to
-// FP64 and added over the lanes in a fixed order; valid in lane 0.  An infinite term makes the
-// sum +Inf (TwoSum on Inf would give NaN).
+// One warp: the sum of the n floats x[0..n) (n a multiple of 128) in a fixed order: per lane
+// four interleaved float-pair accumulators (TwoSum per addition: each pair holds its exact sum
+// to within a few units of 2^-48 of the terms' magnitudes), combined and converted to FP64,
+// then added over the lanes; valid in lane 0.  An infinite term makes the sum +Inf (TwoSum on
+// Inf would give NaN).
 __device__ __forceinline__ double pipe_warp_sum_floats(const float* x, int n) {
   const int lane = threadIdx.x & 31;
-  df s = {0.f, 0.f};
+  df s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   bool inf = false;
-  for (int k = lane; k < n; k += 32) {
-    const float y = x[k];
-    if (isinf(y)) {
-      inf = true;
-    } else {
-      const df t = two_sum(s.hi, y);
-      s = fast_two_sum(t.hi, __fadd_rn(t.lo, s.lo));
+  for (int k = lane; k < n; k += 128) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float y = x[k + 32 * a];
+      inf |= isinf(y);
+      const df t = two_sum(s[a].hi, isinf(y) ? 0.f : y);
+      s[a] = fast_two_sum(t.hi, __fadd_rn(t.lo, s[a].lo));
     }
   }
-  double d = f2d_bits(s.hi) + f2d_bits(s.lo);
+  double d = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) d += f2d_bits(s[a].hi) + f2d_bits(s[a].lo);
   d = pipe_warp_sum(d);
   inf = __any_sync(0xffffffffu, inf);
   return inf ? CUDART_INF : d;
 }
 
-// One warp: the sums of red[0][0..n) and red[1][0..n) in a fixed order (valid in lane 0).
 __device__ __forceinline__ void pipe_warp_pair_sum(const double* r0, const double* r1, int n, double* s0,
                                                    double* s1) {
   const int lane = threadIdx.x & 31;
@@ -158,12 +145,12 @@ __device__ __forceinline__ void pipe_warp_pair_sum(const double* r0, const doubl
   *s1 = pipe_warp_sum(b);
 }
 
-// After every block has written its tiles' partials epart[t] (sum |T| W) and epart[ntiles + t]
-// (b.v) and fenced them: the block that arrives last adds them over the tiles in a fixed order
-// and writes J = sum |T| W - (b.v + shift) (shift = b.X when the caller passes displacements).
-// `red` holds 2 * blockDim.x doubles of shared memory.
-__device__ __forceinline__ void pipe_finish_energy(const double* epart, int64_t ntiles, double shift,
-                                                   unsigned* counter, double* J, double* red) {
+// After every block has written its tiles' partials epart[t] (sum |T| W) and fenced them: the
+// block that arrives last adds them over the tiles in a fixed order, and the node-side b.v
+// partials bvp[0 .. nbv) likewise, and writes J = sum |T| W - (b.v + shift) (shift = b.X
+// when the caller passes displacements).  `red` holds 2 * blockDim.x doubles.
+__device__ __forceinline__ void pipe_finish_energy(const double* epart, int64_t ntiles, const double* bvp, int nbv,
+                                                   double shift, unsigned* counter, double* J, double* red) {
   __shared__ bool am_last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -174,10 +161,9 @@ __device__ __forceinline__ void pipe_finish_energy(const double* epart, int64_t 
   if (!am_last) return;
   __threadfence();
   double s = 0.0, b = 0.0;
-  for (int64_t k = threadIdx.x; k < ntiles; k += blockDim.x) {
-    s += __ldcg(epart + k);
-    b += __ldcg(epart + ntiles + k);
-  }
+  for (int64_t k = threadIdx.x; k < ntiles; k += blockDim.x) s += __ldcg(epart + k);
+  if (bvp)
+    for (int k = threadIdx.x; k < nbv; k += blockDim.x) b += __ldcg(bvp + k);
   red[threadIdx.x] = s;
   red[blockDim.x + threadIdx.x] = b;
   __syncthreads();
