@@ -52,6 +52,14 @@ F64_FLOPS_PER_TET = 250.0
 F64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+# What one step runs in each precision (for the variants' records).
+VARIANT_KERNELS = {
+    "f64": "k_node_prep + k_elem_f64 (local forces to HBM) + k_gather_bulk (patch sums)",
+    "df64": "k_node_prep_df + k_elem_df (local forces to HBM) + k_gather_bulk (patch sums)",
+    "f32": "k_pairs32 (node pairs) + k_tile_f32 (elements and patch sums in shared memory, one persistent "
+           "warp-specialised block per SM) + k_tile_shared (nodes on tile boundaries)",
+}
+
 # DRAM traffic of the element kernels per launch, from an ncu capture (profiles/): valid only
 # while the kernel's sources hash to the value recorded with the capture.
 ORDER_NAMES = {0: "as generated", 1: "Morton", 2: "reverse Cuthill-McKee"}
@@ -218,6 +226,65 @@ def time_oracle(ws, reps):
         om.gradient_exact(ws.v)
         ts.append(time.perf_counter() - t0)
     return ts
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_range_worker(task):
+    """One process of the all-cores timing: the oracle's energy + exact gradient over elements
+    [lo, hi) of the workload (its own single-threaded C code), started together with the other
+    processes at a barrier; returns (start, end) wall-clock times of its `reps` evaluations."""
+    name, lo, hi, reps, start_barrier = task
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import oracle
+    from paper_2109_01158_gb300 import meshgen as mg
+    w = mg.config_workload(name)
+    ws = mg.Workload(w.name + f"_{lo}_{hi}", w.dim, w.d, w.coords, np.ascontiguousarray(w.elems[lo:hi]),
+                     w.dirichlet, w.model, p=w.p, C1=w.C1, D1=w.D1, f=w.f, v=w.v, eps=w.eps)
+    om = oracle.OracleMesh(ws)
+    om.energy(ws.v)                       # page in the working set once
+    start_barrier.wait()
+    t0 = time.time()
+    for _ in range(reps):
+        om.energy(ws.v)
+        om.gradient_exact(ws.v)
+    return t0, time.time()
+
+
+def time_oracle_all_cores(name, ne, reps=2, procs=None):
+    """The oracle on every host core: the mesh's elements split into one contiguous range per
+    process (spawned, one thread each), all started at once; whole-job elements/s over the
+    wall time from the first start to the last end."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        bar = mgr.Barrier(procs)
+        cuts = [ne * k // procs for k in range(procs + 1)]
+        tasks = [(name, cuts[k], cuts[k + 1], reps, bar) for k in range(procs)]
+        with ctx.Pool(procs) as pool:
+            res = pool.map(_oracle_range_worker, tasks)
+    wall = max(t1 for _, t1 in res) - min(t0 for t0, _ in res)
+    return ne * reps / wall / 1e9, procs, wall
 
 
 def run_reference(args, rank, world):
@@ -408,9 +475,14 @@ def run_ours(args, rank, world, local):
         oms, _, oprof = timed(nst, profile=True)
         o_elem = oprof["element"][0] / max(oprof["element"][1], 1)
         ob, on = ELEM_BYTES[(w.dim, other)]
+        o_step_bytes = w.ne * (ob + xe) + w.nn * (on + xn)
         variants[other] = {"value": w.ne * nst / (oms / 1e3) / 1e9, "unit": "Gelem/s",
                            "ms_per_step": oms / nst, "element_kernel_ms": o_elem,
-                           "element_hbm_frac": (w.ne * ob + w.nn * on) / (o_elem / 1e3) / 1e9 / hbm_peak}
+                           "element_hbm_frac": (w.ne * ob + w.nn * on) / (o_elem / 1e3) / 1e9 / hbm_peak,
+                           "step_algorithmic_bytes": o_step_bytes,
+                           "step_hbm_frac": o_step_bytes / (oms / nst / 1e3) / 1e9 / hbm_peak,
+                           "stages_ms": {k: t / n for k, (t, n) in oprof.items() if n},
+                           "kernels": VARIANT_KERNELS.get(other, "")}
     gm.set_precision(code[prec])
 
     # Hessian-vector products (FP64) on the same mesh and state, for context
@@ -495,8 +567,9 @@ def run_ours(args, rank, world, local):
     }
     if rank == 0 and not args.no_serve:
         line["serving"] = run_serving(args, local)
-    if rank == 0 and args.minimize:
-        line["minimize"] = run_minimize(args, local)
+    if rank == 0 and world == 1 and not args.no_minimize:
+        # the bounded set by default (about 30 s); the paper's minimisation benchmarks with --minimize
+        line["minimize"] = run_minimize(args, local, full=args.minimize)
     if rank == 0 and args.paper_tables:
         line["paper_tables"] = run_paper_tables(args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -506,7 +579,19 @@ def run_ours(args, rank, world, local):
         line["cpu_baseline"] = {
             "value": ws.ne / best / 1e9, "unit": "Gelem/s", "cores": 1, "kind": "oracle",
             "sample": (f"first {ws.ne} of {w.ne} elements (whole element layers), energy + exact "
-                       f"gradient, best of 2, single thread")}
+                       f"gradient, best of 2, single thread"),
+            "cpu_model": cpu_model()}
+        try:
+            allv, procs, wall = time_oracle_all_cores(args.workload, w.ne, reps=2)
+            line["cpu_baseline"]["all_cores"] = {
+                "value": allv, "unit": "Gelem/s", "cores": procs, "kind": "oracle",
+                "sample": (f"all {w.ne} elements, split into {procs} contiguous element ranges, one "
+                           f"spawned process per core running the oracle's single-threaded C code; "
+                           f"energy + exact gradient twice each, {wall:.2f} s wall from the first start to "
+                           f"the last end"),
+                "cpu_model": line["cpu_baseline"]["cpu_model"]}
+        except Exception as exc:   # a host without spawn support or memory for every process
+            line["cpu_baseline"]["all_cores"] = {"unavailable": f"{type(exc).__name__}: {exc}"}
     gm.close()
     return line if rank == 0 else None
 
@@ -590,7 +675,29 @@ def run_paper_tables(args, device):
             "paper": "MATLAB R2021a on an M1 MacBook Air (Sec. 7.3); other hardware, context only"}
 
 
-def run_minimize(args, device):
+def served_minimisations(device):
+    """Whole minimisations served by continuous batching: 16 gravity-cube requests
+    (12^3..24^3 x 6, loads 1 + k/16), Poisson arrivals at 40/s; batched rounds vs one request at
+    a time, and whether every result is bitwise the same in both."""
+    import torch
+    from paper_2109_01158_gb300 import serve
+    msrv = serve.MinimizeServer(device)
+    served = {}
+    for mode in ("serial", "batched"):
+        reqs = serve.make_minimize_requests(16, rate=40.0, device=device)
+        served[mode] = (msrv.run(reqs, mode), reqs)
+    msrv.close()
+    same = all(a.result.J == b.result.J and torch.equal(a.result.v, b.result.v)
+               for a, b in zip(served["batched"][1], served["serial"][1]))
+    return {
+        "workload": "16 L-BFGS requests, 3D Neo-Hookean gravity cubes 12^3..24^3 x 6, Poisson arrivals 40/s, "
+                    "||g||_inf <= 1e-6 ||g0||_inf, double-float kernels",
+        "batched": served["batched"][0].as_dict(), "serial": served["serial"][0].as_dict(),
+        "results_identical_alone_and_in_the_mix": same,
+        "converged": all(r.result.converged for r in served["batched"][1])}
+
+
+def run_minimize(args, device, full=True):
     """End-to-end minimisation: 3D Neo-Hookean 64^3 x 6 tetrahedra (1,572,864), face x = 0
     clamped, gravity f = (0, 0, -1e-2), E = 1e4, nu = 0.3, from v = X; L-BFGS (m = 10) on the
     displacement u = v - X (FE_INPUT_DISPLACEMENT) until
@@ -621,11 +728,11 @@ def run_minimize(args, device):
            "runs": {}}
     # L-BFGS pairs and directions in the library's kernels (fe_lbfgs); one run with the same
     # recursion in torch vector operations for comparison
-    for name, prec, grad, devmem in (("df64_exact", fem.FE_DF64, "exact", True),
-                                     ("f64_exact", fem.FE_F64, "exact", True),
-                                     ("f64_exact_torch_memory", fem.FE_F64, "exact", False),
-                                     ("f32_exact", fem.FE_F32_COMP, "exact", True),
-                                     ("f64_fd", fem.FE_F64, "fd", True)):
+    runs = [("df64_exact", fem.FE_DF64, "exact", True), ("f64_exact", fem.FE_F64, "exact", True)]
+    if full:
+        runs += [("f64_exact_torch_memory", fem.FE_F64, "exact", False), ("f32_exact", fem.FE_F32_COMP, "exact", True),
+                 ("f64_fd", fem.FE_F64, "fd", True)]
+    for name, prec, grad, devmem in runs:
         gm.set_precision(prec)
         r = lbfgs(mesh_evaluator(gm, grad, eps=1e-6), v0, gtol=1e-6, relative=True, max_iter=args.minimize_iters,
                   device_memory=devmem)
@@ -648,9 +755,18 @@ def run_minimize(args, device):
     for m in meshes:
         m.set_input(fem.FE_INPUT_DISPLACEMENT)
     batch = fem.Batch(device)
+    t_lock = time.perf_counter()
     rs = lbfgs_batched(batch_evaluator(batch, meshes, device),
                        [torch.zeros(wk.ndof, dtype=torch.float64, device=dev) for wk in ws],
                        gtol=1e-6, relative=True, max_iter=args.minimize_iters, device_memory=True)
+    t_lock = time.perf_counter() - t_lock
+    out["lockstep_8_instances"] = {
+        "workload": f"8 x neohooke3d_{nl}^3x6 gravity, loads 1 + k/8, double-float kernels, one batched launch "
+                    f"per line-search round",
+        "iters": [r.iters for r in rs], "converged": all(r.converged for r in rs), "seconds": t_lock}
+    if not full:
+        out["served_minimisations"] = served_minimisations(device)
+        return out
     # Benchmark 4: the torsion continuation (24 minimisations) on the level-3 bar, FP64
     # kernels with trust-region Newton-CG, against the minimal energies the paper prints
     paper3 = {3: 1.4631, 6: 5.8533, 9: 13.1735, 12: 23.4286, 15: 36.6236, 18: 52.7641, 21: 71.7883, 24: 93.7238}
@@ -695,26 +811,7 @@ def run_minimize(args, device):
                    "converged": all(x.converged for x in rn), "seconds_level8": rn[-1].seconds,
                    "seconds_total": t_nest},
         "paper": "617.92 s, 22 trust-region iterations (exact gradient; MATLAB on an M1)"}
-    # whole minimisations served by continuous batching: 16 gravity-cube requests (12^3..24^3 x 6,
-    # loads 1 + k/16), Poisson arrivals at 40/s; batched rounds vs one request at a time
-    from paper_2109_01158_gb300 import serve
-    msrv = serve.MinimizeServer(device)
-    served = {}
-    for mode in ("serial", "batched"):
-        reqs = serve.make_minimize_requests(16, rate=40.0, device=device)
-        served[mode] = (msrv.run(reqs, mode), reqs)
-    msrv.close()
-    same = all(a.result.J == b.result.J and torch.equal(a.result.v, b.result.v)
-               for a, b in zip(served["batched"][1], served["serial"][1]))
-    out["served_minimisations"] = {
-        "workload": "16 L-BFGS requests, 3D Neo-Hookean gravity cubes 12^3..24^3 x 6, Poisson arrivals 40/s, "
-                    "||g||_inf <= 1e-6 ||g0||_inf, double-float kernels",
-        "batched": served["batched"][0].as_dict(), "serial": served["serial"][0].as_dict(),
-        "results_identical_alone_and_in_the_mix": same,
-        "converged": all(r.result.converged for r in served["batched"][1])}
-    out[f"lockstep_8x{nl}^3x6"] = {"seconds": max(r.seconds for r in rs), "iters": [r.iters for r in rs],
-                                   "evals": [r.evals for r in rs],
-                                   "converged": all(r.converged for r in rs), "J": [r.J for r in rs]}
+    out["served_minimisations"] = served_minimisations(device)
     return out
 
 
@@ -737,7 +834,10 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-budget-gb", type=int, default=8)
-    ap.add_argument("--minimize", action="store_true", help="also run the L-BFGS minimisation (64^3 x 6)")
+    ap.add_argument("--minimize", action="store_true",
+                    help="the full minimisation set: also the FP32, torch-memory and central-difference L-BFGS "
+                         "runs and the paper's Benchmarks 4 and 6")
+    ap.add_argument("--no-minimize", action="store_true", help="skip the minimisations")
     ap.add_argument("--paper-tables", action="store_true",
                     help="also time the energy and both gradients on the twisted bar, levels 1-5 (Tables 2 and 3)")
     ap.add_argument("--minimize-n", type=int, default=64)
