@@ -337,19 +337,29 @@ fe_status fe_profile_read(fe_ctx* ctx, double* ms_host, int64_t* launches_host, 
 /* ---- Batched evaluation over many resident meshes (serving) -------------------------
  * Not in the paper: evaluates J and the exact gradient (same definitions as
  * fe_energy_gradient, double-float arithmetic as FE_DF64) for many independent requests,
- * each on its own precomputed mesh, in three kernel launches whatever their number.  Every
- * request's partial sums are reduced in an order fixed by its own mesh, so its J and g are
- * bitwise the same alone and in any mix of requests (they can differ in the last bits from
- * fe_energy_gradient, whose reduction tree is shaped by the grid). */
+ * each on its own precomputed mesh, in ONE persistent kernel launch whatever their number
+ * (plus one host-to-device copy of the requests' descriptors).  The launch walks a work
+ * list of 256-node and 256-element tiles of all requests in the order given; a tile that
+ * needs the results of others of its request waits for them (bounded: see
+ * fe_batch_set_wait_limit).  Every request's partial sums are reduced in an order fixed by
+ * its own mesh, so its J and g are bitwise the same alone and in any mix of requests (they
+ * can differ in the last bits from fe_energy_gradient, whose reduction tree is shaped by
+ * the grid). */
 typedef struct fe_batch fe_batch;
 
 typedef struct {
     const fe_ctx* mesh; /* precomputed with FE_DF64 and given a model; only read              */
-    const double* v;    /* device, n_nodes*d doubles (caller's dof order)                       */
-    double* J;          /* device, one double                                                   */
-    double* g;          /* device, n_nodes*d doubles                                             */
+    const double* v;    /* n_nodes*d doubles (caller's dof order): device memory, or          */
+                        /* page-locked host memory that the kernel reads directly             */
+    double* J;          /* one double: device or page-locked host memory                      */
+    double* g;          /* n_nodes*d doubles: device or page-locked host memory (written      */
+                        /* directly by the kernel)                                            */
     void* work;         /* device scratch of fe_batch_work_bytes(mesh) bytes, 256-byte aligned;  */
                         /* owned by the caller, one per request in flight                       */
+    int* done;          /* NULL, or an int (device or page-locked host memory) that the        */
+                        /* kernel sets, once this request's J and g are written and visible to */
+                        /* the host, to 1 (or 3 if one of its waits gave up: results invalid); */
+                        /* the caller zeroes it before the call                                 */
 } fe_batch_item;
 
 /* Bytes of device scratch one request on `mesh` needs. */
@@ -357,35 +367,46 @@ fe_status fe_batch_work_bytes(const fe_ctx* mesh, size_t* bytes);
 /* Create a batch executor on `device` enqueuing on `cuda_stream`. */
 fe_status fe_batch_create(fe_batch** out, int device, void* cuda_stream);
 fe_status fe_batch_destroy(fe_batch* b);
+/* SM clocks a tile waits for the tiles it depends on before it gives up (then the request's
+ * results are invalid and fe_batch_sync_status returns FE_ETIMEOUT); 0 restores the default
+ * 2e9; negative is FE_EINVAL.  The waits end by construction (a tile only waits for tiles
+ * handed out before it, to running blocks); the limit guards against a fault elsewhere. */
+fe_status fe_batch_set_wait_limit(fe_batch* b, int64_t cycles);
 /* Enqueue one evaluation of every item (asynchronous; the host descriptors are copied before
  * the call returns).  Items of one call must use distinct `work` buffers.  Neo-Hookean items
  * with some det F <= 0 get J = +Inf and fe_batch_sync_status returns FE_EDOMAIN. */
 fe_status fe_batch_energy_gradient(fe_batch* b, const fe_batch_item* items, int n_items);
-/* Synchronise the batch stream; FE_EDOMAIN if an item had det F <= 0 since the last call. */
+/* Synchronise the batch stream; FE_ETIMEOUT if a wait gave up, else FE_EDOMAIN if an item had
+ * det F <= 0, since the last call. */
 fe_status fe_batch_sync_status(fe_batch* b);
+/* Kernel launches enqueued so far (one per non-empty fe_batch_energy_gradient call). */
 fe_status fe_batch_launch_count(const fe_batch* b, int64_t* count);
 
 /* ---- Continuous-batching server over resident meshes -------------------------------
- * Not in the paper: a native request loop around the batched kernels.  Callers submit
- * energy + gradient requests (host vectors in, host results out); a worker thread admits
- * the requests that have arrived, in FIFO order, while their device bytes fit in the HBM
- * budget (a ring arena allocated at creation), stages their vectors through pinned memory
- * (one host-to-device copy per batch), launches the three batch kernels on the server's own
- * stream, and copies the results back (one device-to-host copy per batch).  Batch k + 1 is
- * prepared and enqueued while batch k runs; a completion thread copies the results into the
- * callers' buffers in launch order, stamps the completion time and frees the arena.  With
- * max_batch = 1 it serves one request at a time with the same kernels.  Results are bitwise
- * those of fe_batch_energy_gradient on the same request (alone or in any mix).
- * Page-locked caller buffers (cudaMallocHost, cudaHostRegister) are copied to and from by
- * DMA directly; pageable ones go through the server's pinned staging (one extra host copy).
- * Times are seconds on a steady clock since fe_server_create. */
+ * Not in the paper: a native request loop around the persistent batched kernel.  Callers
+ * submit energy + gradient requests (host vectors in, host results out); a worker thread
+ * admits the requests that have arrived, in FIFO order, while their device scratch fits in
+ * the HBM budget (a ring arena allocated at creation), orders the batch smallest mesh first
+ * and enqueues it as one persistent launch on the server's own stream.  The kernel reads the
+ * vectors and writes the gradients directly in page-locked host memory -- the caller's
+ * buffers when they are page-locked (cudaMallocHost, cudaHostAlloc, cudaHostRegister),
+ * otherwise the server's pinned staging (one extra host copy each way) -- and raises a
+ * completion flag per request.  Batch k + 1 is prepared and enqueued while batch k runs; a
+ * completion thread polls the flags and completes each request as soon as its own flag is
+ * up (stamping its completion time), frees a batch's arena region once all its requests
+ * are complete.  With max_batch > 1 the (up to three) batches in flight run on streams of
+ * their own, so a batch starts on the SMs its predecessor frees during its last tiles; with
+ * max_batch = 1 it serves one request at a time, in order on one stream, with the same
+ * kernel.
+ * Results are bitwise those of fe_batch_energy_gradient on the same request (alone or in
+ * any mix).  Times are seconds on a steady clock since fe_server_create. */
 typedef struct fe_server fe_server;
 
-/* hbm_budget: bytes of device memory for the in-flight requests (vectors + scratch);
+/* hbm_budget: bytes of device memory for the scratch of the in-flight requests;
  * max_batch >= 1: most requests per batch.  Creates its own non-blocking stream on `device`
  * and allocates everything it serves with up front: the arena, and per batch slot pinned
- * staging of min(max(hbm_budget/16, 1 MB), 256 MB) bytes for each direction (a batch is also
- * bounded by it; a single larger request grows it). */
+ * staging of min(max(hbm_budget/16, 1 MB), 256 MB) bytes for each direction (pageable
+ * vectors also bound a batch by it; a single larger request grows it). */
 fe_status fe_server_create(fe_server** out, int device, size_t hbm_budget, int max_batch);
 /* Serve every submitted request, then stop the threads and free everything. */
 fe_status fe_server_destroy(fe_server* s);
@@ -394,12 +415,13 @@ fe_status fe_server_destroy(fe_server* s);
  * it unchanged until then).  J_host (one double) and g_host (n_nodes*d doubles) receive the
  * results at completion.  t_arrival: when the request arrives (server clock; < 0 = now);
  * arrivals must be submitted in non-decreasing order.  *ticket identifies it.  FE_EINVAL if
- * its device bytes exceed the whole budget. */
+ * its device scratch exceeds the whole budget. */
 fe_status fe_server_submit(fe_server* s, const fe_ctx* mesh, const double* v_host, double* J_host,
                            double* g_host, double t_arrival, int64_t* ticket);
-/* Block until request `ticket` completed; returns its status (FE_OK, or FE_EDOMAIN when some
- * det F <= 0 and J = +Inf) and its arrival, start (batch enqueued) and completion times (any
- * pointer may be NULL).  Each ticket can be waited for once. */
+/* Block until request `ticket` completed; returns its status (FE_OK; FE_EDOMAIN when some
+ * det F <= 0 and J = +Inf; FE_ETIMEOUT or FE_ECUDA when the device failed it) and its
+ * arrival, start (batch enqueued) and completion times (any pointer may be NULL).  Each
+ * ticket can be waited for once. */
 fe_status fe_server_wait(fe_server* s, int64_t ticket, double* t_arrival, double* t_start, double* t_done);
 /* Seconds since fe_server_create on the server clock. */
 fe_status fe_server_now(const fe_server* s, double* t);

@@ -13,18 +13,28 @@ __device__ __forceinline__ df ld_df(const float2* __restrict__ p, int64_t i) {
   return {a.x, a.y};
 }
 
+// Loads of data that other blocks of the same launch write (the persistent batched kernel):
+// through L2 only (ld.global.cg), never the read-only path, which is not kept coherent with
+// writes made during the launch.
+template <bool COH, class T>
+__device__ __forceinline__ T ld_ro(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+
 // Node record of the double-float displacement: D pairs, padded to 4 pairs in 3D.
-template <int D>
+template <int D, bool COH = false>
 __device__ __forceinline__ void load_u_df(const float2* __restrict__ u, int32_t n, df* out) {
   if (D == 1) {
-    out[0] = ld_df(u, n);
+    const float2 a = ld_ro<COH>(u + n);
+    out[0] = {a.x, a.y};
   } else if (D == 2) {
-    const float4 a = __ldg(reinterpret_cast<const float4*>(u) + n);
+    const float4 a = ld_ro<COH>(reinterpret_cast<const float4*>(u) + n);
     out[0] = {a.x, a.y};
     out[1] = {a.z, a.w};
   } else {
     const float4* p = reinterpret_cast<const float4*>(u) + 2 * (int64_t)n;
-    const float4 a = __ldg(p), b = __ldg(p + 1);
+    const float4 a = ld_ro<COH>(p), b = ld_ro<COH>(p + 1);
     out[0] = {a.x, a.y};
     out[1] = {a.z, a.w};
     out[2] = {b.x, b.y};
@@ -112,8 +122,9 @@ static __device__ __noinline__ MatDF<DIM> nh_stress_small_df(MatDF<DIM> H, MatDF
 // One element: gathers the nodal values, forms H = grad u (eq. Dv) and returns W(F) when
 // WANT_W (eq. neoHook or eq. pLaplacian); when GRAD, also writes the local forces
 // r_{T,l} = |T| dW/dF grad(phi_l) (Sec. 6.2) to the CSR slots.  vT receives |T|; `bad` is set
-// when det F <= 0.  Arrays are the structure-of-arrays of fe_ctx with stride ne.
-template <int DIM, int D, int MODEL, bool WANT_W, bool GRAD>
+// when det F <= 0.  Arrays are the structure-of-arrays of fe_ctx with stride ne.  COH: the
+// nodal values u were written earlier in the same launch (coherent loads).
+template <int DIM, int D, int MODEL, bool WANT_W, bool GRAD, bool COH = false>
 __device__ __forceinline__ df elem_df_one(int64_t e, int64_t ne, const int32_t* __restrict__ elems,
                                           const float2* __restrict__ dphi, const float2* __restrict__ vol,
                                           const float2* __restrict__ u, const int32_t* __restrict__ slot,
@@ -122,7 +133,7 @@ __device__ __forceinline__ df elem_df_one(int64_t e, int64_t ne, const int32_t* 
   constexpr int K = DIM + 1;
     df ul[K][D];
 #pragma unroll
-    for (int l = 0; l < K; ++l) load_u_df<D>(u, __ldg(elems + (int64_t)l * ne + e), ul[l]);
+    for (int l = 0; l < K; ++l) load_u_df<D, COH>(u, __ldg(elems + (int64_t)l * ne + e), ul[l]);
     df g[DIM][DIM];
 #pragma unroll
     for (int l = 0; l < DIM; ++l)

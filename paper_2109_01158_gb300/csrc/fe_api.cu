@@ -122,6 +122,7 @@ void free_mesh(fe_ctx* c) {
   dev_free(c, &c->elems, ne * k);
   dev_free(c, &c->dir, nn * c->d);
   dev_free(c, &c->perm, nn);
+  dev_free(c, &c->iperm, nn);
   dev_free(c, &c->eperm, ne);
   c->perm_h.clear();
   c->eperm_h.clear();
@@ -507,11 +508,12 @@ fe_status fe_mesh_upload(fe_ctx* c, int dim, int d, int64_t nn, const double* co
   cudaMemcpy(c->elems, Ed.data(), sizeof(int32_t) * ne * k, cudaMemcpyHostToDevice);
   cudaMemcpy(c->dir, dd.data(), nn * d, cudaMemcpyHostToDevice);
   if (!ident) {
-    if ((st = dev_alloc(c, &c->perm, nn))) {
+    if ((st = dev_alloc(c, &c->perm, nn)) || (st = dev_alloc(c, &c->iperm, nn))) {
       free_mesh(c);
       return st;
     }
     cudaMemcpy(c->perm, c->perm_h.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice);
+    cudaMemcpy(c->iperm, iperm.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice);
   }
   if (!eident) {
     if ((st = dev_alloc(c, &c->eperm, ne))) {

@@ -98,6 +98,7 @@ struct fe_ctx {
   int32_t* elems = nullptr;    // (dim+1) SoA arrays of ne node ids
   uint8_t* dir = nullptr;      // nn*d Dirichlet mask, device order
   int32_t* perm = nullptr;     // nn (null = identity)
+  int32_t* iperm = nullptr;    // nn: caller node -> device node (null = identity)
   int32_t* eperm = nullptr;    // ne (null = identity)
 
   // device: precompute
@@ -193,13 +194,15 @@ fe_status set_error(fe_status st, const std::string& msg);
 fe_status cuda_check(cudaError_t e, const char* what);
 
 // fe_precompute.cu
-// fe_batch.cu: descriptors and launches of the batched kernels (FE_DF64 meshes).  host_stage
-// (pinned) and dev_stage hold n descriptors of batch_item_bytes() each; work buffers hold
-// batch_work_bytes(mesh) bytes, 256-byte aligned.
-size_t batch_item_bytes();
+// fe_batch.cu: the descriptor block and the persistent launch of the batched kernel (FE_DF64
+// meshes).  host_stage (pinned) and dev_stage hold batch_stage_bytes(n) bytes (16-byte
+// aligned); work buffers hold batch_work_bytes(mesh) bytes, 256-byte aligned.  One copy of
+// the block and one launch on stream s; wait_limit (SM clocks, <= 0 = the default 2e9)
+// bounds each wait of a tile for the tiles it depends on.
+size_t batch_stage_bytes(int n);
 size_t batch_work_bytes(const fe_ctx* m);
-fe_status batch_enqueue(cudaStream_t s, const fe_batch_item* items, int n, void* host_stage, void* dev_stage,
-                        int* status);
+fe_status batch_enqueue(cudaStream_t s, int device, const fe_batch_item* items, int n, void* host_stage,
+                        void* dev_stage, int* status, long long wait_limit);
 
 // fe_eval_f64.cu / fe_hessian.cu
 fe_status launch_node_prep_f64(fe_ctx* c, const double* v);

@@ -1,18 +1,23 @@
 // fe_server.cu -- continuous-batching server over resident meshes: the host runtime around
-// the batched kernels of fe_batch.cu (energy + exact gradient, double-float arithmetic).
+// the persistent batched kernel of fe_batch.cu (energy + exact gradient, double-float
+// arithmetic).
 //
 // Threads:
-//   worker     waits for arrived requests; admits them FIFO while their device bytes fit in
-//              one contiguous region of the arena ring; stages their vectors in pinned memory
-//              (one host-to-device copy per batch; vectors the caller keeps in page-locked
-//              memory are copied straight from it); enqueues the three batch kernels and the
-//              device-to-host copies of the results; records a completion event.  It prepares
-//              the next batch while earlier ones run (up to kSlots batches in flight).
-//   completer  waits for the batches in launch order, copies each request's J and g into the
-//              caller's buffers, stamps the completion time, frees the arena region and the
-//              batch slot.
-// Device layout of one batch region: [v_1 .. v_n][g_1 .. g_n][J_1 .. J_n][work_1 .. work_n],
-// every piece 256-byte aligned; the v block is copied in, the g and J blocks copied out.
+//   worker     waits for arrived requests; admits them FIFO while their device scratch fits
+//              in one contiguous region of the arena ring; orders the batch smallest mesh
+//              first (so that small requests sharing a batch with a large one finish early);
+//              enqueues the descriptor copy and the one persistent launch.  The kernel reads
+//              each request's vector and writes its gradient directly in page-locked host
+//              memory (the caller's, or the server's staging for pageable buffers), and
+//              raises a per-request completion flag there.  The worker prepares the next batch
+//              while earlier ones run (up to kSlots batches in flight).  With max_batch > 1
+//              every slot has its own stream, so a batch's blocks start on the SMs that the
+//              batch before it frees during its last tiles; with max_batch = 1 (one request
+//              at a time) all batches run in order on one stream.
+//   completer  polls the completion flags of the batches in flight and completes each
+//              request as soon as its flag is up (copies out of the staging where the caller's
+//              buffer is pageable, stamps the completion time), not at the end of its batch;
+//              frees a batch's arena region and slot once all its requests are complete.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -39,52 +44,70 @@ struct Req {
   const double* v = nullptr;
   double* J = nullptr;
   double* g = nullptr;
+  const double* v_dev = nullptr;   // device address of a page-locked v (null: pageable)
+  double* g_dev = nullptr;         // device address of a page-locked g (null: pageable)
   int64_t ticket = 0;
   size_t nvals = 0;   // n_nodes * d
-  size_t work = 0;    // batch scratch bytes
-  size_t bytes = 0;   // device bytes in a batch region
+  size_t bytes = 0;   // device scratch of the batched kernel (arena bytes)
   double t_arrival = 0.0, t_start = 0.0, t_done = 0.0;
   int status = FE_OK;
   bool done = false;
-  bool v_pinned = false, g_pinned = false;   // page-locked caller buffers: copied by DMA directly
 };
 
 struct Slot {
   std::vector<Req*> reqs;
-  std::vector<size_t> voff, goff, Joff;   // offsets inside the region
-  size_t off = 0, bytes = 0, vbytes = 0, obytes = 0, obase = 0;
-  unsigned char* pin_in = nullptr;
-  unsigned char* pin_out = nullptr;
+  std::vector<size_t> voff, goff;    // offsets in the pinned staging (pageable buffers)
+  std::vector<char> fin;             // request k completed (completer only)
+  std::vector<Req*> newly;           // completed by the last poll, not yet published
+  int nfin = 0;
+  size_t off = 0, bytes = 0;         // arena region
+  unsigned char* pin_in = nullptr;   // staging of pageable vectors
+  unsigned char* pin_out = nullptr;  // J of every request, then staging of pageable gradients
+  unsigned char* pin_in_dev = nullptr;
+  unsigned char* pin_out_dev = nullptr;
   size_t pin_in_cap = 0, pin_out_cap = 0;
-  void* items_host = nullptr;
-  void* items_dev = nullptr;
-  int items_cap = 0;
+  int* flags = nullptr;              // page-locked completion flags, one per request
+  int* flags_dev = nullptr;
+  void* stage_host = nullptr;        // descriptor block (pinned) and its device copy
+  void* stage_dev = nullptr;
   std::vector<fe_batch_item> items;
+  cudaStream_t stream = nullptr;     // the server's stream, or the slot's own (max_batch > 1)
+  bool own_stream = false;
+  bool any_error = false;            // a request of the batch ended with an error flag
   cudaEvent_t done = nullptr;
   fe_status launch_status = FE_OK;
 };
 
-// Grow a pinned host buffer to at least `need` bytes (geometrically after the first
-// allocation; only a request larger than the staging size set at creation grows it).
-fe_status grow_pinned(unsigned char** p, size_t* cap, size_t need) {
-  if (need <= *cap) return FE_OK;
-  size_t n = *cap ? std::max(need, *cap * 2) : need;
-  if (*p) cudaFreeHost(*p);
-  *p = nullptr;
-  *cap = 0;
-  fe_status st = cuda_check(cudaMallocHost((void**)p, n), "server pinned staging");
-  if (!st) *cap = n;
-  return st;
-}
-
-// True for page-locked host memory (cudaMallocHost / cudaHostAlloc / cudaHostRegister).
-bool is_pinned(const void* p) {
+// Device address of page-locked host memory, or null (pageable, or not mapped).
+template <class T>
+T* mapped(T* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return nullptr;
   }
-  return a.type == cudaMemoryTypeHost;
+  if (a.type != cudaMemoryTypeHost) return nullptr;
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, const_cast<void*>(static_cast<const void*>(p)), 0) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return static_cast<T*>(d);
+}
+
+// Grow a pinned host buffer to at least `need` bytes (geometrically after the first
+// allocation; only a request larger than the staging size set at creation grows it) and
+// look up its device address.
+fe_status grow_pinned(unsigned char** p, unsigned char** pd, size_t* cap, size_t need) {
+  if (need <= *cap && *p) return FE_OK;
+  size_t n = *cap ? std::max(need, *cap * 2) : std::max<size_t>(need, 256);
+  if (*p) cudaFreeHost(*p);
+  *p = *pd = nullptr;
+  *cap = 0;
+  fe_status st = cuda_check(cudaMallocHost((void**)p, n), "server pinned staging");
+  if (st) return st;
+  *cap = n;
+  return cuda_check(cudaHostGetDevicePointer((void**)pd, *p, 0), "server pinned staging address");
 }
 
 }  // namespace
@@ -95,9 +118,9 @@ using namespace fe;
 struct fe_server {
   int device = 0;
   cudaStream_t stream = nullptr;
-  int* status = nullptr;        // device status word of the batch kernels (domain bits)
+  int* status = nullptr;        // device status word of the batched kernel
   size_t budget = 0;
-  size_t staging = 0;           // pinned bytes per slot and direction (vectors in, results out)
+  size_t staging = 0;           // pinned bytes per slot and direction (pageable vectors)
   int max_batch = 1;
   unsigned char* arena = nullptr;
   Clock::time_point epoch;
@@ -144,90 +167,52 @@ struct fe_server {
 
   void worker_loop();
   void completer_loop();
+  bool poll(Slot* S);
   fe_status launch(Slot* S);
 };
 
 fe_status fe_server::launch(Slot* S) {
   const int n = (int)S->reqs.size();
-  // layout of the region
-  S->voff.resize(n);
-  S->goff.resize(n);
-  S->Joff.resize(n);
-  size_t o = 0;
+  // smallest mesh first: the tiles of a batch are handed out in this order
+  std::stable_sort(S->reqs.begin(), S->reqs.end(), [](const Req* a, const Req* b) { return a->mesh->ne < b->mesh->ne; });
+  S->voff.assign(n, 0);
+  S->goff.assign(n, 0);
+  S->fin.assign(n, 0);
+  S->newly.clear();
+  S->nfin = 0;
+  size_t vin = 0, out = al256(sizeof(double) * n);
   for (int k = 0; k < n; ++k) {
-    S->voff[k] = o;
-    o += al256(sizeof(double) * S->reqs[k]->nvals);
+    const Req* r = S->reqs[k];
+    if (!r->v_dev) {
+      S->voff[k] = vin;
+      vin += al256(sizeof(double) * r->nvals);
+    }
+    if (!r->g_dev) {
+      S->goff[k] = out;
+      out += al256(sizeof(double) * r->nvals);
+    }
   }
-  S->vbytes = o;
-  S->obase = o;
-  for (int k = 0; k < n; ++k) {
-    S->goff[k] = o;
-    o += al256(sizeof(double) * S->reqs[k]->nvals);
-  }
-  for (int k = 0; k < n; ++k) {
-    S->Joff[k] = o;
-    o += 256;
-  }
-  S->obytes = o - S->obase;
   fe_status st;
-  if ((st = grow_pinned(&S->pin_in, &S->pin_in_cap, S->vbytes))) return st;
-  if ((st = grow_pinned(&S->pin_out, &S->pin_out_cap, S->obytes))) return st;
-  if (n > S->items_cap) {
-    if (S->items_host) cudaFreeHost(S->items_host);
-    if (S->items_dev) cudaFree(S->items_dev);
-    S->items_host = S->items_dev = nullptr;
-    S->items_cap = 0;
-    const int cap = std::max(n, 64);
-    if ((st = cuda_check(cudaMallocHost(&S->items_host, batch_item_bytes() * cap), "server descriptors"))) return st;
-    if ((st = cuda_check(cudaMalloc(&S->items_dev, batch_item_bytes() * cap), "server descriptors"))) return st;
-    S->items_cap = cap;
-  }
+  if ((st = grow_pinned(&S->pin_in, &S->pin_in_dev, &S->pin_in_cap, vin))) return st;
+  if ((st = grow_pinned(&S->pin_out, &S->pin_out_dev, &S->pin_out_cap, out))) return st;
+  std::memset(S->flags, 0, sizeof(int) * n);
   unsigned char* base = arena + S->off;
   S->items.resize(n);
-  bool staged_in = false, staged_out = false;
+  size_t w = 0;
   for (int k = 0; k < n; ++k) {
     Req* r = S->reqs[k];
-    if (!r->v_pinned) {
-      std::memcpy(S->pin_in + S->voff[k], r->v, sizeof(double) * r->nvals);
-      staged_in = true;
-    }
-    if (!r->g_pinned) staged_out = true;
+    if (!r->v_dev) std::memcpy(S->pin_in + S->voff[k], r->v, sizeof(double) * r->nvals);
     fe_batch_item& it = S->items[k];
     it.mesh = r->mesh;
-    it.v = reinterpret_cast<const double*>(base + S->voff[k]);
-    it.g = reinterpret_cast<double*>(base + S->goff[k]);
-    it.J = reinterpret_cast<double*>(base + S->Joff[k]);
-    it.work = nullptr;
+    it.v = r->v_dev ? r->v_dev : reinterpret_cast<const double*>(S->pin_in_dev + S->voff[k]);
+    it.g = r->g_dev ? r->g_dev : reinterpret_cast<double*>(S->pin_out_dev + S->goff[k]);
+    it.J = reinterpret_cast<double*>(S->pin_out_dev) + k;
+    it.done = S->flags_dev + k;
+    it.work = base + w;
+    w += r->bytes;
   }
-  size_t w = o;
-  for (int k = 0; k < n; ++k) {
-    S->items[k].work = base + w;
-    w += S->reqs[k]->work;
-  }
-  // inputs: one copy of the staged block, then the page-locked vectors straight from the callers
-  if (staged_in &&
-      (st = cuda_check(cudaMemcpyAsync(base, S->pin_in, S->vbytes, cudaMemcpyHostToDevice, stream), "server copy in")))
-    return st;
-  for (int k = 0; k < n; ++k) {
-    Req* r = S->reqs[k];
-    if (r->v_pinned && (st = cuda_check(cudaMemcpyAsync(base + S->voff[k], r->v, sizeof(double) * r->nvals,
-                                                        cudaMemcpyHostToDevice, stream), "server copy in")))
-      return st;
-  }
-  if ((st = batch_enqueue(stream, S->items.data(), n, S->items_host, S->items_dev, status))) return st;
-  // outputs: the staged block (all g's and J's, or the J's only), page-locked g's directly
-  const size_t jbase = S->Joff.empty() ? S->obytes : S->Joff[0] - S->obase;
-  const size_t from = staged_out ? 0 : jbase;
-  if ((st = cuda_check(cudaMemcpyAsync(S->pin_out + from, base + S->obase + from, S->obytes - from,
-                                       cudaMemcpyDeviceToHost, stream), "server copy out")))
-    return st;
-  for (int k = 0; k < n; ++k) {
-    Req* r = S->reqs[k];
-    if (r->g_pinned && (st = cuda_check(cudaMemcpyAsync(r->g, base + S->goff[k], sizeof(double) * r->nvals,
-                                                        cudaMemcpyDeviceToHost, stream), "server copy out")))
-      return st;
-  }
-  return cuda_check(cudaEventRecord(S->done, stream), "server event");
+  if ((st = batch_enqueue(S->stream, device, S->items.data(), n, S->stage_host, S->stage_dev, status, 0))) return st;
+  return cuda_check(cudaEventRecord(S->done, S->stream), "server event");
 }
 
 void fe_server::worker_loop() {
@@ -264,11 +249,13 @@ void fe_server::worker_loop() {
     for (Req* r : pending) {
       if (n >= max_batch || r->t_arrival > t || total + r->bytes > avail) break;
       const size_t vb = al256(sizeof(double) * r->nvals);
-      // the staging buffers bound a batch too (a single larger request grows them)
-      if (n > 0 && (vin + vb > staging || vout + vb + 256 > staging)) break;
+      const size_t in = r->v_dev ? 0 : vb, outb = r->g_dev ? 0 : vb;
+      // the staging buffers bound a batch of pageable requests too (a single larger request
+      // grows them)
+      if (n > 0 && (vin + in > staging || vout + outb > staging)) break;
       total += r->bytes;
-      vin += vb;
-      vout += vb + 256;
+      vin += in;
+      vout += outb;
       ++n;
     }
     if (n == 0) {   // the oldest request waits for arena space
@@ -289,15 +276,63 @@ void fe_server::worker_loop() {
     inflight.push_back(S);
     batches += 1;
     maxb = std::max<int64_t>(maxb, n);
-    if (!S->launch_status) launches += 3;
+    if (!S->launch_status) launches += 1;
     cv.notify_all();
   }
   worker_done = true;
   cv.notify_all();
 }
 
+// Complete the requests of S whose flags are up (without the lock); true if any.  A batch
+// whose launch failed, or whose kernel has ended (or failed) with flags still down after a
+// last look at them, completes its remaining requests with an error.
+bool fe_server::poll(Slot* S) {
+  const int n = (int)S->reqs.size();
+  auto scan = [&] {
+    for (int k = 0; k < n; ++k) {
+      if (S->fin[k]) continue;
+      const int f = __atomic_load_n(S->flags + k, __ATOMIC_ACQUIRE);
+      if (!f) continue;
+      Req* r = S->reqs[k];
+      double J;
+      std::memcpy(&J, S->pin_out + sizeof(double) * k, sizeof(double));
+      if (!r->g_dev) std::memcpy(r->g, S->pin_out + S->goff[k], sizeof(double) * r->nvals);
+      *r->J = J;
+      r->status = f != 1 ? FE_ETIMEOUT : (std::isinf(J) && J > 0) ? FE_EDOMAIN : FE_OK;
+      if (f != 1) S->any_error = true;
+      S->fin[k] = 1;
+      S->nfin += 1;
+      S->newly.push_back(r);
+    }
+  };
+  fe_status fail = S->launch_status;
+  if (!fail && S->nfin < n) {
+    scan();
+    if (S->nfin < n) {
+      const cudaError_t q = cudaEventQuery(S->done);
+      if (q == cudaSuccess) {
+        scan();   // the kernel has ended: every flag it raised is visible now
+        if (S->nfin < n) fail = set_error(FE_ECUDA, "server batch: the kernel ended without completing a request");
+      } else if (q != cudaErrorNotReady) {
+        fail = cuda_check(q, "server batch");
+      }
+    }
+  }
+  if (fail) S->any_error = true;
+  if (fail)
+    for (int k = 0; k < n; ++k)
+      if (!S->fin[k]) {
+        S->reqs[k]->status = fail;
+        S->fin[k] = 1;
+        S->nfin += 1;
+        S->newly.push_back(S->reqs[k]);
+      }
+  return !S->newly.empty();
+}
+
 void fe_server::completer_loop() {
   cudaSetDevice(device);
+  std::vector<Slot*> snap;
   std::unique_lock<std::mutex> lk(mu);
   for (;;) {
     if (inflight.empty()) {
@@ -305,34 +340,43 @@ void fe_server::completer_loop() {
       cv.wait(lk);
       continue;
     }
-    Slot* S = inflight.front();
+    snap.assign(inflight.begin(), inflight.end());
     lk.unlock();
-    fe_status st = S->launch_status;
-    if (!st) st = cuda_check(cudaEventSynchronize(S->done), "server batch");
-    for (size_t k = 0; k < S->reqs.size(); ++k) {
-      Req* r = S->reqs[k];
-      if (st) {
-        r->status = st;
-        continue;
-      }
-      if (!r->g_pinned) std::memcpy(r->g, S->pin_out + (S->goff[k] - S->obase), sizeof(double) * r->nvals);
-      double J;
-      std::memcpy(&J, S->pin_out + (S->Joff[k] - S->obase), sizeof(double));
-      *r->J = J;
-      r->status = std::isinf(J) && J > 0 ? FE_EDOMAIN : FE_OK;
-    }
+    bool progress = false;
+    for (Slot* S : snap) progress |= poll(S);
     const double td = now();
     lk.lock();
-    for (Req* r : S->reqs) {
-      r->t_done = td;
-      r->done = true;
+    if (progress) {
+      for (Slot* S : snap) {
+        for (Req* r : S->newly) {
+          r->t_done = td;
+          r->done = true;
+        }
+        completed += (int64_t)S->newly.size();
+        S->newly.clear();
+      }
+      // a batch whose requests are all complete no longer touches its region, staging or
+      // flags (later work on its stream runs after its kernel); after an error its kernel may
+      // still run, so it is waited for first
+      while (!inflight.empty() && inflight.front()->nfin == (int)inflight.front()->reqs.size()) {
+        Slot* S = inflight.front();
+        if (S->any_error) {
+          lk.unlock();
+          cudaEventSynchronize(S->done);
+          lk.lock();
+          S->any_error = false;
+        }
+        S->reqs.clear();
+        inflight.pop_front();
+        regions.pop_front();
+        free_slots.push_back(S);
+      }
+      cv.notify_all();
+    } else {
+      lk.unlock();
+      std::this_thread::yield();
+      lk.lock();
     }
-    completed += (int64_t)S->reqs.size();
-    S->reqs.clear();
-    inflight.pop_front();
-    regions.pop_front();
-    free_slots.push_back(S);
-    cv.notify_all();
   }
 }
 
@@ -354,17 +398,23 @@ fe_status fe_server_create(fe_server** out, int device, size_t hbm_budget, int m
   if (!st) st = cuda_check(cudaMalloc((void**)&s->status, sizeof(int)), "server status");
   if (!st) st = cuda_check(cudaMemset(s->status, 0, sizeof(int)), "server status");
   if (!st) st = cuda_check(cudaMalloc((void**)&s->arena, s->budget), "server arena");
-  // pinned staging and descriptors of every slot are allocated here, so that serving
+  // pinned staging, flags and descriptors of every slot are allocated here, so that serving
   // allocates nothing (allocating pinned memory costs milliseconds)
   s->staging = std::min<size_t>(std::max<size_t>(s->budget / 16, 1 << 20), (size_t)256 << 20);
   for (int k = 0; k < kSlots && !st; ++k) {
     Slot& S = s->slot_store[k];
-    st = cuda_check(cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming), "server event");
-    if (!st) st = grow_pinned(&S.pin_in, &S.pin_in_cap, s->staging);
-    if (!st) st = grow_pinned(&S.pin_out, &S.pin_out_cap, s->staging);
-    if (!st) st = cuda_check(cudaMallocHost(&S.items_host, batch_item_bytes() * max_batch), "server descriptors");
-    if (!st) st = cuda_check(cudaMalloc(&S.items_dev, batch_item_bytes() * max_batch), "server descriptors");
-    if (!st) S.items_cap = max_batch;
+    S.stream = s->stream;
+    if (max_batch > 1) {
+      st = cuda_check(cudaStreamCreateWithFlags(&S.stream, cudaStreamNonBlocking), "server slot stream");
+      S.own_stream = !st;
+    }
+    if (!st) st = cuda_check(cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming), "server event");
+    if (!st) st = grow_pinned(&S.pin_in, &S.pin_in_dev, &S.pin_in_cap, s->staging);
+    if (!st) st = grow_pinned(&S.pin_out, &S.pin_out_dev, &S.pin_out_cap, s->staging);
+    if (!st) st = cuda_check(cudaMallocHost((void**)&S.flags, sizeof(int) * max_batch), "server flags");
+    if (!st) st = cuda_check(cudaHostGetDevicePointer((void**)&S.flags_dev, S.flags, 0), "server flags");
+    if (!st) st = cuda_check(cudaMallocHost(&S.stage_host, batch_stage_bytes(max_batch)), "server descriptors");
+    if (!st) st = cuda_check(cudaMalloc(&S.stage_dev, batch_stage_bytes(max_batch)), "server descriptors");
     s->free_slots.push_back(&S);
   }
   if (prev >= 0) cudaSetDevice(prev);
@@ -393,10 +443,15 @@ fe_status fe_server_destroy(fe_server* s) {
   cudaSetDevice(s->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
   for (Slot& S : s->slot_store) {
+    if (S.own_stream) {
+      cudaStreamSynchronize(S.stream);
+      cudaStreamDestroy(S.stream);
+    }
     if (S.pin_in) cudaFreeHost(S.pin_in);
     if (S.pin_out) cudaFreeHost(S.pin_out);
-    if (S.items_host) cudaFreeHost(S.items_host);
-    if (S.items_dev) cudaFree(S.items_dev);
+    if (S.flags) cudaFreeHost(S.flags);
+    if (S.stage_host) cudaFreeHost(S.stage_host);
+    if (S.stage_dev) cudaFree(S.stage_dev);
     if (S.done) cudaEventDestroy(S.done);
   }
   if (s->arena) cudaFree(s->arena);
@@ -423,10 +478,9 @@ fe_status fe_server_submit(fe_server* s, const fe_ctx* mesh, const double* v_hos
   r->J = J_host;
   r->g = g_host;
   r->nvals = (size_t)mesh->nn * mesh->d;
-  r->work = batch_work_bytes(mesh);
-  r->v_pinned = is_pinned(v_host);
-  r->g_pinned = is_pinned(g_host);
-  r->bytes = 2 * al256(sizeof(double) * r->nvals) + 256 + r->work;
+  r->v_dev = mapped(v_host);
+  r->g_dev = mapped(g_host);
+  r->bytes = batch_work_bytes(mesh);
   if (r->bytes > s->budget) {
     delete r;
     return set_error(FE_EINVAL, "server request larger than the HBM budget");

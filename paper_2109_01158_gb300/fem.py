@@ -90,6 +90,7 @@ _SIGNATURES = {
     "fe_batch_energy_gradient": [_vp, _vp, _int],
     "fe_batch_sync_status": [_vp],
     "fe_batch_launch_count": [_vp, _vp],
+    "fe_batch_set_wait_limit": [_vp, _i64],
     "fe_server_create": [_vp, _int, ctypes.c_size_t, _int],
     "fe_server_destroy": [_vp],
     "fe_server_submit": [_vp, _vp, _vp, _vp, _vp, _dbl, _vp],
@@ -254,6 +255,7 @@ fe_batch_create = _checked("fe_batch_create")
 fe_batch_destroy = _checked("fe_batch_destroy")
 fe_batch_energy_gradient = _checked("fe_batch_energy_gradient")
 fe_batch_launch_count = _checked("fe_batch_launch_count")
+fe_batch_set_wait_limit = _checked("fe_batch_set_wait_limit")
 
 
 def fe_batch_sync_status(batch) -> int:
@@ -266,12 +268,13 @@ def fe_batch_sync_status(batch) -> int:
 
 class BatchItem(ctypes.Structure):
     """ctypes mirror of fe_batch_item."""
-    _fields_ = [("mesh", _vp), ("v", _vp), ("J", _vp), ("g", _vp), ("work", _vp)]
+    _fields_ = [("mesh", _vp), ("v", _vp), ("J", _vp), ("g", _vp), ("work", _vp), ("done", _vp)]
 
 
 class Batch:
     """Batched executor (fe_batch) on one device and stream: `run(items)` enqueues one
-    energy + gradient evaluation of every (mesh, v, J, g, work) item in three launches."""
+    energy + gradient evaluation of every (mesh, v, J, g, work) item in one persistent
+    launch."""
 
     def __init__(self, device=0):
         self.device = torch.device("cuda", device)
@@ -291,9 +294,15 @@ class Batch:
         """items: list of (FEMesh, v, J, g, work) with device tensors; work is a uint8 tensor
         of at least work_bytes(mesh) bytes whose data pointer is 256-byte aligned."""
         arr = (BatchItem * max(len(items), 1))()
-        for k, (mesh, v, J, g, work) in enumerate(items):
-            arr[k] = BatchItem(mesh.ctx.value, v.data_ptr(), J.data_ptr(), g.data_ptr(), work.data_ptr())
+        for k, item in enumerate(items):
+            mesh, v, J, g, work = item[:5]
+            done = item[5].data_ptr() if len(item) > 5 and item[5] is not None else None
+            arr[k] = BatchItem(mesh.ctx.value, v.data_ptr(), J.data_ptr(), g.data_ptr(), work.data_ptr(), done)
         fe_batch_energy_gradient(self.handle, arr, len(items))
+
+    def set_wait_limit(self, cycles: int = 0):
+        """SM clocks a tile waits for the tiles it depends on (0 = the default 2e9)."""
+        fe_batch_set_wait_limit(self.handle, int(cycles))
 
     def sync_status(self) -> int:
         return fe_batch_sync_status(self.handle)

@@ -4,10 +4,11 @@ A request asks for J(v) and grad J(v) on one mesh.  Meshes are precomputed once 
 resident on the device (a catalogue keyed by model and size).  The server runs in real time
 in the library (fe_server): requests arrive (Poisson process), wait in a FIFO, and are
 admitted while their device bytes (the scratch of the batched kernels plus v and g) fit in
-the HBM budget.  Each batch is evaluated in three launches whatever its size; requests that
-arrive while a batch runs join the next one, which is prepared and enqueued while the GPU
-is still busy.  The one-at-a-time baseline runs the same kernels with batches of one
-request, in arrival order.
+the HBM budget.  Each batch is evaluated in one persistent launch whatever its size, which
+reads the vectors and writes the results straight in page-locked host memory and completes
+each request on its own flag; requests that arrive while a batch runs join the next one,
+which is prepared and enqueued while the GPU is still busy.  The one-at-a-time baseline runs
+the same kernel with batches of one request, in arrival order.
 
 Latency of a request = completion time - arrival time; the report gives p50/p99 latency,
 requests/s and elements/s for both modes at the same offered load.
@@ -301,8 +302,8 @@ class MinimizeServer:
     its directions computed by the library's L-BFGS kernels (fe_lbfgs).  A request is admitted
     once it has arrived and its device bytes (the batched kernels' scratch, the 2 (m + 1)
     vectors of the L-BFGS memory and 6 more of its mesh's size) fit in the HBM budget.  Every round evaluates the
-    pending trial point of every admitted job in one batched launch (fe_batch, three kernels
-    whatever the number of jobs), feeds each job its J and g, and retires the jobs that have
+    pending trial point of every admitted job in one batched launch (fe_batch, one persistent
+    kernel whatever the number of jobs), feeds each job its J and g, and retires the jobs that have
     finished, which frees their bytes for the next arrivals.  Mode 'serial' admits one job at
     a time, in arrival order, with the same kernels.  A job's evaluations do not depend on the
     other jobs in the launch, so its iterates are the same in either mode."""

@@ -82,6 +82,97 @@ def test_batch_results_same_alone_and_in_the_mix():
 
 
 @pytest.mark.gpu
+def test_batch_in_page_locked_host_memory_with_completion_flags():
+    """v, J and g in page-locked host memory (read and written by the kernel directly) give
+    bitwise the results of device buffers; each request's completion flag is raised (1);
+    the whole batch is one launch."""
+    fem, serve = _gpu()
+    cat = serve.Catalogue(0)
+    keys = [("nh3", 11), ("plap", 3.0, 45), ("nh2", 32), ("plap", 1.5, 23)]
+    batch = fem.Batch(0)
+    dev_items, host_items = [], []
+    for k, key in enumerate(keys):
+        mesh = cat.get(key)
+        v = serve.request_vector(cat.workloads[key], k)
+        dev_items.append(_item(fem, mesh, v))
+        it = _item(fem, mesh, v)
+        vh = torch.from_numpy(v).pin_memory()
+        Jh = torch.zeros(1, dtype=torch.float64).pin_memory()
+        gh = torch.zeros(mesh.ndof, dtype=torch.float64).pin_memory()
+        done = torch.zeros(1, dtype=torch.int32).pin_memory()
+        host_items.append((mesh, vh, Jh, gh, it[4], done))
+    n0 = batch.launch_count()
+    batch.run(dev_items)
+    assert batch.sync_status() == fem.FE_OK
+    batch.run(host_items)
+    assert batch.sync_status() == fem.FE_OK
+    assert batch.launch_count() - n0 == 2
+    for d, h in zip(dev_items, host_items):
+        assert h[5].item() == 1
+        assert h[2].item() == d[2].item()
+        np.testing.assert_array_equal(h[3].numpy(), d[3].cpu().numpy())
+
+
+@pytest.mark.gpu
+def test_batch_wait_limit_runs_out_then_recovers():
+    """With a wait limit of one SM clock the first gather tile of a large request gives up
+    waiting for the element tiles still running (FE_ETIMEOUT, completion flag 3); the next
+    call with the default limit returns bitwise the results of a fresh executor."""
+    fem, serve = _gpu()
+    cat = serve.Catalogue(0)
+    key = ("nh3", 38)
+    mesh = cat.get(key)
+    v = serve.request_vector(cat.workloads[key], 0)
+    ref = _item(fem, mesh, v)
+    fresh = fem.Batch(0)
+    fresh.run([ref])
+    assert fresh.sync_status() == fem.FE_OK
+    batch = fem.Batch(0)
+    with pytest.raises(fem.FEError):
+        batch.set_wait_limit(-1)
+    batch.set_wait_limit(1)
+    it = _item(fem, mesh, v)
+    done = torch.zeros(1, dtype=torch.int32, device="cuda")
+    batch.run([it + (done,)])
+    with pytest.raises(fem.FEError) as e:
+        batch.sync_status()
+    assert e.value.status == fem.FE_ETIMEOUT and done.item() == 3
+    batch.set_wait_limit(0)
+    it2 = _item(fem, mesh, v)
+    done.zero_()
+    batch.run([it2 + (done,)])
+    assert batch.sync_status() == fem.FE_OK and done.item() == 1
+    assert it2[2].item() == ref[2].item()
+    np.testing.assert_array_equal(it2[3].cpu().numpy(), ref[3].cpu().numpy())
+
+
+@pytest.mark.gpu
+def test_native_server_completes_small_requests_before_the_large_one_of_their_batch():
+    """A batch holding one large request and several small ones: the small ones run first
+    (smallest mesh first) and complete on their own flags, before the large one."""
+    fem, serve = _gpu()
+    cat = serve.Catalogue(0)
+    big, smalls = ("nh3", 70), [("plap", 2.0, 23), ("nh2", 23), ("plap", 3.0, 32), ("nh3", 6)]
+    keys = [big] + smalls
+    bufs = []
+    for k, key in enumerate(keys):
+        mesh = cat.get(key)
+        v = torch.from_numpy(serve.request_vector(cat.workloads[key], k)).pin_memory()
+        g = torch.empty(mesh.ndof, dtype=torch.float64).pin_memory()
+        bufs.append((mesh, v, np.empty(1), g))
+    srv = fem.NativeServer(0, 2 << 30, 64)
+    for _ in range(2):   # the second round is timed: everything is warm
+        t0 = srv.now() + 0.02
+        tickets = [srv.submit(m, v.numpy(), J, g.numpy(), t0) for m, v, J, g in bufs]
+        res = [srv.wait(t) for t in tickets]
+    assert all(r[0] == fem.FE_OK for r in res)
+    assert len({r[2] for r in res}) == 1          # one batch: the same start time
+    t_big = res[0][3]
+    assert max(r[3] for r in res[1:]) < t_big
+    srv.close()
+
+
+@pytest.mark.gpu
 def test_batch_reports_domain_error_per_item():
     fem, serve = _gpu()
     w = mg.neohooke_cube3d(3)
@@ -124,9 +215,9 @@ def test_server_stream_results(mode):
 @pytest.mark.parametrize("max_batch", [256, 1], ids=["batched", "serial"])
 def test_native_server_results_equal_the_batch_call(max_batch, pinned):
     """fe_server (host vectors in, host results out; staged through its pinned buffers, or
-    copied by DMA straight from page-locked caller buffers) returns bitwise the J and g of the
-    batch call on each request alone, whatever the batching; every request completes after
-    it arrives and after it started."""
+    read and written by the kernel straight in page-locked caller buffers) returns bitwise the
+    J and g of the batch call on each request alone, whatever the batching, in one launch per
+    batch; every request completes after it arrives and after it started."""
     fem, serve = _gpu()
     cat = serve.Catalogue(0)
     keys = [("plap", 3.0, 23), ("nh3", 8), ("nh2", 45), ("plap", 1.5, 32), ("nh3", 8), ("nh2", 23)] * 3
@@ -160,7 +251,7 @@ def test_native_server_results_equal_the_batch_call(max_batch, pinned):
         assert J[0] == Ja
         np.testing.assert_array_equal(g, ga)
     stats = srv.stats()
-    assert stats["completed"] == len(reqs) and stats["launches"] == 3 * stats["batches"]
+    assert stats["completed"] == len(reqs) and stats["launches"] == stats["batches"]
     if max_batch == 1:
         assert stats["max_batch"] == 1 and stats["batches"] == len(reqs)
     srv.close()
