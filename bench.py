@@ -44,12 +44,26 @@ ELEM_BYTES = {  # (dim, precision) -> (bytes per element, bytes per node)
 # Whole-step algorithmic bytes add the patch CSR entries (4 B per element-node pair), the
 # row pointers (4 B per node) and the gradient written in FP64.
 STEP_EXTRA = {3: (4 * 4, 4 + 24), 2: (3 * 4, 4 + 16)}
-# FP64 operations of the 3D Neo-Hookean energy + exact gradient per element, counted on the
-# algorithm (F: 36 fma, cofactors/det: 27 + 5, I1: 9 fma, W ~ 6, dW/dF ~ 40, forces 36 fma;
-# an fma counts 2; log and one division counted as one operation each).
-F64_FLOPS_PER_TET = 250.0
-# FP64 peak of GB300: 152 SMs x 2 FP64 FMA lanes per SM per clock x 2 flops x 2.07 GHz.
-F64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 operations of the 3D Neo-Hookean energy + exact gradient per element, measured with
+# ncu on the 64^3 x 6 element kernel: 81.18 DFMA (2 flops each) + 33.56 DADD + 45.07 DMUL
+# thread instructions per tet.
+F64_FLOPS_PER_TET = 240.98
+
+
+def fp64_peak_tflops(dev_index: int, sm_max_mhz):
+    """FP64 peak of this GPU from its measured DFMA issue rate (fe_fp64_rate: operations per
+    SM clock per SM), its SM count and its maximum SM clock (nvidia-smi; the probe's own clock
+    when that is unknown): 2 flops x rate x SMs x clock."""
+    import torch
+    from paper_2109_01158_gb300 import fem
+    rate, ghz = fem.fp64_rate(dev_index, fem.FE_RATE_DFMA)
+    add_rate, _ = fem.fp64_rate(dev_index, fem.FE_RATE_DADD)
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    mhz = sm_max_mhz if sm_max_mhz else ghz * 1e3
+    peak = 2.0 * rate * sms * mhz * 1e6 / 1e12
+    return peak, {"dfma_per_clk_per_sm": rate, "dadd_per_clk_per_sm": add_rate, "sms": sms,
+                  "sm_mhz": mhz, "probe_sm_ghz": ghz,
+                  "formula": "2 flops x measured DFMA/clk/SM x SMs x max SM clock"}
 
 
 # What one step runs in each precision (for the variants' records).
@@ -410,9 +424,10 @@ def run_ours(args, rank, world, local):
     hbm_achieved = elem_bytes / (elem_ms / 1e3) / 1e9
     if prec == "f64" and w.dim == 3 and w.model == mg.MODEL_NEOHOOKE:
         achieved = F64_FLOPS_PER_TET * w.ne / (elem_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": F64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / F64_PEAK_TFLOPS, "traffic": None,
-                "peak_kind": "derived FP64 (152 SMs x 2 FMA/clk x 2.07 GHz)",
+        f64_peak, f64_probe = fp64_peak_tflops(local, clocks.get("sm_max_mhz"))
+        roof = {"bound": "alu", "achieved": achieved, "peak": f64_peak, "unit": "TFLOP/s",
+                "frac": achieved / f64_peak, "traffic": None,
+                "peak_kind": "derived FP64 from a measured DFMA rate", "fp64_probe": f64_probe,
                 "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                         "frac": hbm_achieved / hbm_peak, "peak_kind": peak_kind}}
     else:

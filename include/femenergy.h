@@ -431,6 +431,17 @@ fe_status fe_server_stats(const fe_server* s, int64_t* batches, int64_t* max_bat
 /* Zero those counters (e.g. between measurement runs). */
 fe_status fe_server_reset_stats(fe_server* s);
 
+/* ---- Device characterisation -------------------------------------------------------
+ * Not in the paper: the issue rate of the FP64 unit, the roof of the FP64 kernels (bound by
+ * FP64 arithmetic).  Runs eight independent chains of one operation per thread, four
+ * 256-thread blocks per SM, 2^14 iterations (two launches of a few milliseconds), and
+ * returns operations per SM clock per SM (*per_clock_per_sm, from the SM cycle counter of
+ * every block) and the SM clock the launch ran at in GHz (*sm_ghz, from the cycles and the
+ * event time; may be NULL).  op: FE_RATE_DFMA, FE_RATE_DADD or FE_RATE_DMUL; anything else
+ * is FE_EINVAL. */
+enum { FE_RATE_DFMA = 0, FE_RATE_DADD = 1, FE_RATE_DMUL = 2 };
+fe_status fe_fp64_rate(int device, int op, double* per_clock_per_sm, double* sm_ghz);
+
 /* Energy without any allocation (the paper has no counterpart: this is an interface for
  * callers that cannot let this library allocate device memory -- a host program whose GPU
  * memory is owned entirely by its own pool allocator, or one whose time-critical loop must

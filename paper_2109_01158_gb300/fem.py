@@ -91,6 +91,7 @@ _SIGNATURES = {
     "fe_batch_sync_status": [_vp],
     "fe_batch_launch_count": [_vp, _vp],
     "fe_batch_set_wait_limit": [_vp, _i64],
+    "fe_fp64_rate": [_int, _int, _vp, _vp],
     "fe_server_create": [_vp, _int, ctypes.c_size_t, _int],
     "fe_server_destroy": [_vp],
     "fe_server_submit": [_vp, _vp, _vp, _vp, _vp, _dbl, _vp],
@@ -256,6 +257,15 @@ fe_batch_destroy = _checked("fe_batch_destroy")
 fe_batch_energy_gradient = _checked("fe_batch_energy_gradient")
 fe_batch_launch_count = _checked("fe_batch_launch_count")
 fe_batch_set_wait_limit = _checked("fe_batch_set_wait_limit")
+fe_fp64_rate = _checked("fe_fp64_rate")
+FE_RATE_DFMA, FE_RATE_DADD, FE_RATE_DMUL = range(3)
+
+
+def fp64_rate(device=0, op=FE_RATE_DFMA):
+    """(operations per SM clock per SM, SM GHz during the measurement) of one FP64 operation."""
+    r, ghz = ctypes.c_double(), ctypes.c_double()
+    fe_fp64_rate(int(device), int(op), ctypes.byref(r), ctypes.byref(ghz))
+    return r.value, ghz.value
 
 
 def fe_batch_sync_status(batch) -> int:

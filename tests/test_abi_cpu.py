@@ -98,3 +98,23 @@ def test_binding_fails_loudly_without_library(tmp_path):
             fem.load_library(str(tmp_path / "missing.so"))
         finally:
             fem._lib = fem._lib_saved
+
+
+def test_device_free_argument_checks(libpath):
+    """Argument checks that come before any device call: the FP64 rate probe with an unknown
+    operation or a null result pointer, a batch executor's negative wait limit on a null
+    handle.  Run in a child process, so that a crash fails the test instead of the session."""
+    code = "\n".join([
+        "import ctypes, sys",
+        f"lib = ctypes.CDLL({libpath!r})",
+        "lib.fe_fp64_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]",
+        "lib.fe_batch_set_wait_limit.argtypes = [ctypes.c_void_p, ctypes.c_int64]",
+        "r = ctypes.c_double()",
+        "got = [lib.fe_fp64_rate(0, 3, ctypes.byref(r), None), lib.fe_fp64_rate(0, -1, ctypes.byref(r), None),",
+        "       lib.fe_fp64_rate(0, 0, None, None), lib.fe_batch_set_wait_limit(None, 5)]",
+        "print(got)",
+        "sys.exit(0 if got == [1, 1, 1, 1] else 1)",
+    ])
+    import sys
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0, (res.stdout, res.stderr)
