@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
   using S = typename P::S;
   constexpr int K = DIM + 1, NXY = P::NXY, DP = P::DP;
   constexpr int NE = kTileElems, NEW = NE / 32;              // element threads and warps
+  static_assert(NEW <= 32, "the producer adds one energy pair per element warp in one warp");
   constexpr int NN = 32 * kTileNodeWarps;                    // node threads
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ PipeBars bars;
@@ -172,6 +173,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
     return reinterpret_cast<float*>(smem + S::kRs + (i & 1) * S::kRsBytes + NXY * 4 * S::kSlots);
   };
   auto EW = [&](int i) { return reinterpret_cast<float*>(smem + S::kEw + (i & 1) * S::kEwBytes); };
+  auto BDB = [&](int i) { return reinterpret_cast<double*>(smem + S::kBd + (i % 3) * S::kBdBytes); };
+  auto BDM = [&](int i) { return reinterpret_cast<int*>(smem + S::kBd + (i % 3) * S::kBdBytes + S::kBdMaskOff); };
   // every thread of a warp calls wait() together and gets the same answer (the warp leaves the
   // pipeline as a whole, so no lane is left behind in a warp-wide operation)
   bool ok = true;
@@ -204,12 +207,23 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
     pipe_issue_elems<S, 4>(E(i), ta, in.x, in.y, &bars.e_full[i & 1]);
     ++nE[i & 1];
   };
-  auto issue_recs = [&](int i) {
+  // the element and node ranges of the next tile whose records are issued, loaded one issue
+  // ahead so that the issuer does not wait for them
+  int4 pre = make_int4(0, 0, 0, 0);
+  int pre_i = -1;
+  auto load_pre = [&](int i) {
+    if (i >= my_tiles) return;
     const int64_t tq = tile_of(i);
-    const int k0 = __ldg(ta.nbeg + tq);
-    info[i % 3] = make_int4(__ldg(ta.ebeg + tq), __ldg(ta.ebeg + tq + 1), k0, __ldg(ta.nbeg + tq + 1) - k0);
-    pipe_issue_recs(R(i), ta, k0, info[i % 3].w, &bars.r_full[i % 3]);
+    pre = make_int4(__ldg(ta.ebeg + tq), __ldg(ta.ebeg + tq + 1), __ldg(ta.nbeg + tq), __ldg(ta.nbeg + tq + 1));
+    pre_i = i;
+  };
+  auto issue_recs = [&](int i) {
+    if (pre_i != i) load_pre(i);
+    const int4 raw = pre;
+    info[i % 3] = make_int4(raw.x, raw.y, raw.z, raw.w - raw.z);
+    pipe_issue_recs(R(i), ta, raw.z, raw.w - raw.z, &bars.r_full[i % 3]);
     ++nR[i % 3];
+    load_pre(i + 1);
   };
   if (tid == 0) abort_flag = 0;
   if (issuer) {
@@ -246,7 +260,11 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
       }
       if (!wait(&bars.rs_full[i & 1], i >> 1)) break;
       if (ENERGY) {
-        const double x = pipe_warp_sum_floats(EW(i), NE);   // FP64 across lanes from float pairs
+        // the element warps' pairs, in FP64 across lanes in a fixed order
+        const float2 wp = lane < NEW ? reinterpret_cast<const float2*>(EW(i))[lane] : make_float2(0.f, 0.f);
+        const bool inf = __any_sync(0xffffffffu, isinf(wp.x));
+        double x = pipe_warp_sum(f2d_bits(wp.x) + f2d_bits(wp.y));
+        if (inf) x = CUDART_INF;
         if (lane == 0) epart[tile_of(i)] = x;
       }
       __syncwarp();
@@ -266,11 +284,40 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
       const int4* rec = R(i);
       float2* us = U(i);
       const int nt = info[i % 3].w;
-      for (int k = ntid; k < nt; k += NN) {
-        float2 w[D];
-        load_pairs_g<D>(upairs, rec[k].x, w);
+      double* bd = BDB(i);
+      int* bm = BDM(i);
+      // all loads of a thread's nodes first, then the stores: the loads are in flight together
+      // instead of one round trip per node; with the nodal values, each node's load b_i and
+      // Dirichlet mask for the patch sums
+      constexpr int RN = (S::kNodes + NN - 1) / NN;
+      float2 w[RN][D];
+      double bb[RN][D];
+      int mk[RN];
 #pragma unroll
-        for (int j = 0; j < D; ++j) us[k * DP + j] = w[j];
+      for (int q = 0; q < RN; ++q) {
+        const int k = ntid + q * NN;
+        mk[q] = 0;
+        if (k < nt) {
+          const int64_t n = rec[k].x;
+          load_pairs_g<D>(upairs, n, w[q]);
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            bb[q][j] = (GRAD && b) ? __ldg(b + n * D + j) : 0.0;
+            if (GRAD) mk[q] |= __ldg(dir + n * D + j) ? (1 << j) : 0;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < RN; ++q) {
+        const int k = ntid + q * NN;
+        if (k < nt) {
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            us[k * DP + j] = w[q][j];
+            if (GRAD) bd[k * D + j] = bb[q][j];
+          }
+          if (GRAD) bm[k] = mk[q];
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars.u_full[i & 1]);
@@ -280,9 +327,57 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
     for (int i = 1; i < my_tiles && ok; ++i)
       if (!gather(i)) break;
   } else if (elem_warp) {
-    // B: one thread per element of tile i
+    // Software-pipelined over the tiles: B (the elements) of tile i, then C (the patch sums)
+    // of tile i - 1, whose forces every element warp wrote before its own B of tile i -- so a
+    // warp that finishes B early goes on to C instead of waiting for the slowest warp.
     const float C1 = (float)mp.C1, D1 = (float)mp.D1;
+    // C: the patch sums of tile i, one thread per (tile node, component)
+    auto patch_sums = [&](int i) {
+      if (!wait(&bars.rs_full[i & 1], i >> 1)) return false;
+      if (GRAD) {
+        const int4* Rr = R(i);
+        const float2* rxy = RXY(i);
+        const float* rz = RZ(i);
+        const double* bd = BDB(i);
+        const int* bm = BDM(i);
+        const int nt = info[i % 3].w;
+        for (int w = tid; w < nt * D; w += NE) {
+          const int k = w / D, j = w - k * D;
+          const int4 rec = Rr[k];
+          const int beg = rec.z & 0xffff, cnt = (int)((unsigned)rec.z >> 16);
+          const float* col = (NXY && j < NXY) ? reinterpret_cast<const float*>(rxy) + j : rz;
+          const int str = (NXY && j < NXY) ? 2 : 1;
+          // walk the node's slots from position p (a function of k and cnt: consecutive nodes
+          // then start on different shared-memory banks), wrapping around; the order is
+          // fixed by the mesh alone
+          float sum = 0.f;
+          if (cnt > 0) {
+            const int p = (k & 7) < cnt ? (k & 7) : 0;
+            sum = col[(beg + p) * str];
+#pragma unroll 4
+            for (int q = beg + p + 1; q < beg + cnt; ++q) sum = __fadd_rn(sum, col[q * str]);
+#pragma unroll 4
+            for (int q = beg; q < beg + p; ++q) sum = __fadd_rn(sum, col[q * str]);
+          }
+          const int dst = (rec.w >> 1) - 1;
+          const int64_t n = rec.x;
+          if (dst < 0) {
+            const int64_t o = caller_order ? (int64_t)rec.y : n;
+            g[o * D + j] = ((bm[k] >> j) & 1) ? 0.0 : f2d_bits(sum) - bd[k * D + j];
+          } else {
+            part[(int64_t)dst * D + j] = sum;
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bars.rs_empty[i & 1]);
+        mbar_arrive(&bars.r_empty[i % 3]);
+      }
+      return true;
+    };
     for (int i = 0; i < my_tiles && ok; ++i) {
+      // B: one thread per element of tile i
       if (!wait(&bars.e_full[i & 1], i >> 1) || !wait(&bars.u_full[i & 1], i >> 1)) break;
       if (i >= 2 && !wait(&bars.rs_empty[i & 1], (i >> 1) - 1)) break;
       const int4 in = info[i % 3];
@@ -331,53 +426,27 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
           if constexpr (D != 2) rz[sl[0]] = r0[D - 1];
         }
       }
-      if (ENERGY) EW(i)[tid] = ew;
+      if (ENERGY) {
+        // the warp's |T| W as a float pair: a fixed TwoSum tree over the lanes (+Inf apart,
+        // as TwoSum on Inf gives NaN); the producer adds the tile's warp pairs in FP64
+        const bool inf = __any_sync(0xffffffffu, isinf(ew));
+        df p = {isinf(ew) ? 0.f : ew, 0.f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const df q = {__shfl_down_sync(0xffffffffu, p.hi, o), __shfl_down_sync(0xffffffffu, p.lo, o)};
+          p = df_add(p, q);
+        }
+        if (lane == 0) reinterpret_cast<float2*>(EW(i))[warp] = inf ? make_float2(CUDART_INF_F, 0.f) : make_float2(p.hi, p.lo);
+      }
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(&bars.e_empty[i & 1]);
         mbar_arrive(&bars.u_empty[i & 1]);
         mbar_arrive(&bars.rs_full[i & 1]);
       }
-      // C: patch sums of tile i once every element warp has written its forces, one thread
-      // per (tile node, component)
-      if (!wait(&bars.rs_full[i & 1], i >> 1)) break;
-      if (GRAD) {
-        const int4* Rr = R(i);
-        const int nt = in.w;
-        for (int w = tid; w < nt * D; w += NE) {
-          const int k = w / D, j = w - k * D;
-          const int4 rec = Rr[k];
-          const int beg = rec.z & 0xffff, cnt = (int)((unsigned)rec.z >> 16);
-          const float* col = (NXY && j < NXY) ? reinterpret_cast<const float*>(rxy) + j : rz;
-          const int str = (NXY && j < NXY) ? 2 : 1;
-          // walk the node's slots from position k mod cnt, wrapping around: consecutive nodes
-          // then start on different shared-memory banks; the order is fixed by the mesh alone
-          float sum = 0.f;
-          if (cnt > 0) {
-            const int p = (int)((unsigned)k % (unsigned)cnt);
-            sum = col[(beg + p) * str];
-#pragma unroll 4
-            for (int q = beg + p + 1; q < beg + cnt; ++q) sum = __fadd_rn(sum, col[q * str]);
-#pragma unroll 4
-            for (int q = beg; q < beg + p; ++q) sum = __fadd_rn(sum, col[q * str]);
-          }
-          const int dst = (rec.w >> 1) - 1;
-          const int64_t n = rec.x;
-          if (dst < 0) {
-            const int64_t o = caller_order ? (int64_t)rec.y : n;
-            const double sj = f2d_bits(sum);
-            g[o * D + j] = __ldg(dir + n * D + j) ? 0.0 : (b ? sj - __ldg(b + n * D + j) : sj);
-          } else {
-            part[(int64_t)dst * D + j] = sum;
-          }
-        }
-      }
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&bars.rs_empty[i & 1]);
-        mbar_arrive(&bars.r_empty[i % 3]);
-      }
+      if (i >= 1 && !patch_sums(i - 1)) break;
     }
+    if (ok && my_tiles > 0) patch_sums(my_tiles - 1);
   }
 
   __syncthreads();

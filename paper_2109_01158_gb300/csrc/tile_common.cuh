@@ -37,7 +37,11 @@ __device__ __forceinline__ double f2d_bits(float f) {
 //   R[3]   node records (int4 per tile node);
 //   U[2]   the tile's nodal values, NU bytes per node;
 //   Rs[2]  the tile's local forces, RB bytes per slot;
-//   Ew[2]  the tile's element energies |T| W (float per element).
+//   Ew[2]  the tile's element energies |T| W (float per element);
+//   Bd[3]  the tile nodes' load b_i (D doubles per node) and Dirichlet mask (an int per node,
+//          bit j for dof j), copied by the node warps with the nodal values, so that the
+//          patch sums read them from shared memory; three buffers like the records, as they
+//          are read until the patch sums of the tile are done.
 template <int DIM, int D, int EB, int NU, int RB>
 struct TilePipe {
   static constexpr int kNodes = tile_max_nodes(DIM);
@@ -51,12 +55,16 @@ struct TilePipe {
   static constexpr int kUBytes = (kNodes * NU + 15) / 16 * 16;
   static constexpr int kRsBytes = (kSlots * RB + 15) / 16 * 16;
   static constexpr int kEwBytes = kTileElems * 4;
+  static constexpr int kBdMaskOff = kNodes * D * 8;                 // ints after the doubles
+  static constexpr int kBdBytes = (kBdMaskOff + kNodes * 4 + 15) / 16 * 16;
   static constexpr int kE = 0;
   static constexpr int kR = kE + 2 * kEBytes;
   static constexpr int kU = kR + 3 * kRBytes;
   static constexpr int kRs = kU + 2 * kUBytes;
   static constexpr int kEw = kRs + 2 * kRsBytes;
-  static constexpr int kBytes = kEw + 2 * kEwBytes;
+  static constexpr int kBd = kEw + 2 * kEwBytes;
+  static constexpr int kBytes = kBd + 3 * kBdBytes;
+  static_assert(kBytes <= 227 * 1024, "the pipeline must fit in the shared memory of one block");
   static_assert(kEBytes % 16 == 0 && kRBytes % 16 == 0, "alignment");
   static_assert(kTileElems % 128 == 0, "the energy sum reads the tile in rows of 128");
   static_assert(2 * kRsBytes >= 2 * kTileThreads * 8, "the final reduction reuses Rs");
