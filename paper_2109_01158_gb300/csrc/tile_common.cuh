@@ -84,13 +84,15 @@ struct TileArgs {
 };
 
 // Thread 0: bulk copies of the element arrays of elements [e0, e1) into the stage at `st`,
-// completing on `bar` (one arrival; an empty range completes the phase at once).
+// completing on `bar` (one arrival; an empty range completes the phase at once).  The stage
+// was last read by ordinary loads of the element warps, which released it through the empty
+// barrier the caller waited for; a bulk copy that overwrites data read that way needs no
+// proxy fence (only data written by ordinary stores and read by the copy engine would).
 template <class S, int EB>
 __device__ __forceinline__ void pipe_issue_elems(unsigned char* st, const TileArgs& A, int e0, int e1,
                                                  uint64_t* bar) {
   const int n = e1 - e0;
   const uint32_t bytes = ((uint32_t)n * EB + 15u) & ~15u;
-  fence_proxy_async_smem();
   mbar_arrive_expect_tx(bar, S::kArrays * bytes + (uint32_t)n * 16u);
   if (n > 0) {
 #pragma unroll
@@ -102,9 +104,9 @@ __device__ __forceinline__ void pipe_issue_elems(unsigned char* st, const TileAr
   }
 }
 
-// Thread 0: bulk copy of the node records [k0, k0 + nt) into `rb`, completing on `bar`.
+// Thread 0: bulk copy of the node records [k0, k0 + nt) into `rb`, completing on `bar` (the
+// slot was released like an element stage, so no proxy fence either).
 __device__ __forceinline__ void pipe_issue_recs(int4* rb, const TileArgs& A, int k0, int nt, uint64_t* bar) {
-  fence_proxy_async_smem();
   mbar_arrive_expect_tx(bar, (uint32_t)nt * 16u);
   if (nt > 0) bulk_g2s(rb, A.node + k0, (uint32_t)nt * 16u, bar);
 }
