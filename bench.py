@@ -697,6 +697,8 @@ def served_minimisations(device):
     import torch
     from paper_2109_01158_gb300 import serve
     msrv = serve.MinimizeServer(device)
+    for mode in ("serial", "batched"):   # untimed warm-up of both modes (first-use costs)
+        msrv.run(serve.make_minimize_requests(2, rate=40.0, device=device), mode)
     served = {}
     for mode in ("serial", "batched"):
         reqs = serve.make_minimize_requests(16, rate=40.0, device=device)
@@ -747,6 +749,14 @@ def run_minimize(args, device, full=True):
     if full:
         runs += [("f64_exact_torch_memory", fem.FE_F64, "exact", False), ("f32_exact", fem.FE_F32_COMP, "exact", True),
                  ("f64_fd", fem.FE_F64, "fd", True)]
+    # untimed warm-up of every method (a few iterations): the first use of a kernel in a
+    # process loads its module, which would otherwise be timed with the first run
+    for name, prec, grad, devmem in runs:
+        gm.set_precision(prec)
+        lbfgs(mesh_evaluator(gm, grad, eps=1e-6), v0, gtol=1e-6, relative=True, max_iter=3, device_memory=devmem)
+    gm.set_precision(fem.FE_F64)
+    newton_cg(mesh_evaluator(gm), mesh_hvp(gm), v0, gtol=1e-6, relative=True, cg=mesh_cg(gm), max_iter=1)
+    torch.cuda.synchronize(dev)
     for name, prec, grad, devmem in runs:
         gm.set_precision(prec)
         r = lbfgs(mesh_evaluator(gm, grad, eps=1e-6), v0, gtol=1e-6, relative=True, max_iter=args.minimize_iters,
