@@ -50,20 +50,23 @@ STEP_EXTRA = {3: (4 * 4, 4 + 24), 2: (3 * 4, 4 + 16)}
 F64_FLOPS_PER_TET = 240.98
 
 
-def fp64_peak_tflops(dev_index: int, sm_max_mhz):
-    """FP64 peak of this GPU from its measured DFMA issue rate (fe_fp64_rate: operations per
-    SM clock per SM), its SM count and its maximum SM clock (nvidia-smi; the probe's own clock
-    when that is unknown): 2 flops x rate x SMs x clock."""
+def fp64_probe(dev_index: int):
+    """The FP64 issue rates of this GPU (fe_fp64_rate: operations per SM clock per SM) and its
+    SM count; run before the timed regions."""
     import torch
     from paper_2109_01158_gb300 import fem
     rate, ghz = fem.fp64_rate(dev_index, fem.FE_RATE_DFMA)
     add_rate, _ = fem.fp64_rate(dev_index, fem.FE_RATE_DADD)
     sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
-    mhz = sm_max_mhz if sm_max_mhz else ghz * 1e3
-    peak = 2.0 * rate * sms * mhz * 1e6 / 1e12
-    return peak, {"dfma_per_clk_per_sm": rate, "dadd_per_clk_per_sm": add_rate, "sms": sms,
-                  "sm_mhz": mhz, "probe_sm_ghz": ghz,
-                  "formula": "2 flops x measured DFMA/clk/SM x SMs x max SM clock"}
+    return {"dfma_per_clk_per_sm": rate, "dadd_per_clk_per_sm": add_rate, "sms": sms, "probe_sm_ghz": ghz}
+
+
+def fp64_peak_tflops(probe: dict, sm_max_mhz):
+    """FP64 peak from the measured DFMA rate, the SM count and the maximum SM clock
+    (nvidia-smi; the probe's own clock when that is unknown): 2 flops x rate x SMs x clock."""
+    mhz = sm_max_mhz if sm_max_mhz else probe["probe_sm_ghz"] * 1e3
+    peak = 2.0 * probe["dfma_per_clk_per_sm"] * probe["sms"] * mhz * 1e6 / 1e12
+    return peak, dict(probe, sm_mhz=mhz, formula="2 flops x measured DFMA/clk/SM x SMs x max SM clock")
 
 
 # What one step runs in each precision (for the variants' records).
@@ -398,6 +401,7 @@ def run_ours(args, rank, world, local):
             gm.profile(False)
         return ms, gm.launch_count() - l0, prof
 
+    probe = fp64_probe(local) if (args.precision == "f64" and w.dim == 3 and w.model == mg.MODEL_NEOHOOKE) else None
     steps(args.warmup)
     assert gm.sync_status() == fem.FE_OK, "domain error in the benchmark workload"
     uuid = None
@@ -424,7 +428,7 @@ def run_ours(args, rank, world, local):
     hbm_achieved = elem_bytes / (elem_ms / 1e3) / 1e9
     if prec == "f64" and w.dim == 3 and w.model == mg.MODEL_NEOHOOKE:
         achieved = F64_FLOPS_PER_TET * w.ne / (elem_ms / 1e3) / 1e12
-        f64_peak, f64_probe = fp64_peak_tflops(local, clocks.get("sm_max_mhz"))
+        f64_peak, f64_probe = fp64_peak_tflops(probe, clocks.get("sm_max_mhz"))
         roof = {"bound": "alu", "achieved": achieved, "peak": f64_peak, "unit": "TFLOP/s",
                 "frac": achieved / f64_peak, "traffic": None,
                 "peak_kind": "derived FP64 from a measured DFMA rate", "fp64_probe": f64_probe,
@@ -453,7 +457,7 @@ def run_ours(args, rank, world, local):
     gh = [torch.empty(w.ndof, dtype=torch.float64).pin_memory() for _ in range(2)]
     Jh = torch.empty((2, 1), dtype=torch.float64).pin_memory()
     vh_np, gh_np, Jh_np = vh.numpy(), [t.numpy() for t in gh], Jh.numpy()
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = max(10, args.steps)
 
     def host_steps(n, pipelined):
         for k in range(n):
