@@ -34,10 +34,8 @@ namespace {
 template <int DIM, int D>
 struct Pipe32 {
   static constexpr int DP = D == 3 ? 4 : D;   // float pairs per node record (padded)
-  static constexpr int NXY = D >= 2 ? 2 : 0;  // components of r kept as float2
-  // nodal values: DP float pairs per node; r: components 0 and 1 as float2 per slot (D >= 2),
-  // the last (D = 1 or 3) as float
-  using S = TilePipe<DIM, D, 4, DP * 8, D * 4>;
+  // nodal values: DP float pairs per node; r: one float column per component
+  using S = TilePipe<DIM, D, 4, DP * 8, 4>;
 };
 
 template <int D>
@@ -151,7 +149,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
     unsigned* counter, double* J, int* status) {
   using P = Pipe32<DIM, D>;
   using S = typename P::S;
-  constexpr int K = DIM + 1, NXY = P::NXY, DP = P::DP;
+  constexpr int K = DIM + 1, DP = P::DP;
   constexpr int NE = kTileElems, NEW = NE / 32;              // element threads and warps
   static_assert(NEW <= 32, "the producer adds one energy pair per element warp in one warp");
   constexpr int NN = 32 * kTileNodeWarps;                    // node threads
@@ -168,10 +166,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
   auto E = [&](int i) { return smem + S::kE + (i & 1) * S::kEBytes; };
   auto R = [&](int i) { return reinterpret_cast<int4*>(smem + S::kR + (i % 3) * S::kRBytes); };
   auto U = [&](int i) { return reinterpret_cast<float2*>(smem + S::kU + (i & 1) * S::kUBytes); };
-  auto RXY = [&](int i) { return reinterpret_cast<float2*>(smem + S::kRs + (i & 1) * S::kRsBytes); };
-  auto RZ = [&](int i) {
-    return reinterpret_cast<float*>(smem + S::kRs + (i & 1) * S::kRsBytes + NXY * 4 * S::kSlots);
-  };
+  // component j of the local forces of tile i, by local slot
+  auto RC = [&](int i, int j) { return reinterpret_cast<float*>(smem + S::kRs + (i & 1) * S::kRsBytes + j * S::kColBytes); };
   auto EW = [&](int i) { return reinterpret_cast<float*>(smem + S::kEw + (i & 1) * S::kEwBytes); };
   auto BDB = [&](int i) { return reinterpret_cast<double*>(smem + S::kBd + (i % 3) * S::kBdBytes); };
   auto BDM = [&](int i) { return reinterpret_cast<int*>(smem + S::kBd + (i % 3) * S::kBdBytes + S::kBdMaskOff); };
@@ -336,8 +332,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
       if (!wait(&bars.rs_full[i & 1], i >> 1)) return false;
       if (GRAD) {
         const int4* Rr = R(i);
-        const float2* rxy = RXY(i);
-        const float* rz = RZ(i);
+        const float* rc0 = RC(i, 0);
         const double* bd = BDB(i);
         const int* bm = BDM(i);
         const int nt = info[i % 3].w;
@@ -345,19 +340,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
           const int k = w / D, j = w - k * D;
           const int4 rec = Rr[k];
           const int beg = rec.z & 0xffff, cnt = (int)((unsigned)rec.z >> 16);
-          const float* col = (NXY && j < NXY) ? reinterpret_cast<const float*>(rxy) + j : rz;
-          const int str = (NXY && j < NXY) ? 2 : 1;
-          // walk the node's slots from position p (a function of k and cnt: consecutive nodes
-          // then start on different shared-memory banks), wrapping around; the order is
-          // fixed by the mesh alone
+          // the node's slots in order (each node's slots are consecutive in its column)
+          const float* col = rc0 + j * (S::kColBytes / 4) + beg;
           float sum = 0.f;
           if (cnt > 0) {
-            const int p = (k & 7) < cnt ? (k & 7) : 0;
-            sum = col[(beg + p) * str];
+            sum = col[0];
 #pragma unroll 4
-            for (int q = beg + p + 1; q < beg + cnt; ++q) sum = __fadd_rn(sum, col[q * str]);
-#pragma unroll 4
-            for (int q = beg; q < beg + p; ++q) sum = __fadd_rn(sum, col[q * str]);
+            for (int q = 1; q < cnt; ++q) sum = __fadd_rn(sum, col[q]);
           }
           const int dst = (rec.w >> 1) - 1;
           const int64_t n = rec.x;
@@ -383,8 +372,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
       const int4 in = info[i % 3];
       const unsigned char* St = E(i);
       const float2* us = U(i);
-      float2* rxy = RXY(i);
-      float* rz = RZ(i);
+      float* rc0 = RC(i, 0);
       float ew = 0.f;
       const int e = in.x + tid;
       if (e < in.y) {
@@ -419,11 +407,11 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
               r[j] = s;
               r0[j] = (l == 1) ? -s : __fsub_rn(r0[j], s);
             }
-            if constexpr (NXY) rxy[sl[l]] = make_float2(r[0], r[1]);
-            if constexpr (D != 2) rz[sl[l]] = r[D - 1];
+#pragma unroll
+            for (int j = 0; j < D; ++j) rc0[j * (S::kColBytes / 4) + sl[l]] = r[j];
           }
-          if constexpr (NXY) rxy[sl[0]] = make_float2(r0[0], r0[1]);
-          if constexpr (D != 2) rz[sl[0]] = r0[D - 1];
+#pragma unroll
+          for (int j = 0; j < D; ++j) rc0[j * (S::kColBytes / 4) + sl[0]] = r0[j];
         }
       }
       if (ENERGY) {

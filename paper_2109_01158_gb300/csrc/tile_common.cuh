@@ -36,7 +36,9 @@ __device__ __forceinline__ double f2d_bits(float f) {
 //          copied range starts 16-byte aligned;
 //   R[3]   node records (int4 per tile node);
 //   U[2]   the tile's nodal values, NU bytes per node;
-//   Rs[2]  the tile's local forces, RB bytes per slot;
+//   Rs[2]  the tile's local forces: D columns (one per component) of RB bytes per slot,
+//          each column 16 bytes longer than the slots (so the columns of one slot fall in
+//          different shared-memory banks);
 //   Ew[2]  the tile's element energies |T| W (float per element);
 //   Bd[3]  the tile nodes' load b_i (D doubles per node) and Dirichlet mask (an int per node,
 //          bit j for dof j), copied by the node warps with the nodal values, so that the
@@ -53,7 +55,8 @@ struct TilePipe {
   static constexpr int kEBytes = kElemOff + kTileElems * 16;
   static constexpr int kRBytes = kNodes * 16;
   static constexpr int kUBytes = (kNodes * NU + 15) / 16 * 16;
-  static constexpr int kRsBytes = (kSlots * RB + 15) / 16 * 16;
+  static constexpr int kColBytes = (kSlots * RB + 15) / 16 * 16 + 16;   // one component's column
+  static constexpr int kRsBytes = D * kColBytes;
   static constexpr int kEwBytes = kTileElems * 4;
   static constexpr int kBdMaskOff = kNodes * D * 8;                 // ints after the doubles
   static constexpr int kBdBytes = (kBdMaskOff + kNodes * 4 + 15) / 16 * 16;
