@@ -443,9 +443,12 @@ def run_ours(args, rank, world, local):
         sc = w.ne / trec["elements"]
         roof["traffic_read"] = trec["dram_bytes_read"] * sc
         roof["traffic_write"] = trec["dram_bytes_write"] * sc
-        roof["traffic_note"] = ("reads are the algorithmic element and node bytes (no re-reads); writes are "
-                                "the local forces (dim+1)*d per element, read back by the patch gather")
-    roof["kernel"] = "k_elem_%s (energy+gradient)" % prec
+        roof["traffic_note"] = (
+            "scaled by the element count from an ncu capture of %s on %s; reads are the algorithmic element "
+            "and node bytes (no re-reads); writes are the local forces (dim+1)*d per element (FP64 and "
+            "double-float; the FP32 tiles keep them on chip), undercounted by the lines still in L2 when the "
+            "captured launch ended" % (trec["kernel"], trec["workload"]))
+    roof["kernel"] = {"f64": "k_elem_f64", "df64": "k_elem_df", "f32": "k_tile_f32"}[prec] + " (energy+gradient)"
     roof["kernel_ms"] = elem_ms
     roof["algorithmic_bytes_per_launch"] = elem_bytes
     stages = {k: {"ms_per_launch": t / n if n else 0.0, "launches": n} for k, (t, n) in prof.items() if n}

@@ -434,7 +434,7 @@ fe_status fe_server_reset_stats(fe_server* s);
 /* ---- Device characterisation -------------------------------------------------------
  * Not in the paper: the issue rate of the FP64 unit, the roof of the FP64 kernels (bound by
  * FP64 arithmetic).  Runs eight independent chains of one operation per thread, four
- * 256-thread blocks per SM, 2^14 iterations (two launches of a few milliseconds), and
+ * 256-thread blocks per SM, 2^12 iterations (two launches of about 10 ms), and
  * returns operations per SM clock per SM (*per_clock_per_sm, from the SM cycle counter of
  * every block) and the SM clock the launch ran at in GHz (*sm_ghz, from the cycles and the
  * event time; may be NULL).  op: FE_RATE_DFMA, FE_RATE_DADD or FE_RATE_DMUL; anything else

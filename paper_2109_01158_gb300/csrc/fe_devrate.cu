@@ -58,7 +58,7 @@ fe_status fe_fp64_rate(int device, int op, double* per_clock_per_sm, double* sm_
   if (st) return st;
   const int sms = sm_count(device);
   const int blocks = sms * kRateBlocksPerSM;
-  const int iters = 1 << 14;
+  const int iters = 1 << 12;
   double* sink = nullptr;
   long long* cyc = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
