@@ -14,11 +14,14 @@ __device__ __forceinline__ df ld_df(const float2* __restrict__ p, int64_t i) {
 }
 
 // Loads of data that other blocks of the same launch write (the persistent batched kernel):
-// through L2 only (ld.global.cg), never the read-only path, which is not kept coherent with
-// writes made during the launch.
+// ordinary cached loads (ld.global.ca), never the read-only path (ld.global.nc), which is
+// not kept coherent with writes made during the launch.  The caller has synchronised with
+// the writers first (an acquire at GPU scope, then a block barrier), after which ordinary
+// loads see the written values, and neighbouring elements still share the L1 lines of
+// their nodes.
 template <bool COH, class T>
 __device__ __forceinline__ T ld_ro(const T* p) {
-  if constexpr (COH) return __ldcg(p);
+  if constexpr (COH) return __ldca(p);
   else return __ldg(p);
 }
 

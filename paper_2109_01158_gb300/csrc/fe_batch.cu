@@ -265,7 +265,7 @@ __device__ __forceinline__ void gather_nodes(const BItem& it, int64_t t) {
   for (int q = 0; q < kNPT; ++q)
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      const float2 a = n[q] > 0 ? __ldcg(it.r + (int64_t)q0[q] * D + j) : make_float2(0.f, 0.f);
+      const float2 a = n[q] > 0 ? __ldca(it.r + (int64_t)q0[q] * D + j) : make_float2(0.f, 0.f);
       s[q][j] = {a.x, a.y};
     }
   for (int m = 1; m < len; ++m) {
@@ -273,7 +273,7 @@ __device__ __forceinline__ void gather_nodes(const BItem& it, int64_t t) {
 #pragma unroll
     for (int q = 0; q < kNPT; ++q)
 #pragma unroll
-      for (int j = 0; j < D; ++j) a[q][j] = m < n[q] ? __ldcg(it.r + (int64_t)(q0[q] + m) * D + j) : make_float2(0.f, 0.f);
+      for (int j = 0; j < D; ++j) a[q][j] = m < n[q] ? __ldca(it.r + (int64_t)(q0[q] + m) * D + j) : make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < kNPT; ++q)
       if (m < n[q])
