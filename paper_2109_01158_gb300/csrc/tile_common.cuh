@@ -39,7 +39,7 @@ __device__ __forceinline__ double f2d_bits(float f) {
 //   Rs[2]  the tile's local forces: D columns (one per component) of RB bytes per slot,
 //          each column 16 bytes longer than the slots (so the columns of one slot fall in
 //          different shared-memory banks);
-//   Ew[2]  the tile's element energies |T| W (float per element);
+//   Ew[2]  the tile's energy |T| W per element warp (a float pair each);
 //   Bd[3]  the tile nodes' load b_i (D doubles per node) and Dirichlet mask (an int per node,
 //          bit j for dof j), copied by the node warps with the nodal values, so that the
 //          patch sums read them from shared memory; three buffers like the records, as they
@@ -57,7 +57,7 @@ struct TilePipe {
   static constexpr int kUBytes = (kNodes * NU + 15) / 16 * 16;
   static constexpr int kColBytes = (kSlots * RB + 15) / 16 * 16 + 16;   // one component's column
   static constexpr int kRsBytes = D * kColBytes;
-  static constexpr int kEwBytes = kTileElems * 4;
+  static constexpr int kEwBytes = (kTileElems / 32 * 8 + 15) / 16 * 16;
   static constexpr int kBdMaskOff = kNodes * D * 8;                 // ints after the doubles
   static constexpr int kBdBytes = (kBdMaskOff + kNodes * 4 + 15) / 16 * 16;
   static constexpr int kE = 0;
@@ -69,7 +69,6 @@ struct TilePipe {
   static constexpr int kBytes = kBd + 3 * kBdBytes;
   static_assert(kBytes <= 227 * 1024, "the pipeline must fit in the shared memory of one block");
   static_assert(kEBytes % 16 == 0 && kRBytes % 16 == 0, "alignment");
-  static_assert(kTileElems % 128 == 0, "the energy sum reads the tile in rows of 128");
   static_assert(2 * kRsBytes >= 2 * kTileThreads * 8, "the final reduction reuses Rs");
 };
 
@@ -118,32 +117,6 @@ __device__ __forceinline__ double pipe_warp_sum(double x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
   return x;
-}
-
-// One warp: the sum of the n floats x[0..n) (n a multiple of 128) in a fixed order: per lane
-// four interleaved float-pair accumulators (TwoSum per addition: each pair holds its exact sum
-// to within a few units of 2^-48 of the terms' magnitudes), combined and converted to FP64,
-// then added over the lanes; valid in lane 0.  An infinite term makes the sum +Inf (TwoSum on
-// Inf would give NaN).
-__device__ __forceinline__ double pipe_warp_sum_floats(const float* x, int n) {
-  const int lane = threadIdx.x & 31;
-  df s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  bool inf = false;
-  for (int k = lane; k < n; k += 128) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const float y = x[k + 32 * a];
-      inf |= isinf(y);
-      const df t = two_sum(s[a].hi, isinf(y) ? 0.f : y);
-      s[a] = fast_two_sum(t.hi, __fadd_rn(t.lo, s[a].lo));
-    }
-  }
-  double d = 0.0;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) d += f2d_bits(s[a].hi) + f2d_bits(s[a].lo);
-  d = pipe_warp_sum(d);
-  inf = __any_sync(0xffffffffu, inf);
-  return inf ? CUDART_INF : d;
 }
 
 __device__ __forceinline__ void pipe_warp_pair_sum(const double* r0, const double* r1, int n, double* s0,
