@@ -381,6 +381,14 @@ fe_status fe_batch_energy_gradient(fe_batch* b, const fe_batch_item* items, int 
 fe_status fe_batch_sync_status(fe_batch* b);
 /* Kernel launches enqueued so far (one per non-empty fe_batch_energy_gradient call). */
 fe_status fe_batch_launch_count(const fe_batch* b, int64_t* count);
+/* The work list the batched kernel follows (host only, for inspection and tests): for n
+ * requests with prep_tiles[k] node tiles and elem_tiles[k] element tiles (each >= 1) on a GPU
+ * of resident_blocks resident blocks, the 3n ranges (request_out[q], step_out[q]: 0 prep,
+ * 1 element, 2 gather) in list order, each starting at item start_out[q] and holding that
+ * step's tiles; *total_out = the number of items.  Requests are grouped into waves of at
+ * least 4 * resident_blocks tiles, pipelined as P(s), E(s-1), G(s-2). */
+fe_status fe_batch_plan(int n, const int64_t* prep_tiles, const int64_t* elem_tiles, int64_t resident_blocks,
+                        int64_t* start_out, int32_t* request_out, int32_t* step_out, int64_t* total_out);
 
 /* ---- Continuous-batching server over resident meshes -------------------------------
  * Not in the paper: a native request loop around the persistent batched kernel.  Callers

@@ -410,6 +410,38 @@ int persistent_blocks(int device) {
   return b;
 }
 
+// The work list: waves of consecutive requests with at least four tiles per resident block in
+// all, pipelined as P(s), E(s-1), G(s-2) at stage s (P, E, G: the prep, element and gather
+// ranges of the wave's requests, in request order); out[3n] receives the ranges in list
+// order.  Returns the number of items.
+int64_t plan_work(int n, const int64_t* nnt, const int64_t* net, int64_t resident, BRange* out) {
+  std::vector<int> wb{0};
+  int64_t acc = 0;
+  for (int k = 0; k < n; ++k) {
+    acc += 2 * nnt[k] + net[k];
+    if (acc >= 4 * resident || k == n - 1) {
+      wb.push_back(k + 1);
+      acc = 0;
+    }
+  }
+  const int nw = (int)wb.size() - 1;
+  int nr = 0;
+  int64_t w = 0;
+  auto emit = [&](int wave, int step) {
+    if (wave < 0 || wave >= nw) return;
+    for (int k = wb[wave]; k < wb[wave + 1]; ++k) {
+      out[nr++] = BRange{(long long)w, k, step};
+      w += step == 1 ? net[k] : nnt[k];
+    }
+  };
+  for (int st = 0; st < nw + 2; ++st) {
+    emit(st, 0);
+    emit(st - 1, 1);
+    emit(st - 2, 2);
+  }
+  return w;
+}
+
 }  // namespace
 
 size_t batch_stage_bytes(int n) { return stage_ranges_off(n) + sizeof(BRange) * 3 * (size_t)(n > 0 ? n : 1); }
@@ -472,32 +504,13 @@ fe_status batch_enqueue(cudaStream_t s, int device, const fe_batch_item* items, 
     hcnt[k] = BCount{0, 0, 0, 0};
     tab = m->log_tab;
   }
-  // waves: consecutive requests with at least four tiles per resident block in all
-  std::vector<int> wb{0};
-  int64_t acc = 0;
+  std::vector<int64_t> nnt(n), net(n);
   for (int k = 0; k < n; ++k) {
-    acc += 2 * host[k].nntiles + host[k].netiles;
-    if (acc >= 4 * resident || k == n - 1) {
-      wb.push_back(k + 1);
-      acc = 0;
-    }
+    nnt[k] = host[k].nntiles;
+    net[k] = host[k].netiles;
   }
-  // the work list, pipelined over the waves: P(s), E(s-1), G(s-2) at stage s
-  const int nw = (int)wb.size() - 1;
-  int nr = 0;
-  int64_t w = 0;
-  auto emit = [&](int wave, int step) {
-    if (wave < 0 || wave >= nw) return;
-    for (int k = wb[wave]; k < wb[wave + 1]; ++k) {
-      hr[nr++] = BRange{(long long)w, k, step};
-      w += step == 1 ? host[k].netiles : host[k].nntiles;
-    }
-  };
-  for (int st = 0; st < nw + 2; ++st) {
-    emit(st, 0);
-    emit(st - 1, 1);
-    emit(st - 2, 2);
-  }
+  const int64_t w = plan_work(n, nnt.data(), net.data(), resident, hr);
+  const int nr = 3 * n;
   if (w >= (1ll << 40)) return set_error(FE_EINVAL, "batch too large");
   head->next = 0;
   head->total = w;
@@ -654,6 +667,23 @@ fe_status fe_batch_sync_status(fe_batch* b) {
   if (st) return st;
   if (hs & kStatusTimeout) return set_error(FE_ETIMEOUT, "a bounded wait of the batched kernel gave up");
   if (hs & kStatusDomain) return set_error(FE_EDOMAIN, "an element has det F <= 0");
+  return FE_OK;
+}
+
+fe_status fe_batch_plan(int n, const int64_t* prep_tiles, const int64_t* elem_tiles, int64_t resident_blocks,
+                        int64_t* start_out, int32_t* request_out, int32_t* step_out, int64_t* total_out) {
+  if (n < 0 || (n > 0 && (!prep_tiles || !elem_tiles || !start_out || !request_out || !step_out)) || !total_out ||
+      resident_blocks < 1)
+    return set_error(FE_EINVAL, "bad arguments");
+  for (int k = 0; k < n; ++k)
+    if (prep_tiles[k] < 1 || elem_tiles[k] < 1) return set_error(FE_EINVAL, "every request has at least one tile per step");
+  std::vector<BRange> r((size_t)3 * n);
+  *total_out = n > 0 ? plan_work(n, prep_tiles, elem_tiles, resident_blocks, r.data()) : 0;
+  for (int q = 0; q < 3 * n; ++q) {
+    start_out[q] = r[q].start;
+    request_out[q] = r[q].k;
+    step_out[q] = r[q].step;
+  }
   return FE_OK;
 }
 

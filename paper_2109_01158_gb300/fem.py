@@ -92,6 +92,7 @@ _SIGNATURES = {
     "fe_batch_launch_count": [_vp, _vp],
     "fe_batch_set_wait_limit": [_vp, _i64],
     "fe_fp64_rate": [_int, _int, _vp, _vp],
+    "fe_batch_plan": [_int, _vp, _vp, _i64, _vp, _vp, _vp, _vp],
     "fe_server_create": [_vp, _int, ctypes.c_size_t, _int],
     "fe_server_destroy": [_vp],
     "fe_server_submit": [_vp, _vp, _vp, _vp, _vp, _dbl, _vp],
@@ -258,6 +259,20 @@ fe_batch_energy_gradient = _checked("fe_batch_energy_gradient")
 fe_batch_launch_count = _checked("fe_batch_launch_count")
 fe_batch_set_wait_limit = _checked("fe_batch_set_wait_limit")
 fe_fp64_rate = _checked("fe_fp64_rate")
+fe_batch_plan = _checked("fe_batch_plan")
+
+
+def batch_plan(prep_tiles, elem_tiles, resident_blocks):
+    """The batched kernel's work list: a list of (start, request, step) and the item count."""
+    n = len(prep_tiles)
+    pt = (ctypes.c_int64 * max(n, 1))(*prep_tiles)
+    et = (ctypes.c_int64 * max(n, 1))(*elem_tiles)
+    st = (ctypes.c_int64 * max(3 * n, 1))()
+    rq = (ctypes.c_int32 * max(3 * n, 1))()
+    sp = (ctypes.c_int32 * max(3 * n, 1))()
+    tot = ctypes.c_int64()
+    fe_batch_plan(n, pt, et, int(resident_blocks), st, rq, sp, ctypes.byref(tot))
+    return [(st[q], rq[q], sp[q]) for q in range(3 * n)], tot.value
 FE_RATE_DFMA, FE_RATE_DADD, FE_RATE_DMUL = range(3)
 
 
