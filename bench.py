@@ -87,7 +87,8 @@ FLUSH_BYTES = 256 << 20     # a write of this size evicts L2
 KERNEL_SOURCES = {
     "f64": ["fe_eval_f64.cu", "fe_internal.cuh", "phi_f64.cuh", "phi_table_f64.h"],
     "df64": ["fe_eval_df64.cu", "elem_df.cuh", "df64.cuh", "fe_internal.cuh"],
-    "f32": ["fe_eval_f32.cu", "elem_f32.cuh", "tile_common.cuh", "fe_tiles.cu", "df64.cuh", "fe_internal.cuh"],
+    "f32": ["fe_eval_f32.cu", "elem_f32.cuh", "tile_common.cuh", "fe_tiles.cu", "df64.cuh", "fe_internal.cuh",
+            "async_copy.cuh"],
 }
 
 
