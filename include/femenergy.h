@@ -251,6 +251,18 @@ fe_status fe_lbfgs_direction(fe_lbfgs* lb, const double* g_dev, double* d_dev, d
  * receives s.y, g_new.d and max |g_new|.  The same pairs and direction as the two calls. */
 fe_status fe_lbfgs_step(fe_lbfgs* lb, const double* v_new_dev, const double* v_dev, const double* g_new_dev,
                         const double* g_dev, double* d_dev, double* out3);
+/* Checkpoint (not in the paper; its Benchmark 4 only warm-starts from the previous minimum):
+ * copy the pairs in use, oldest first, to host memory -- s_host and y_host receive pair i at
+ * [i*n, (i+1)*n), sy_host and yy_host the products s_i.y_j and y_i.y_j at [i*count + j] --
+ * and *count the number of pairs.  Every buffer must hold m pairs (m*n, m*m doubles); the
+ * buffers may be NULL when no pair is held.  Waits for the memory's stream. */
+fe_status fe_lbfgs_save(const fe_lbfgs* lb, double* s_host, double* y_host, double* sy_host, double* yy_host,
+                        int* count);
+/* Resume: replace the memory of lb (created with the same n and an m >= count) by count saved
+ * pairs and their products, as written by fe_lbfgs_save.  The directions and updates that
+ * follow are bitwise those the saved memory would have given.  FE_EINVAL for count > m. */
+fe_status fe_lbfgs_restore(fe_lbfgs* lb, const double* s_host, const double* y_host, const double* sy_host,
+                           const double* yy_host, int count);
 
 /* Central-difference gradient over nodal patches (Sec. 6.1, eqs. CD, CDS, jgradpm,
  * sumpatch): for dof n of node i, component j,

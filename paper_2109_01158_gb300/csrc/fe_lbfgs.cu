@@ -21,6 +21,7 @@
 // the slots in use; the host keeps the pair when s.y > 0 (the spare joins the ring and the
 // oldest slot becomes the spare when the memory is full).
 #include <new>
+#include <vector>
 
 #include "fe_internal.cuh"
 #include "reduce.cuh"
@@ -415,6 +416,80 @@ fe_status fe_lbfgs_direction(fe_lbfgs* L, const double* g, double* d, double* gd
   fe_status st = cuda_check(cudaGetLastError(), "lbfgs direction launch");
   if (st || (st = lb_read_scalars(L))) return st;
   *gd = L->host[1];
+  return FE_OK;
+}
+
+}  // extern "C"
+
+// ---- checkpoint / resume ----------------------------------------------------------------------
+// The memory of a minimisation can be saved to the host and restored into another memory of
+// the same size: the pairs in use (oldest first) and their products s_i.y_j and y_i.y_j are
+// copied as they are, so the directions computed after a restore are bitwise those the saved
+// memory would have given (the kernels read pairs and products in pair order, whatever slots
+// hold them).
+
+extern "C" {
+
+fe_status fe_lbfgs_save(const fe_lbfgs* L, double* s_host, double* y_host, double* sy_host, double* yy_host,
+                        int* count) {
+  if (!L || !count || (L->count > 0 && (!s_host || !y_host || !sy_host || !yy_host)))
+    return set_error(FE_EINVAL, "null argument");
+  LbDeviceGuard guard(L->device);
+  fe_status st = cuda_check(cudaStreamSynchronize(L->stream), "lbfgs sync");
+  if (st) return st;
+  const int k = L->count, ld = L->m + 1;
+  const size_t n = (size_t)L->n;
+  std::vector<double> sy((size_t)ld * ld), yy((size_t)ld * ld);
+  if (k > 0 && ((st = cuda_check(cudaMemcpy(sy.data(), L->SY, sizeof(double) * sy.size(), cudaMemcpyDeviceToHost),
+                                 "lbfgs save")) ||
+                (st = cuda_check(cudaMemcpy(yy.data(), L->YY, sizeof(double) * yy.size(), cudaMemcpyDeviceToHost),
+                                 "lbfgs save"))))
+    return st;
+  for (int i = 0; i < k; ++i) {
+    const int a = L->ring[i];
+    if ((st = cuda_check(cudaMemcpy(s_host + i * n, L->S + (size_t)a * n, sizeof(double) * n, cudaMemcpyDeviceToHost),
+                         "lbfgs save")) ||
+        (st = cuda_check(cudaMemcpy(y_host + i * n, L->Y + (size_t)a * n, sizeof(double) * n, cudaMemcpyDeviceToHost),
+                         "lbfgs save")))
+      return st;
+    for (int j = 0; j < k; ++j) {
+      sy_host[i * k + j] = sy[(size_t)a * ld + L->ring[j]];
+      yy_host[i * k + j] = yy[(size_t)a * ld + L->ring[j]];
+    }
+  }
+  *count = k;
+  return FE_OK;
+}
+
+fe_status fe_lbfgs_restore(fe_lbfgs* L, const double* s_host, const double* y_host, const double* sy_host,
+                           const double* yy_host, int count) {
+  if (!L || count < 0 || count > L->m || (count > 0 && (!s_host || !y_host || !sy_host || !yy_host)))
+    return set_error(FE_EINVAL, "bad arguments");
+  LbDeviceGuard guard(L->device);
+  fe_status st = cuda_check(cudaStreamSynchronize(L->stream), "lbfgs sync");
+  if (st) return st;
+  const int ld = L->m + 1;
+  const size_t n = (size_t)L->n;
+  std::vector<double> sy((size_t)ld * ld, 0.0), yy((size_t)ld * ld, 0.0);
+  for (int i = 0; i < count; ++i) {
+    if ((st = cuda_check(cudaMemcpy(L->S + i * n, s_host + i * n, sizeof(double) * n, cudaMemcpyHostToDevice),
+                         "lbfgs restore")) ||
+        (st = cuda_check(cudaMemcpy(L->Y + i * n, y_host + i * n, sizeof(double) * n, cudaMemcpyHostToDevice),
+                         "lbfgs restore")))
+      return st;
+    for (int j = 0; j < count; ++j) {
+      sy[(size_t)i * ld + j] = sy_host[i * count + j];
+      yy[(size_t)i * ld + j] = yy_host[i * count + j];
+    }
+  }
+  if ((st = cuda_check(cudaMemcpy(L->SY, sy.data(), sizeof(double) * sy.size(), cudaMemcpyHostToDevice),
+                       "lbfgs restore")) ||
+      (st = cuda_check(cudaMemcpy(L->YY, yy.data(), sizeof(double) * yy.size(), cudaMemcpyHostToDevice),
+                       "lbfgs restore")))
+    return st;
+  for (int i = 0; i < count; ++i) L->ring[i] = i;
+  L->count = count;
+  L->spare = count;
   return FE_OK;
 }
 

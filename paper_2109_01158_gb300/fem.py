@@ -93,6 +93,8 @@ _SIGNATURES = {
     "fe_batch_set_wait_limit": [_vp, _i64],
     "fe_fp64_rate": [_int, _int, _vp, _vp],
     "fe_batch_plan": [_int, _vp, _vp, _i64, _vp, _vp, _vp, _vp],
+    "fe_lbfgs_save": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "fe_lbfgs_restore": [_vp, _vp, _vp, _vp, _vp, _int],
     "fe_server_create": [_vp, _int, ctypes.c_size_t, _int],
     "fe_server_destroy": [_vp],
     "fe_server_submit": [_vp, _vp, _vp, _vp, _vp, _dbl, _vp],
@@ -231,6 +233,26 @@ class LbfgsMemory:
         fe_lbfgs_step(self.handle, _ptr(v_new), _ptr(v), _ptr(g_new), _ptr(g), _ptr(d), o)
         return d, o[0], o[1], o[2]
 
+    def save(self):
+        """(S, Y, SY, YY): the pairs in use, oldest first, as host arrays (k x n each) and their
+        products s_i.y_j, y_i.y_j (k x k), for restore()."""
+        S = np.empty((self.m, self.n)); Y = np.empty((self.m, self.n))
+        SY = np.empty((self.m, self.m)); YY = np.empty((self.m, self.m))
+        k = ctypes.c_int(0)
+        fe_lbfgs_save(self.handle, _ptr(S), _ptr(Y), _ptr(SY), _ptr(YY), ctypes.byref(k))
+        k = k.value
+        return (S[:k].copy(), Y[:k].copy(), SY.ravel()[:k * k].reshape(k, k).copy(),
+                YY.ravel()[:k * k].reshape(k, k).copy())
+
+    def restore(self, state):
+        """Replace the memory by a state from save() (same n, at most m pairs)."""
+        S, Y, SY, YY = (np.ascontiguousarray(a, dtype=np.float64) for a in state)
+        k = S.shape[0]
+        if Y.shape[0] != k or S.shape[1:] != (self.n,) or Y.shape[1:] != (self.n,) or SY.shape != (k, k) \
+                or YY.shape != (k, k):
+            raise ValueError("state does not match this memory")
+        fe_lbfgs_restore(self.handle, _ptr(S), _ptr(Y), _ptr(SY), _ptr(YY), int(k))
+
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             fe_lbfgs_destroy(self.handle)
@@ -260,6 +282,8 @@ fe_batch_launch_count = _checked("fe_batch_launch_count")
 fe_batch_set_wait_limit = _checked("fe_batch_set_wait_limit")
 fe_fp64_rate = _checked("fe_fp64_rate")
 fe_batch_plan = _checked("fe_batch_plan")
+fe_lbfgs_save = _checked("fe_lbfgs_save")
+fe_lbfgs_restore = _checked("fe_lbfgs_restore")
 
 
 def batch_plan(prep_tiles, elem_tiles, resident_blocks):

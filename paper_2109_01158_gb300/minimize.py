@@ -36,6 +36,7 @@ class LBFGSResult:
     converged: bool
     seconds: float
     history: list = field(default_factory=list)   # (J, ||g||_inf) per iteration
+    checkpoint: dict | None = None                # LbfgsJob.checkpoint() at the stop, when asked for
 
 
 def _gnorm(g):
@@ -191,16 +192,51 @@ class LbfgsJob:
 
     def __init__(self, v0, *, m: int = 10, gtol: float = 1e-6, relative: bool = False, max_iter: int = 20000,
                  c1: float = 1e-4, sigma: float = 0.9, eps_f: float = 1e-10, max_evals_per_iter: int = 60,
-                 device_memory: bool = False):
+                 device_memory: bool = False, resume: dict | None = None, keep_checkpoint: bool = False):
         self.v0 = v0
         self.device_memory = device_memory and v0.is_cuda
         self.m, self.gtol, self.relative, self.max_iter = m, gtol, relative, max_iter
         self.c1, self.sigma, self.eps_f, self.max_evals = c1, sigma, eps_f, max_evals_per_iter
+        self.keep_checkpoint = keep_checkpoint
+        self.final_checkpoint = None
         self.st = None
         self.done = False
         self.t0 = time.perf_counter()
         self.seconds = 0.0
         self._trial = v0
+        if resume is not None:
+            self._resume(resume)
+
+    # ---- checkpoint / resume (device memory only) ---------------------------------------
+    def checkpoint(self) -> dict:
+        """The state between two iterations, on the host: iterate, J, g, the L-BFGS pairs and
+        their products, counters and history.  A job built with resume=<this> continues with
+        bitwise the iterates this one would have produced.  Only between iterations (after
+        construction from a resume, or when the job stopped at max_iter with keep_checkpoint)."""
+        if not self.device_memory:
+            raise ValueError("checkpoints need the device L-BFGS memory (device_memory=True)")
+        st = self.st
+        if st is None:
+            raise ValueError("no iteration yet")
+        return {"v": st.v.detach().cpu().numpy().copy(), "J": float(st.J), "g": st.g.detach().cpu().numpy().copy(),
+                "gn": float(self.gn), "tol": float(self.tol), "iters": int(st.iters), "evals": int(st.evals),
+                "history": list(st.history), "m": int(self.m), "memory": st.mem.save()}
+
+    def _resume(self, ck: dict):
+        if not self.device_memory:
+            raise ValueError("resuming needs the device L-BFGS memory (device_memory=True, a CUDA v0)")
+        if int(ck["m"]) != self.m or ck["v"].shape != tuple(self.v0.shape):
+            raise ValueError("checkpoint does not match this problem (m or size)")
+        dev = self.v0.device
+        v = torch.from_numpy(ck["v"]).to(dev)
+        g = torch.from_numpy(ck["g"]).to(dev)
+        self.st = _DeviceState(v, float(ck["J"]), g, self.m)
+        self.st.mem.restore(ck["memory"])
+        self.st.iters, self.st.evals = int(ck["iters"]), int(ck["evals"])
+        self.st.history = list(ck["history"])
+        self.gn, self.tol = float(ck["gn"]), float(ck["tol"])
+        self._next_iteration()
+
 
     def trial(self):
         return self._trial
@@ -263,23 +299,31 @@ class LbfgsJob:
         self._trial = None
         self.seconds = time.perf_counter() - self.t0
         if isinstance(self.st, _DeviceState):
+            if self.keep_checkpoint:
+                self.final_checkpoint = self.checkpoint()
             self.st.close()
 
     def result(self) -> LBFGSResult:
         st = self.st
-        return LBFGSResult(st.v, st.J, self.gn, st.iters, st.evals, self.gn <= self.tol, self.seconds, st.history)
+        return LBFGSResult(st.v, st.J, self.gn, st.iters, st.evals, self.gn <= self.tol, self.seconds, st.history,
+                           self.final_checkpoint)
 
 
 def lbfgs(ev, v0: torch.Tensor, *, m: int = 10, gtol: float = 1e-6, relative: bool = False,
           max_iter: int = 20000, c1: float = 1e-4, sigma: float = 0.9, eps_f: float | None = None,
-          max_evals_per_iter: int = 60, device_memory: bool = False) -> LBFGSResult:
+          max_evals_per_iter: int = 60, device_memory: bool = False, resume: dict | None = None,
+          checkpoint: bool = False) -> LBFGSResult:
     """Minimise J from v0.  Stops when ||g||_inf <= gtol (times ||g0||_inf if relative), or when
     a line search finds no acceptable step (converged is then False).  eps_f is the relative
     rounding level of the evaluated J used by the approximate Wolfe test.  device_memory keeps
     the pairs and computes the directions in the library's kernels (fe_lbfgs; CUDA v0 only)
-    instead of torch vector operations."""
+    instead of torch vector operations.  checkpoint=True returns the state at the stop in
+    result.checkpoint (device memory only); resume=<such a state> continues from it (v0 then
+    only gives the device and size), with bitwise the iterates of an uninterrupted run, and
+    max_iter counts the iterations of the whole run."""
     job = LbfgsJob(v0, m=m, gtol=gtol, relative=relative, max_iter=max_iter, c1=c1, sigma=sigma,
-                   eps_f=_noise(ev, eps_f), max_evals_per_iter=max_evals_per_iter, device_memory=device_memory)
+                   eps_f=_noise(ev, eps_f), max_evals_per_iter=max_evals_per_iter, device_memory=device_memory,
+                   resume=resume, keep_checkpoint=checkpoint)
     while not job.done:
         J, g = ev(job.trial())
         job.feed(J, g)

@@ -129,3 +129,62 @@ def test_smallest_memory_and_one_unknown():
     d, gd = mem.direction(g)
     assert abs(float(d[0]) + 0.7 / a) <= 1e-15 and abs(gd + 0.49 / a) <= 1e-15
     mem.close()
+
+
+def test_memory_save_restore_gives_bitwise_directions():
+    """fe_lbfgs_save / fe_lbfgs_restore: a memory restored from a saved one (wrapped ring, so
+    the pairs sit in other slots) gives bitwise the same directions and, after one more pair,
+    the same updates; restoring more pairs than m is refused."""
+    fem = _fem()
+    n, m = 3001, 5
+    a = fem.LbfgsMemory(n, m)
+    for v_new, v, g_new, g in _pairs(n, 8, seed=5):    # 8 > m: the ring has wrapped
+        a.update(v_new, v, g_new, g)
+    state = a.save()
+    assert state[0].shape == (m, n) and state[2].shape == (m, m)
+    b = fem.LbfgsMemory(n, m)
+    b.restore(state)
+    assert b.pairs() == m
+    g0 = torch.randn(n, dtype=torch.float64, generator=torch.Generator().manual_seed(3)).cuda()
+    da, gda = a.direction(g0)
+    db, gdb = b.direction(g0)
+    assert torch.equal(da, db) and gda == gdb
+    (v_new, v, g_new, g), = _pairs(n, 1, seed=11)
+    assert a.update(v_new, v, g_new, g) == b.update(v_new, v, g_new, g)
+    da, _ = a.direction(g0)
+    db, _ = b.direction(g0)
+    assert torch.equal(da, db)
+    small = fem.LbfgsMemory(n, m - 1)
+    with pytest.raises(fem.FEError):
+        small.restore(state)
+    empty = fem.LbfgsMemory(n, m)
+    empty.restore(fem.LbfgsMemory(n, m).save())
+    assert empty.pairs() == 0
+    for x in (a, b, small, empty):
+        x.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "df64"])
+def test_lbfgs_checkpoint_and_resume_continue_bitwise(precision):
+    """An L-BFGS run stopped at 25 iterations with a checkpoint, the checkpoint pickled and
+    resumed, reaches bitwise the iterate, J, counters and history of one uninterrupted run."""
+    import pickle
+    fem = _fem()
+    from paper_2109_01158_gb300 import minimize
+    w = mg.neohooke_cube3d(10)
+    w.f = np.tile([0.0, 0.0, -1e-2], w.nn)
+    prec = fem.FE_F64 if precision == "f64" else fem.FE_DF64
+    gm = fem.FEMesh.from_workload(w, precisions=(prec,))
+    gm.set_input(fem.FE_INPUT_DISPLACEMENT)
+    u0 = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+    kw = dict(gtol=1e-9, relative=True, device_memory=True)
+    full = minimize.lbfgs(minimize.mesh_evaluator(gm), u0, max_iter=60, **kw)
+    part = minimize.lbfgs(minimize.mesh_evaluator(gm), u0, max_iter=25, checkpoint=True, **kw)
+    assert part.iters == 25 and part.checkpoint is not None
+    ck = pickle.loads(pickle.dumps(part.checkpoint))
+    rest = minimize.lbfgs(minimize.mesh_evaluator(gm), u0, max_iter=60, resume=ck, **kw)
+    assert rest.iters == full.iters and rest.evals == full.evals
+    assert rest.J == full.J and torch.equal(rest.v, full.v)
+    assert rest.history == full.history
+    with pytest.raises(ValueError):
+        minimize.lbfgs(minimize.mesh_evaluator(gm), u0, max_iter=60, resume=ck, gtol=1e-9, relative=True)
