@@ -33,7 +33,8 @@ def nvcc() -> str:
 
 
 def _deps_mtime() -> float:
-    files = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    files = (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
+             + glob.glob(os.path.join(INCLUDE, "*.h")))
     return max((os.path.getmtime(f) for f in files), default=0.0)
 
 

@@ -9,6 +9,7 @@
 
 #include "async_copy.cuh"  // kWaitCycles
 #include "fe_internal.cuh"
+#include "trace.h"
 
 namespace fe {
 
@@ -455,6 +456,7 @@ fe_status fe_set_stream(fe_ctx* c, void* cuda_stream) {
 
 fe_status fe_mesh_upload(fe_ctx* c, int dim, int d, int64_t nn, const double* coords, int64_t ne,
                          const int32_t* elems, const uint8_t* dirichlet, int order) {
+  FE_TRACE("fe_mesh_upload");
   if (!c) return set_error(FE_EINVAL, "null context");
   if (d != 1 && d != dim) return set_error(FE_EINVAL, "d must be 1 or dim");
   fe_status st0 = check_mesh(dim, nn, coords, ne, elems, order);
@@ -571,6 +573,7 @@ fe_status fe_set_load(fe_ctx* c, const double* f_host) {
 }
 
 fe_status fe_precompute(fe_ctx* c, unsigned precisions) {
+  FE_TRACE("fe_precompute");
   if (!c) return set_error(FE_EINVAL, "null context");
   if (!c->have_mesh) return set_error(FE_EINVAL, "no mesh uploaded");
   if (precisions == 0 || (precisions & ~7u)) return set_error(FE_EINVAL, "bad precision mask");
@@ -658,6 +661,7 @@ fe_status fe_footprint(const fe_ctx* c, size_t* bytes) {
 }
 
 fe_status fe_energy(fe_ctx* c, const double* v, double* J, double* dens) {
+  FE_TRACE("fe_energy");
   fe_status st = check_ready(c);
   if (st) return st;
   if (!v || !J) return set_error(FE_EINVAL, "null v or J");
@@ -666,6 +670,7 @@ fe_status fe_energy(fe_ctx* c, const double* v, double* J, double* dens) {
 }
 
 fe_status fe_gradient_exact(fe_ctx* c, const double* v, double* gout) {
+  FE_TRACE("fe_gradient_exact");
   fe_status st = check_ready(c);
   if (st) return st;
   if (!v || !gout) return set_error(FE_EINVAL, "null v or g");
@@ -674,6 +679,7 @@ fe_status fe_gradient_exact(fe_ctx* c, const double* v, double* gout) {
 }
 
 fe_status fe_energy_gradient(fe_ctx* c, const double* v, double* J, double* gout) {
+  FE_TRACE("fe_energy_gradient");
   fe_status st = check_ready(c);
   if (st) return st;
   if (!v || !J || !gout) return set_error(FE_EINVAL, "null v, J or g");
@@ -682,6 +688,7 @@ fe_status fe_energy_gradient(fe_ctx* c, const double* v, double* J, double* gout
 }
 
 fe_status fe_hessian_vector(fe_ctx* c, const double* v, const double* w, double* Hw) {
+  FE_TRACE("fe_hessian_vector");
   fe_status st = check_ready(c);
   if (st) return st;
   if (!v || !w || !Hw) return set_error(FE_EINVAL, "null v, w or Hw");
@@ -738,6 +745,7 @@ fe_status fe_from_device_order(fe_ctx* c, const double* y, double* x) { return p
 
 fe_status fe_cg_steihaug(fe_ctx* c, const double* v, const double* g, double radius, double tol, int max_cg,
                          double* z, double* Hz, int* iters, int* boundary) {
+  FE_TRACE("fe_cg_steihaug");
   fe_status st = check_ready(c);
   if (st) return st;
   if (!v || !g || !z || !Hz || !iters || !boundary) return set_error(FE_EINVAL, "null argument");
@@ -766,6 +774,7 @@ fe_status fe_cg_steihaug(fe_ctx* c, const double* v, const double* g, double rad
 
 fe_status fe_gradient_fd(fe_ctx* c, const double* v, double eps, double* gout, const int64_t* dofs,
                          int64_t ndofs) {
+  FE_TRACE("fe_gradient_fd");
   fe_status st = check_ready(c);
   if (st) return st;
   if (!v || !gout) return set_error(FE_EINVAL, "null v or g");
@@ -789,6 +798,7 @@ static void* mapped_device_ptr(const void* host) {
 }
 
 fe_status fe_energy_gradient_host(fe_ctx* c, const double* v_host, double* J_host, double* g_host) {
+  FE_TRACE("fe_energy_gradient_host");
   fe_status st = check_ready(c);
   if (st) return st;
   if (!v_host || !J_host || !g_host) return set_error(FE_EINVAL, "null argument");
@@ -812,6 +822,7 @@ fe_status fe_energy_gradient_host(fe_ctx* c, const double* v_host, double* J_hos
 }
 
 fe_status fe_energy_gradient_host_async(fe_ctx* c, const double* v_host, double* J_host, double* g_host) {
+  FE_TRACE("fe_energy_gradient_host_async");
   fe_status st = check_ready(c);
   if (st) return st;
   if (!v_host || !J_host || !g_host) return set_error(FE_EINVAL, "null argument");

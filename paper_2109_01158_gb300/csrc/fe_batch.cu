@@ -41,6 +41,7 @@
 
 #include "elem_df.cuh"
 #include "fe_internal.cuh"
+#include "trace.h"
 
 namespace fe {
 namespace {
@@ -603,6 +604,7 @@ fe_status fe_batch_set_wait_limit(fe_batch* b, int64_t cycles) {
 }
 
 fe_status fe_batch_energy_gradient(fe_batch* b, const fe_batch_item* items, int n) {
+  FE_TRACE("fe_batch_energy_gradient");
   if (!b || (n > 0 && !items) || n < 0) return set_error(FE_EINVAL, "bad arguments");
   if (n == 0) return FE_OK;
   int prev = -1;

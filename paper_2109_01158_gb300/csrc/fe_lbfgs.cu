@@ -25,6 +25,7 @@
 
 #include "fe_internal.cuh"
 #include "reduce.cuh"
+#include "trace.h"
 
 namespace {
 constexpr int kMaxPairs = 16;
@@ -359,6 +360,7 @@ extern "C" {
 
 fe_status fe_lbfgs_step(fe_lbfgs* L, const double* v_new, const double* v, const double* g_new, const double* g,
                         double* d, double* out3) {
+  FE_TRACE("fe_lbfgs_step");
   if (!L || !v_new || !v || !g_new || !g || !d || !out3) return set_error(FE_EINVAL, "null argument");
   LbDeviceGuard guard(L->device);
   const int nb = grid_for(L->n, kMaxNodeBlocks);
@@ -395,6 +397,7 @@ extern "C" {
 
 fe_status fe_lbfgs_update(fe_lbfgs* L, const double* v_new, const double* v, const double* g_new, const double* g,
                           double* sy) {
+  FE_TRACE("fe_lbfgs_update");
   if (!L || !v_new || !v || !g_new || !g || !sy) return set_error(FE_EINVAL, "null argument");
   LbDeviceGuard guard(L->device);
   const LbSlots sl = slots_of(L);
@@ -408,6 +411,7 @@ fe_status fe_lbfgs_update(fe_lbfgs* L, const double* v_new, const double* v, con
 }
 
 fe_status fe_lbfgs_direction(fe_lbfgs* L, const double* g, double* d, double* gd) {
+  FE_TRACE("fe_lbfgs_direction");
   if (!L || !g || !d || !gd) return set_error(FE_EINVAL, "null argument");
   LbDeviceGuard guard(L->device);
   const LbSlots sl = slots_of(L);

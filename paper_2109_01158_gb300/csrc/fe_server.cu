@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "fe_internal.cuh"
+#include "trace.h"
 
 namespace fe {
 namespace {
@@ -172,6 +173,7 @@ struct fe_server {
 };
 
 fe_status fe_server::launch(Slot* S) {
+  FE_TRACE("fe_server_launch");
   const int n = (int)S->reqs.size();
   // smallest mesh first: the tiles of a batch are handed out in this order
   std::stable_sort(S->reqs.begin(), S->reqs.end(), [](const Req* a, const Req* b) { return a->mesh->ne < b->mesh->ne; });
@@ -465,6 +467,7 @@ fe_status fe_server_destroy(fe_server* s) {
 
 fe_status fe_server_submit(fe_server* s, const fe_ctx* mesh, const double* v_host, double* J_host,
                            double* g_host, double t_arrival, int64_t* ticket) {
+  FE_TRACE("fe_server_submit");
   if (!s || !mesh || !v_host || !J_host || !g_host || !ticket) return set_error(FE_EINVAL, "null argument");
   if (!mesh->have_pre || !mesh->model_set || !(mesh->pre_mask & (1u << FE_DF64)))
     return set_error(FE_EINVAL, "server request: mesh must be precomputed with FE_DF64 and have a model");
@@ -499,6 +502,7 @@ fe_status fe_server_submit(fe_server* s, const fe_ctx* mesh, const double* v_hos
 }
 
 fe_status fe_server_wait(fe_server* s, int64_t ticket, double* t_arrival, double* t_start, double* t_done) {
+  FE_TRACE("fe_server_wait");
   if (!s) return set_error(FE_EINVAL, "null server");
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->reqs.find(ticket);
