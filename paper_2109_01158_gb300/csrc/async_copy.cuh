@@ -95,10 +95,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t phase, long long limit,
                                                    const volatile int* abort) {
   const bool poll = limit < kWaitCycles;
+  if (poll ? mbar_test_wait(bar, phase) : mbar_try_wait(bar, phase)) return true;   // no clock read
   const long long t0 = clock64();
   for (;;) {
-    if (poll ? mbar_test_wait(bar, phase) : mbar_try_wait(bar, phase)) return true;
     if (*abort) return false;
+    if (poll ? mbar_test_wait(bar, phase) : mbar_try_wait(bar, phase)) return true;
     if (clock64() - t0 > limit) return false;
   }
 }

@@ -65,8 +65,10 @@ __device__ __noinline__ bool far_from_identity_f64(const float* Hf, int dim, flo
 // result of the same size; adding the (tiny) lo difference and rounding once leaves at most
 // about one float ulp of the difference.  (Rounding u itself to float first would lose the
 // factor by which u exceeds its differences across an element.)
+// The two differences are one paired instruction (b * -1 + a: a - b rounded once).
 __device__ __forceinline__ float pair_diff(float2 a, float2 b) {
-  return __fadd_rn(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
+  const float2 d = __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+  return __fadd_rn(d.x, d.y);
 }
 
 // One element in float: from the differences a[l][j] = (u_{l+1} - u_0)_j (l = 0..DIM-1) and
@@ -76,9 +78,10 @@ template <int DIM, int D, int MODEL, bool WANT_W, bool GRAD>
 __device__ __forceinline__ float elem_f32(const float (&a)[DIM][D], const float (&g)[DIM][DIM], float vT,
                                           float C1, float D1, const ModelParams& mp, float (&P)[D][DIM],
                                           bool& bad) {
-  // every product and sum is an explicit fmaf or _rn intrinsic: the compiler cannot contract
-  // them differently in the energy-only and the gradient instantiations, which therefore give
-  // bitwise the same W (and the two gradient instantiations the same P)
+  // every product and sum is an explicit fmaf or _rn intrinsic (or its paired form, two
+  // independent operations in one instruction, rounded the same way): the compiler cannot
+  // contract them differently in the energy-only and the gradient instantiations, which
+  // therefore give bitwise the same W (and the two gradient instantiations the same P)
   float H[D][DIM];
 #pragma unroll
   for (int j = 0; j < D; ++j)
@@ -91,12 +94,18 @@ __device__ __forceinline__ float elem_f32(const float (&a)[DIM][D], const float 
     }
   float W = 0.f;
   if constexpr (MODEL == FE_NEOHOOKE) {
-    float hsq = __fmul_rn(H[0][0], H[0][0]);
+    // |H|^2 with two accumulators (the even and the odd row-major entries, one paired
+    // instruction per two entries), added at the end
+    float hsq;
+    {
+      const float* Hf = &H[0][0];
+      float2 acc = __fmul2_rn(make_float2(Hf[0], Hf[1]), make_float2(Hf[0], Hf[1]));
 #pragma unroll
-    for (int j = 0; j < DIM; ++j)
-#pragma unroll
-      for (int m = 0; m < DIM; ++m)
-        if (j + m > 0) hsq = fmaf(H[j][m], H[j][m], hsq);
+      for (int f = 2; f + 1 < DIM * DIM; f += 2)
+        acc = __ffma2_rn(make_float2(Hf[f], Hf[f + 1]), make_float2(Hf[f], Hf[f + 1]), acc);
+      hsq = __fadd_rn(acc.x, acc.y);
+      if (DIM * DIM % 2) hsq = fmaf(Hf[DIM * DIM - 1], Hf[DIM * DIM - 1], hsq);
+    }
     float tr, q, C[DIM][DIM];  // q = i2(H) + det H, C = cof(I + H)
     if constexpr (DIM == 3) {
       tr = __fadd_rn(__fadd_rn(H[0][0], H[1][1]), H[2][2]);
@@ -159,15 +168,34 @@ __device__ __forceinline__ float elem_f32(const float (&a)[DIM][D], const float 
       const float aa = __fmul_rn(__fmul_rn(2.f, C1), vT);
       const float c = __fmul_rn(__fmul_rn(__fmul_rn(2.f, D1), delta), vT);
       const float ai = __fmul_rn(aa, inv_det);
+      float ch[DIM][DIM];
 #pragma unroll
       for (int j = 0; j < DIM; ++j)
 #pragma unroll
         for (int m = 0; m < DIM; ++m) {
-          float ch = __fmul_rn(C[j][0], H[m][0]);  // (C H^T)_jm = sum_k C_jk H_mk
+          float t = __fmul_rn(C[j][0], H[m][0]);  // (C H^T)_jm = sum_k C_jk H_mk
 #pragma unroll
-          for (int k = 1; k < DIM; ++k) ch = fmaf(C[j][k], H[m][k], ch);
-          P[j][m] = fmaf(aa, H[j][m], fmaf(ai, ch, __fmul_rn(c, C[j][m])));
+          for (int k = 1; k < DIM; ++k) t = fmaf(C[j][k], H[m][k], t);
+          ch[j][m] = t;
         }
+      // P elementwise, two entries per paired instruction (row-major order)
+      const float* Hf = &H[0][0];
+      const float* Cf = &C[0][0];
+      const float* chf = &ch[0][0];
+      float* Pf = &P[0][0];
+      const float2 aa2 = make_float2(aa, aa), ai2 = make_float2(ai, ai), c2 = make_float2(c, c);
+#pragma unroll
+      for (int f = 0; f + 1 < DIM * DIM; f += 2) {
+        const float2 t = __ffma2_rn(aa2, make_float2(Hf[f], Hf[f + 1]),
+                                    __ffma2_rn(ai2, make_float2(chf[f], chf[f + 1]),
+                                               __fmul2_rn(c2, make_float2(Cf[f], Cf[f + 1]))));
+        Pf[f] = t.x;
+        Pf[f + 1] = t.y;
+      }
+      if (DIM * DIM % 2) {
+        const int f = DIM * DIM - 1;
+        Pf[f] = fmaf(aa, Hf[f], fmaf(ai, chf[f], __fmul_rn(c, Cf[f])));
+      }
     }
   } else {
     float s = __fmul_rn(H[0][0], H[0][0]);

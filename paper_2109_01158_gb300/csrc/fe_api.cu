@@ -96,8 +96,7 @@ void free_precompute(fe_ctx* c) {
   dev_free(c, &c->ent, ne * k);
   dev_free(c, &c->slot, ne * k);
   dev_free(c, &c->b, nn * c->d);
-  dev_free(c, &c->dphi32, padded_ne(ne) * c->dim * c->dim);
-  dev_free(c, &c->vol32, padded_ne(ne));
+  dev_free(c, &c->blk32, (size_t)c->n_tiles * tile_block_bytes_f32(c->dim));
   dev_free(c, &c->dphi_df, ne * c->dim * c->dim);
   dev_free(c, &c->vol_df, ne);
   dev_free(c, &c->log_tab, kLogTable);
@@ -597,8 +596,7 @@ fe_status fe_precompute(fe_ctx* c, unsigned precisions) {
     }
   }
   if (precisions & (1u << FE_F32_COMP)) {
-    if ((st = dev_alloc(c, &c->dphi32, padded_ne(ne) * c->dim * c->dim)) || (st = dev_alloc(c, &c->vol32, padded_ne(ne))) ||
-        (st = build_tiles(c))) {
+    if ((st = build_tiles(c)) || (st = dev_alloc(c, &c->blk32, (size_t)c->n_tiles * tile_block_bytes_f32(c->dim)))) {
       free_precompute(c);
       return st;
     }

@@ -9,18 +9,22 @@
 //                 and the block partials of b.v;
 //   k_tile_f32    one persistent block per SM walks its element tiles (fe_tiles.cu,
 //                 tile_common.cuh) with specialised warps:
-//                   node warps copy the next tile's float pairs into shared memory;
+//                   the producer warp stages each tile's element block (dphi, vol, local
+//                      ids and slots, laid out per tile by k_tile_blocks32) with one bulk
+//                      copy, and its node records with another;
+//                   node warps copy the tile's float pairs, b_i and Dirichlet masks into
+//                      shared memory;
 //                   element warps, one thread per element: H from float-pair differences of
 //                      u, W and |T| dW/dF in float, and the local forces
 //                      r_{T,l} = |T| dW/dF grad(phi_l) written to the element's local slots in
-//                      shared memory;
-//                   node warps then sum the patches, one thread per tile node: the node's
-//                      local slots summed in float in a fixed order; a node whose patch lies
-//                      in the tile gets g_i = sum - b_i (0 on Dirichlet dofs), a shared node
-//                      leaves its partial sum;
-//                   the producer warp issues the bulk copies and adds the tile's |T| W into its
-//                      energy partial (float pairs per lane, FP64 across lanes); the last block
-//                      adds the partials in tile order;
+//                      shared memory; then the patch sums of the previous tile, one thread per
+//                      (tile node, component): the node's local slots summed in float in a
+//                      fixed order; a node whose patch lies in the tile gets g_i = sum - b_i
+//                      (0 on Dirichlet dofs), a shared node leaves its partial sum;
+//                   each element warp adds its |T| W by a pairwise tree in float, and the
+//                      producer the tile's warp sums by a TwoSum tree (float pairs) into the
+//                      tile's energy partial (FP64); the last block adds the partials in tile
+//                      order;
 //   k_tile_shared adds the shared nodes' partials in tile order.
 // The local forces never leave the chip (only the shared nodes' partials do), and every sum
 // has a fixed order: bitwise reproducible whatever the number of blocks.
@@ -49,6 +53,24 @@ __device__ __forceinline__ void load_pairs_g(const float2* __restrict__ u, int64
   } else {
     const float4* p = reinterpret_cast<const float4*>(u) + 2 * n;
     const float4 a = __ldg(p), b = __ldg(p + 1);
+    w[0] = make_float2(a.x, a.y);
+    w[1] = make_float2(a.z, a.w);
+    w[2] = make_float2(b.x, b.y);
+  }
+}
+
+// The D float pairs of tile node k from shared memory (DP pairs per node).
+template <int D, int DP>
+__device__ __forceinline__ void load_pairs_s(const float2* us, int k, float2 (&w)[D]) {
+  if constexpr (DP == 1) {
+    w[0] = us[k];
+  } else if constexpr (DP == 2) {
+    const float4 a = reinterpret_cast<const float4*>(us)[k];
+    w[0] = make_float2(a.x, a.y);
+    w[1] = make_float2(a.z, a.w);
+  } else {
+    const float4* p = reinterpret_cast<const float4*>(us) + 2 * k;
+    const float4 a = p[0], b = p[1];
     w[0] = make_float2(a.x, a.y);
     w[1] = make_float2(a.z, a.w);
     w[2] = make_float2(b.x, b.y);
@@ -128,11 +150,12 @@ __global__ void __launch_bounds__(kThreads) k_pairs32(int64_t nn, const double* 
 
 // Barriers of the tile pipeline (index: buffer of the tile).
 struct PipeBars {
-  uint64_t e_full[2], e_empty[2];    // element stage: TMA landed / element warps done
-  uint64_t r_full[3], r_empty[3];    // node records: TMA landed / node warps done
-  uint64_t u_full[2], u_empty[2];    // nodal values: node warps wrote / element warps done
-  uint64_t rs_full[2], rs_empty[2];  // local forces and energies: element warps wrote / node
-                                     // warps and producer done
+  uint64_t e_full[2];                // element stage: its bulk copy landed
+  uint64_t in_full[2];               // element stage landed and nodal values written
+  uint64_t in_empty[2];              // element warps done with the element stage and nodal values
+  uint64_t r_full[kRecBufs], r_empty[kRecBufs];   // node records: landed / patch sums done
+  uint64_t rs_full[2], rs_empty[2];  // local forces and energies: element warps wrote / patch
+                                     // sums and producer done
 };
 
 // The block: warps 0 .. kTileElems/32 - 1 are element warps (one thread per element of a
@@ -155,7 +178,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
   constexpr int NN = 32 * kTileNodeWarps;                    // node threads
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ PipeBars bars;
-  __shared__ int4 info[3];        // {e0, e1, k0, nt} of the tile whose records are in R[slot]
+  __shared__ int4 info[kRecBufs];        // {e0, e1, k0, nt} of the tile whose records are in R[slot]
   __shared__ volatile int abort_flag;
   const int G = gridDim.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool elem_warp = warp < NEW, node_warp = !elem_warp && warp < NEW + kTileNodeWarps;
@@ -164,13 +187,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
   const int my_tiles = (int)((ntiles - blockIdx.x + G - 1) / G);   // tiles blockIdx.x + i G
   auto tile_of = [&](int i) { return (int64_t)blockIdx.x + (int64_t)i * G; };
   auto E = [&](int i) { return smem + S::kE + (i & 1) * S::kEBytes; };
-  auto R = [&](int i) { return reinterpret_cast<int4*>(smem + S::kR + (i % 3) * S::kRBytes); };
+  auto R = [&](int i) { return reinterpret_cast<int4*>(smem + S::kR + (i % kRecBufs) * S::kRBytes); };
   auto U = [&](int i) { return reinterpret_cast<float2*>(smem + S::kU + (i & 1) * S::kUBytes); };
   // component j of the local forces of tile i, by local slot
   auto RC = [&](int i, int j) { return reinterpret_cast<float*>(smem + S::kRs + (i & 1) * S::kRsBytes + j * S::kColBytes); };
   auto EW = [&](int i) { return reinterpret_cast<float*>(smem + S::kEw + (i & 1) * S::kEwBytes); };
-  auto BDB = [&](int i) { return reinterpret_cast<double*>(smem + S::kBd + (i % 3) * S::kBdBytes); };
-  auto BDM = [&](int i) { return reinterpret_cast<int*>(smem + S::kBd + (i % 3) * S::kBdBytes + S::kBdMaskOff); };
+  auto BDB = [&](int i) { return reinterpret_cast<double*>(smem + S::kBd + (i % kRecBufs) * S::kBdBytes); };
+  auto BDM = [&](int i) { return reinterpret_cast<int*>(smem + S::kBd + (i % kRecBufs) * S::kBdBytes + S::kBdMaskOff); };
   // every thread of a warp calls wait() together and gets the same answer (the warp leaves the
   // pipeline as a whole, so no lane is left behind in a warp-wide operation)
   bool ok = true;
@@ -197,10 +220,9 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
     return ok;
   };
   // the issuer's copies: how many were issued into each buffer (to drain them on abort)
-  int nE[2] = {0, 0}, nR[3] = {0, 0, 0};
+  int nE[2] = {0, 0}, nR[kRecBufs] = {};
   auto issue_elems = [&](int i) {
-    const int4 in = info[i % 3];
-    pipe_issue_elems<S, 4>(E(i), ta, in.x, in.y, &bars.e_full[i & 1]);
+    pipe_issue_elems<S>(E(i), ta, tile_of(i), &bars.e_full[i & 1]);
     ++nE[i & 1];
   };
   // the element and node ranges of the next tile whose records are issued, loaded one issue
@@ -216,22 +238,21 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
   auto issue_recs = [&](int i) {
     if (pre_i != i) load_pre(i);
     const int4 raw = pre;
-    info[i % 3] = make_int4(raw.x, raw.y, raw.z, raw.w - raw.z);
-    pipe_issue_recs(R(i), ta, raw.z, raw.w - raw.z, &bars.r_full[i % 3]);
-    ++nR[i % 3];
+    info[i % kRecBufs] = make_int4(raw.x, raw.y, raw.z, raw.w - raw.z);
+    pipe_issue_recs(R(i), ta, raw.z, raw.w - raw.z, &bars.r_full[i % kRecBufs]);
+    ++nR[i % kRecBufs];
     load_pre(i + 1);
   };
   if (tid == 0) abort_flag = 0;
   if (issuer) {
     for (int q = 0; q < 2; ++q) {
       mbar_init(&bars.e_full[q], 1);
-      mbar_init(&bars.e_empty[q], NEW);
-      mbar_init(&bars.u_full[q], kTileNodeWarps);
-      mbar_init(&bars.u_empty[q], NEW);
+      mbar_init(&bars.in_full[q], kTileNodeWarps);
+      mbar_init(&bars.in_empty[q], NEW);
       mbar_init(&bars.rs_full[q], NEW);
       mbar_init(&bars.rs_empty[q], NEW + 1);
     }
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < kRecBufs; ++q) {
       mbar_init(&bars.r_full[q], 1);
       mbar_init(&bars.r_empty[q], NEW);
     }
@@ -243,43 +264,50 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
   if (warp == NEW + kTileNodeWarps) {
     // producer warp: lane 0 issues the bulk copies; the warp adds the tiles' energy partials
     if (issuer) {
-      // records of the first three tiles, elements of the first two
-      for (int i = 0; i < 3 && i < my_tiles; ++i) issue_recs(i);
+      // records of the first kRecBufs tiles, elements of the first two
+      for (int i = 0; i < kRecBufs && i < my_tiles; ++i) issue_recs(i);
       for (int i = 0; i < 2 && i < my_tiles; ++i) issue_elems(i);
     }
+    // In the order the element warps free the buffers: the element stage of tile i when they
+    // are done with its elements (B(i)), which is also when its energies are complete; the
+    // record slot of tile i - 1 only after its patch sums (C(i - 1), done after B(i)), so that
+    // the next element copy never waits behind patch sums.
     for (int i = 0; i < my_tiles; ++i) {
-      // the element stage of tile i is free once the element warps are done with it (the same
-      // moment as their forces and energies are complete)
       if (i + 2 < my_tiles) {
-        if (!wait_lane0(&bars.e_empty[i & 1], i >> 1)) break;
+        if (!wait_lane0(&bars.in_empty[i & 1], i >> 1)) break;
         if (issuer) issue_elems(i + 2);
       }
       if (!wait(&bars.rs_full[i & 1], i >> 1)) break;
       if (ENERGY) {
-        // the element warps' pairs, in FP64 across lanes in a fixed order
-        const float2 wp = lane < NEW ? reinterpret_cast<const float2*>(EW(i))[lane] : make_float2(0.f, 0.f);
-        const bool inf = __any_sync(0xffffffffu, isinf(wp.x));
-        double x = pipe_warp_sum(f2d_bits(wp.x) + f2d_bits(wp.y));
-        if (inf) x = CUDART_INF;
-        if (lane == 0) epart[tile_of(i)] = x;
+        // the element warps' sums as float pairs, added by a fixed TwoSum tree across the lanes
+        // (FP32 operations: a chain of FP64 additions has a long latency on this GPU), then
+        // hi + lo in FP64; +Inf apart, as TwoSum on Inf gives NaN
+        const float w = lane < NEW ? EW(i)[lane] : 0.f;
+        const bool inf = __any_sync(0xffffffffu, isinf(w));
+        df p = {isinf(w) ? 0.f : w, 0.f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const df q = {__shfl_down_sync(0xffffffffu, p.hi, o), __shfl_down_sync(0xffffffffu, p.lo, o)};
+          p = df_add(p, q);
+        }
+        if (lane == 0) epart[tile_of(i)] = inf ? CUDART_INF : f2d_bits(p.hi) + f2d_bits(p.lo);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars.rs_empty[i & 1]);
-      // the record slot of tile i is free once the node warps have summed its patches
-      if (i + 3 < my_tiles) {
-        if (!wait_lane0(&bars.r_empty[i % 3], i / 3)) break;
-        if (issuer) issue_recs(i + 3);
+      if (i >= 1 && i - 1 + kRecBufs < my_tiles) {
+        if (!wait_lane0(&bars.r_empty[(i - 1) % kRecBufs], (i - 1) / kRecBufs)) break;
+        if (issuer) issue_recs(i - 1 + kRecBufs);
       }
     }
   } else if (node_warp) {
     const int ntid = tid - NE;
     // the nodal values of tile i (its records must have landed) into U(i)
     auto gather = [&](int i) {
-      if (!wait(&bars.r_full[i % 3], i / 3)) return false;
-      if (i >= 2 && !wait(&bars.u_empty[i & 1], (i >> 1) - 1)) return false;
+      if (!wait(&bars.r_full[i % kRecBufs], i / kRecBufs)) return false;
+      if (i >= 2 && !wait(&bars.in_empty[i & 1], (i >> 1) - 1)) return false;
       const int4* rec = R(i);
       float2* us = U(i);
-      const int nt = info[i % 3].w;
+      const int nt = info[i % kRecBufs].w;
       double* bd = BDB(i);
       int* bm = BDM(i);
       // all loads of a thread's nodes first, then the stores: the loads are in flight together
@@ -315,8 +343,11 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
           if (GRAD) bm[k] = mk[q];
         }
       }
+      // the first node warp also waits for the tile's element copy, so that the element warps
+      // wait on one barrier for both (its completion orders the copy before their loads)
+      if (warp == NEW && !wait(&bars.e_full[i & 1], i >> 1)) return false;
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bars.u_full[i & 1]);
+      if (lane == 0) mbar_arrive(&bars.in_full[i & 1]);
       return true;
     };
     if (my_tiles > 0) gather(0);
@@ -335,7 +366,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
         const float* rc0 = RC(i, 0);
         const double* bd = BDB(i);
         const int* bm = BDM(i);
-        const int nt = info[i % 3].w;
+        const int nt = info[i % kRecBufs].w;
         for (int w = tid; w < nt * D; w += NE) {
           const int k = w / D, j = w - k * D;
           const int4 rec = Rr[k];
@@ -361,15 +392,15 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(&bars.rs_empty[i & 1]);
-        mbar_arrive(&bars.r_empty[i % 3]);
+        mbar_arrive(&bars.r_empty[i % kRecBufs]);
       }
       return true;
     };
     for (int i = 0; i < my_tiles && ok; ++i) {
       // B: one thread per element of tile i
-      if (!wait(&bars.e_full[i & 1], i >> 1) || !wait(&bars.u_full[i & 1], i >> 1)) break;
+      if (!wait(&bars.in_full[i & 1], i >> 1)) break;
       if (i >= 2 && !wait(&bars.rs_empty[i & 1], (i >> 1) - 1)) break;
-      const int4 in = info[i % 3];
+      const int4 in = info[i % kRecBufs];
       const unsigned char* St = E(i);
       const float2* us = U(i);
       float* rc0 = RC(i, 0);
@@ -378,11 +409,15 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
       if (e < in.y) {
         const uint4 le = reinterpret_cast<const uint4*>(St + S::kElemOff)[tid];
         const int lid[4] = {(int)(le.x & 0xffffu), (int)(le.x >> 16), (int)(le.y & 0xffffu), (int)(le.y >> 16)};
+        // each node's pairs in 16-byte loads (a node record is DP pairs, 16-byte aligned)
+        float2 un[K][D];
+#pragma unroll
+        for (int l = 0; l < K; ++l) load_pairs_s<D, DP>(us, lid[l], un[l]);
         float a[DIM][D];
 #pragma unroll
         for (int l = 1; l < K; ++l)
 #pragma unroll
-          for (int j = 0; j < D; ++j) a[l - 1][j] = pair_diff(us[lid[l] * DP + j], us[lid[0] * DP + j]);
+          for (int j = 0; j < D; ++j) a[l - 1][j] = pair_diff(un[l][j], un[0][j]);
         float gg[DIM][DIM];
 #pragma unroll
         for (int l = 0; l < DIM; ++l)
@@ -415,21 +450,15 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
         }
       }
       if (ENERGY) {
-        // the warp's |T| W as a float pair: a fixed TwoSum tree over the lanes (+Inf apart,
-        // as TwoSum on Inf gives NaN); the producer adds the tile's warp pairs in FP64
-        const bool inf = __any_sync(0xffffffffu, isinf(ew));
-        df p = {isinf(ew) ? 0.f : ew, 0.f};
+        // the warp's |T| W by a fixed pairwise tree in float (every term >= 0, +Inf allowed:
+        // relative error at most 5 roundings); the producer adds the tile's 24 warp sums
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const df q = {__shfl_down_sync(0xffffffffu, p.hi, o), __shfl_down_sync(0xffffffffu, p.lo, o)};
-          p = df_add(p, q);
-        }
-        if (lane == 0) reinterpret_cast<float2*>(EW(i))[warp] = inf ? make_float2(CUDART_INF_F, 0.f) : make_float2(p.hi, p.lo);
+        for (int o = 16; o > 0; o >>= 1) ew = __fadd_rn(ew, __shfl_xor_sync(0xffffffffu, ew, o));
+        if (lane == 0) EW(i)[warp] = ew;
       }
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive(&bars.e_empty[i & 1]);
-        mbar_arrive(&bars.u_empty[i & 1]);
+        mbar_arrive(&bars.in_empty[i & 1]);
         mbar_arrive(&bars.rs_full[i & 1]);
       }
       if (i >= 1 && !patch_sums(i - 1)) break;
@@ -444,7 +473,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
     if (issuer) {
       for (int q = 0; q < 2; ++q)
         if (nE[q] > 0) mbar_wait_bounded(&bars.e_full[q], (uint32_t)(nE[q] - 1) & 1u);
-      for (int q = 0; q < 3; ++q)
+      for (int q = 0; q < kRecBufs; ++q)
         if (nR[q] > 0) mbar_wait_bounded(&bars.r_full[q], (uint32_t)(nR[q] - 1) & 1u);
       if (ENERGY)
         for (int i = 0; i < my_tiles; ++i) epart[tile_of(i)] = CUDART_NAN;
@@ -455,6 +484,33 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
   if (ENERGY) pipe_finish_energy(epart, ntiles, bvp, nbv, shift, counter, J, reinterpret_cast<double*>(smem + S::kRs));
 }
 
+// The tiles' element blocks: for tile t, its elements' dphi (DIM*DIM arrays) and vol in float,
+// then their local ids / slots, each array at its offset of the element stage (S::kArrayBytes
+// apart, S::kElemOff), element k of the tile at index k; entries past the tile's last element
+// are zero.  One thread per (tile, element slot).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_tile_blocks32(int64_t ntiles, const int32_t* __restrict__ ebeg,
+                                                            const double* __restrict__ dphi,
+                                                            const double* __restrict__ vol,
+                                                            const uint4* __restrict__ telem, int64_t ne,
+                                                            unsigned char* __restrict__ blk) {
+  using S = typename Pipe32<DIM, DIM>::S;
+  const int64_t n = ntiles * kTileElems;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n; w += stride) {
+    const int64_t t = w / kTileElems;
+    const int k = (int)(w - t * kTileElems);
+    const int64_t e = (int64_t)__ldg(ebeg + t) + k;
+    const bool in = e < (int64_t)__ldg(ebeg + t + 1);
+    unsigned char* B = blk + t * S::kEBytes;
+#pragma unroll
+    for (int a = 0; a < DIM * DIM; ++a)
+      reinterpret_cast<float*>(B + a * S::kArrayBytes)[k] = in ? (float)__ldg(dphi + a * ne + e) : 0.f;
+    reinterpret_cast<float*>(B + DIM * DIM * S::kArrayBytes)[k] = in ? (float)__ldg(vol + e) : 0.f;
+    reinterpret_cast<uint4*>(B + S::kElemOff)[k] = in ? __ldg(telem + e) : make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
 template <int DIM, int D, int MODEL, bool E, bool G, bool DN>
 fe_status launch_tile_f32(fe_ctx* c, const ModelParams& mp, double* J, double* dens, double* g, const double* bvp,
                           int nbv) {
@@ -463,9 +519,7 @@ fe_status launch_tile_f32(fe_ctx* c, const ModelParams& mp, double* J, double* d
   static std::atomic<uint64_t> smem_set{0};
   fe_status st = ensure_smem((const void*)kern, c->device, S::kBytes, smem_set);
   if (st) return st;
-  TileArgs ta{c->tile_ebeg, c->tile_nbeg, c->tile_node, reinterpret_cast<const unsigned char*>(c->dphi32),
-              reinterpret_cast<const unsigned char*>(c->vol32), c->tile_elem, c->n_tiles, padded_ne(c->ne),
-              c->wait_limit};
+  TileArgs ta{c->tile_ebeg, c->tile_nbeg, c->tile_node, c->blk32, c->n_tiles, c->wait_limit};
   const bool disp = input_is_disp(c);
   const double* b = c->f_host.empty() ? nullptr : c->b;
   const int64_t grid = std::min<int64_t>(c->n_tiles, sm_count(c->device));
@@ -513,6 +567,23 @@ fe_status eval32_t(fe_ctx* c, const double* v, double* J, double* dens, double* 
 }
 
 }  // namespace
+
+size_t tile_block_bytes_f32(int dim) {
+  return dim == 3 ? (size_t)Pipe32<3, 3>::S::kEBytes : (size_t)Pipe32<2, 2>::S::kEBytes;
+}
+
+fe_status launch_tile_blocks_f32(fe_ctx* c) {
+  const int64_t n = c->n_tiles * kTileElems;
+  if (n == 0) return FE_OK;
+  if (c->dim == 3)
+    k_tile_blocks32<3><<<grid_for(n, 4 * kMaxElemBlocks), kThreads, 0, c->stream>>>(
+        c->n_tiles, c->tile_ebeg, c->dphi, c->vol, c->tile_elem, c->ne, c->blk32);
+  else
+    k_tile_blocks32<2><<<grid_for(n, 4 * kMaxElemBlocks), kThreads, 0, c->stream>>>(
+        c->n_tiles, c->tile_ebeg, c->dphi, c->vol, c->tile_elem, c->ne, c->blk32);
+  c->launches++;
+  return cuda_check(cudaGetLastError(), "f32 tile blocks");
+}
 
 fe_status launch_eval_f32(fe_ctx* c, const double* v, double* J, double* dens, double* g,
                           bool want_energy, bool want_grad) {

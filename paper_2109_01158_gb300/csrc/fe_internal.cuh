@@ -47,9 +47,7 @@ constexpr int kTileElems = 768;      // 128 hexahedra of six tetrahedra: one oct
 constexpr int kTileNodeWarps = 3;    // warps that gather nodal values and sum patches
 constexpr int kTileThreads = kTileElems + 32 * kTileNodeWarps + 32;   // + one producer warp
 constexpr int tile_max_nodes(int dim) { return dim == 3 ? 256 : 512; }
-// Tiles start on multiples of kTileAlign elements, and the element arrays the tile kernels
-// stage (dphi32, vol32, ...) use the padded stride padded_ne(ne): every staged range then
-// starts 16-byte aligned.
+// Tiles start on multiples of kTileAlign elements.
 constexpr int kTileAlign = 4;
 inline int64_t padded_ne(int64_t ne) { return (ne + kTileAlign - 1) / kTileAlign * kTileAlign; }
 
@@ -108,8 +106,10 @@ struct fe_ctx {
   int32_t* ent = nullptr;      // ne*(dim+1): e*(dim+1)+l, rows in increasing element order
   int32_t* slot = nullptr;     // (dim+1) SoA arrays of ne: CSR position of (e, l)
   double* b = nullptr;         // nn*d, device order
-  float* dphi32 = nullptr;     // FP32 copy of dphi (array stride padded_ne(ne))
-  float* vol32 = nullptr;      // FP32 copy of vol (padded_ne(ne) entries)
+  // FP32 element data of the tiles (fe_eval_f32.cu): one block of tile_block_bytes_f32(dim)
+  // bytes per tile, holding the tile's dphi, vol and tile_elem entries, so that one bulk copy
+  // stages a tile
+  unsigned char* blk32 = nullptr;
   float2* dphi_df = nullptr;   // double-float copy of dphi (hi, lo)
   float2* vol_df = nullptr;    // double-float copy of vol
   fe::LogEntry* log_tab = nullptr;  // table of the double-float logarithm
@@ -286,6 +286,11 @@ int sm_count(int device);
 // device-order mesh; freed with the precompute).
 fe_status build_tiles(fe_ctx* c);
 void free_tiles(fe_ctx* c);
+
+// fe_eval_f32.cu: bytes of one tile's FP32 element block, and the kernel that fills blk32 from
+// dphi, vol and tile_elem (after the precompute).
+size_t tile_block_bytes_f32(int dim);
+fe_status launch_tile_blocks_f32(fe_ctx* c);
 
 // Bracket a launch with profiling events when timing is enabled (no-op otherwise).
 enum Stage { kStagePrep = 0, kStageElem = 1, kStageGather = 2, kStageFdElem = 3, kStageFdGather = 4 };

@@ -224,17 +224,6 @@ __global__ void __launch_bounds__(kThreads) k_load(int64_t nn, int64_t ne, const
   }
 }
 
-// FP32 copies of `arrays` structure-of-arrays of ne doubles, written with the padded stride
-// ne4 (a multiple of 4 elements: every array starts 16-byte aligned).
-__global__ void k_to_f32(int arrays, int64_t ne, const double* __restrict__ a, int64_t ne4, float* __restrict__ o) {
-  const int64_t n = (int64_t)arrays * ne;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int64_t q = i / ne, e = i - q * ne;
-    o[q * ne4 + e] = (float)a[i];
-  }
-}
-
 template <int DIM>
 fe_status precompute_dim(fe_ctx* c) {
   constexpr int K = DIM + 1;
@@ -273,14 +262,7 @@ fe_status precompute_dim(fe_ctx* c) {
     k_slots<K><<<grid_for(nn, 4 * kMaxNodeBlocks), kThreads, 0, s>>>(nn, ne, c->row_ptr, c->ent, c->slot);
     c->launches += 3;
   }
-  if (c->pre_mask & (1u << FE_F32_COMP)) {
-    if (ne > 0) {
-      k_to_f32<<<grid_for(ne * DIM * DIM, 4 * kMaxElemBlocks), kThreads, 0, s>>>(DIM * DIM, ne, c->dphi,
-                                                                                padded_ne(ne), c->dphi32);
-      k_to_f32<<<grid_for(ne, 4 * kMaxElemBlocks), kThreads, 0, s>>>(1, ne, c->vol, padded_ne(ne), c->vol32);
-      c->launches += 2;
-    }
-  }
+  if ((c->pre_mask & (1u << FE_F32_COMP)) && ne > 0 && (st = launch_tile_blocks_f32(c))) return st;
   return cuda_check(cudaGetLastError(), "precompute launch");
 }
 

@@ -31,19 +31,22 @@ __device__ __forceinline__ double f2d_bits(float f) {
 
 // Shared-memory layout of the pipeline of one block (buffers of consecutive tiles alternate):
 //   E[2]   element stages: DIM*DIM shape-gradient arrays and the volume (EB bytes per element
-//          each), then the local ids / local slots (16 bytes per element); tiles start on
-//          multiples of kTileAlign elements and the arrays use the padded stride, so every
-//          copied range starts 16-byte aligned;
-//   R[3]   node records (int4 per tile node);
+//          each), then the local ids / local slots (16 bytes per element): the layout of a
+//          tile's block in device memory, which one bulk copy stages;
+//   R[kRecBufs]  node records (int4 per tile node);
 //   U[2]   the tile's nodal values, NU bytes per node;
 //   Rs[2]  the tile's local forces: D columns (one per component) of RB bytes per slot,
 //          each column 16 bytes longer than the slots (so the columns of one slot fall in
 //          different shared-memory banks);
-//   Ew[2]  the tile's energy |T| W per element warp (a float pair each);
-//   Bd[3]  the tile nodes' load b_i (D doubles per node) and Dirichlet mask (an int per node,
-//          bit j for dof j), copied by the node warps with the nodal values, so that the
-//          patch sums read them from shared memory; three buffers like the records, as they
+//   Ew[2]  the tile's energy |T| W per element warp (a float each);
+//   Bd[kRecBufs]  the tile nodes' load b_i (D doubles per node) and Dirichlet mask (an int per
+//          node, bit j for dof j), copied by the node warps with the nodal values, so that the
+//          patch sums read them from shared memory; as many buffers as the records, as they
 //          are read until the patch sums of the tile are done.
+// The records are requested kRecBufs tiles ahead, so that their copies are never what the
+// gather of a tile's nodal values waits for.
+constexpr int kRecBufs = 4;
+
 template <int DIM, int D, int EB, int NU, int RB>
 struct TilePipe {
   static constexpr int kNodes = tile_max_nodes(DIM);
@@ -57,53 +60,41 @@ struct TilePipe {
   static constexpr int kUBytes = (kNodes * NU + 15) / 16 * 16;
   static constexpr int kColBytes = (kSlots * RB + 15) / 16 * 16 + 16;   // one component's column
   static constexpr int kRsBytes = D * kColBytes;
-  static constexpr int kEwBytes = (kTileElems / 32 * 8 + 15) / 16 * 16;
+  static constexpr int kEwBytes = (kTileElems / 32 * 4 + 15) / 16 * 16;
   static constexpr int kBdMaskOff = kNodes * D * 8;                 // ints after the doubles
   static constexpr int kBdBytes = (kBdMaskOff + kNodes * 4 + 15) / 16 * 16;
   static constexpr int kE = 0;
   static constexpr int kR = kE + 2 * kEBytes;
-  static constexpr int kU = kR + 3 * kRBytes;
+  static constexpr int kU = kR + kRecBufs * kRBytes;
   static constexpr int kRs = kU + 2 * kUBytes;
   static constexpr int kEw = kRs + 2 * kRsBytes;
   static constexpr int kBd = kEw + 2 * kEwBytes;
-  static constexpr int kBytes = kBd + 3 * kBdBytes;
-  static_assert(kBytes <= 227 * 1024, "the pipeline must fit in the shared memory of one block");
+  static constexpr int kBytes = kBd + kRecBufs * kBdBytes;
+  // (the kernels also hold about 300 bytes of static shared memory: barriers and tile info)
+  static_assert(kBytes + 512 <= 227 * 1024, "the pipeline must fit in the shared memory of one block");
   static_assert(kEBytes % 16 == 0 && kRBytes % 16 == 0, "alignment");
   static_assert(2 * kRsBytes >= 2 * kTileThreads * 8, "the final reduction reuses Rs");
 };
 
-// The tile structure and element arrays of one precision (structure of arrays, stride ne).
+// The tile structure and element blocks of one precision.
 struct TileArgs {
   const int32_t* ebeg;         // ntiles + 1
   const int32_t* nbeg;         // ntiles + 1
   const int4* node;            // node records
-  const unsigned char* dphi;   // DIM*DIM arrays of `stride` entries of EB bytes
-  const unsigned char* vol;    // `stride` entries of EB bytes
-  const uint4* elem;           // local ids / slots
+  const unsigned char* blk;    // ntiles blocks of S::kEBytes: the layout of an element stage
   int64_t ntiles;
-  int64_t stride;              // padded_ne(ne)
   long long wait_limit;
 };
 
-// Thread 0: bulk copies of the element arrays of elements [e0, e1) into the stage at `st`,
-// completing on `bar` (one arrival; an empty range completes the phase at once).  The stage
-// was last read by ordinary loads of the element warps, which released it through the empty
-// barrier the caller waited for; a bulk copy that overwrites data read that way needs no
-// proxy fence (only data written by ordinary stores and read by the copy engine would).
-template <class S, int EB>
-__device__ __forceinline__ void pipe_issue_elems(unsigned char* st, const TileArgs& A, int e0, int e1,
-                                                 uint64_t* bar) {
-  const int n = e1 - e0;
-  const uint32_t bytes = ((uint32_t)n * EB + 15u) & ~15u;
-  mbar_arrive_expect_tx(bar, S::kArrays * bytes + (uint32_t)n * 16u);
-  if (n > 0) {
-#pragma unroll
-    for (int a = 0; a < S::kArrays; ++a) {
-      const unsigned char* p = (a < S::kArrays - 1 ? A.dphi + (int64_t)a * A.stride * EB : A.vol) + (int64_t)e0 * EB;
-      bulk_g2s(st + a * S::kArrayBytes, p, bytes, bar);
-    }
-    bulk_g2s(st + S::kElemOff, A.elem + e0, (uint32_t)n * 16u, bar);
-  }
+// Thread 0: one bulk copy of tile t's element block into the stage at `st`, completing on
+// `bar` (one arrival and the block's bytes).  The stage was last read by ordinary loads of the
+// element warps, which released it through the empty barrier the caller waited for; a bulk
+// copy that overwrites data read that way needs no proxy fence (only data written by ordinary
+// stores and read by the copy engine would).
+template <class S>
+__device__ __forceinline__ void pipe_issue_elems(unsigned char* st, const TileArgs& A, int64_t t, uint64_t* bar) {
+  mbar_arrive_expect_tx(bar, (uint32_t)S::kEBytes);
+  bulk_g2s(st, A.blk + t * S::kEBytes, (uint32_t)S::kEBytes, bar);
 }
 
 // Thread 0: bulk copy of the node records [k0, k0 + nt) into `rb`, completing on `bar` (the
