@@ -462,6 +462,28 @@ fe_status fe_server_reset_stats(fe_server* s);
 enum { FE_RATE_DFMA = 0, FE_RATE_DADD = 1, FE_RATE_DMUL = 2 };
 fe_status fe_fp64_rate(int device, int op, double* per_clock_per_sm, double* sm_ghz);
 
+/* ---- Bounds-checking build ----------------------------------------------------------
+ * Not in the paper: a debugging aid in place of a memory checker.  The library built with
+ * -DFE_DEBUG_BOUNDS (libfemenergy_bounds.so; the Python package builds it with
+ * build.build(bounds=True)) checks, in its kernels, every index read from memory before it
+ * addresses another buffer: node ids of elements and tile records, CSR slots and rows,
+ * local ids and slots of the FP32 tiles, caller node and element indices.  An index out of
+ * range is not used (the access goes to entry 0 instead) and the first one is recorded with
+ * the site that saw it (the BoundsSite numbers of csrc/bounds.cuh); no kernel traps.  In the
+ * ordinary build the checks are not compiled in.
+ *
+ * fe_debug_bounds_enabled: 1 in the bounds-checking build, 0 otherwise.
+ * fe_debug_bounds: reads and clears the record of `device` (waits for nothing: synchronise
+ *   first); *site = 0 when nothing was out of range, else the site and *index the index.  In
+ *   the ordinary build always *site = 0.
+ * fe_debug_bounds_selftest: one checked read of entry `index` of a device buffer of n
+ *   doubles (1 <= n <= 1024), so that an index outside [0, n) is recorded with site 99;
+ *   synchronises the device.  FE_EINVAL in the ordinary build (the read would not be
+ *   checked). */
+int fe_debug_bounds_enabled(void);
+fe_status fe_debug_bounds(int device, int* site, int64_t* index);
+fe_status fe_debug_bounds_selftest(int device, int64_t index, int64_t n);
+
 /* Energy without any allocation (the paper has no counterpart: this is an interface for
  * callers that cannot let this library allocate device memory -- a host program whose GPU
  * memory is owned entirely by its own pool allocator, or one whose time-critical loop must

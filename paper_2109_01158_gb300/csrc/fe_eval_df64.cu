@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) k_node_prep_df(int64_t nn, const dou
   double dot = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
-    const int64_t src = perm ? (int64_t)perm[i] : i;
+    const int64_t src = perm ? (int64_t)FE_CHK(perm[i], nn, kSiteNodePerm) : i;
     df w[DP];
 #pragma unroll
     for (int j = 0; j < D; ++j) {

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kThreads) k_pairs32(int64_t nn, const double* 
   double dot = 0.0;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // one node per thread
   if (i < nn) {
-    const int64_t src = perm ? (int64_t)__ldg(perm + i) : i;
+    const int64_t src = perm ? (int64_t)FE_CHK(__ldg(perm + i), nn, kSiteNodePerm) : i;
     float2 w[DP];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
         const int k = ntid + q * NN;
         mk[q] = 0;
         if (k < nt) {
-          const int64_t n = rec[k].x;
+          const int64_t n = FE_CHK(rec[k].x, mp.nn, kSiteTileNode);
           load_pairs_g<D>(upairs, n, w[q]);
 #pragma unroll
           for (int j = 0; j < D; ++j) {
@@ -380,12 +380,12 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
             for (int q = 1; q < cnt; ++q) sum = __fadd_rn(sum, col[q]);
           }
           const int dst = (rec.w >> 1) - 1;
-          const int64_t n = rec.x;
+          const int64_t n = FE_CHK(rec.x, mp.nn, kSiteTileNode);
           if (dst < 0) {
-            const int64_t o = caller_order ? (int64_t)rec.y : n;
+            const int64_t o = caller_order ? (int64_t)FE_CHK(rec.y, mp.nn, kSiteTileNode) : n;
             g[o * D + j] = ((bm[k] >> j) & 1) ? 0.0 : f2d_bits(sum) - bd[k * D + j];
           } else {
-            part[(int64_t)dst * D + j] = sum;
+            part[(int64_t)FE_CHK(dst, ta.npart, kSiteTilePart) * D + j] = sum;
           }
         }
       }
@@ -408,7 +408,9 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
       const int e = in.x + tid;
       if (e < in.y) {
         const uint4 le = reinterpret_cast<const uint4*>(St + S::kElemOff)[tid];
-        const int lid[4] = {(int)(le.x & 0xffffu), (int)(le.x >> 16), (int)(le.y & 0xffffu), (int)(le.y >> 16)};
+        const int nt_i = in.w;
+        const int lid[4] = {(int)FE_CHK(le.x & 0xffffu, nt_i, kSiteTileLocal), (int)FE_CHK(le.x >> 16, nt_i, kSiteTileLocal),
+                            (int)FE_CHK(le.y & 0xffffu, nt_i, kSiteTileLocal), (int)FE_CHK(le.y >> 16, nt_i, kSiteTileLocal)};
         // each node's pairs in 16-byte loads (a node record is DP pairs, 16-byte aligned)
         float2 un[K][D];
 #pragma unroll
@@ -429,7 +431,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
         if (ENERGY) ew = __fmul_rn(vT, W);
         if (DENS) dens[eperm ? (int64_t)__ldg(eperm + e) : (int64_t)e] = (double)W;
         if (GRAD) {
-          const int sl[4] = {(int)(le.z & 0xffffu), (int)(le.z >> 16), (int)(le.w & 0xffffu), (int)(le.w >> 16)};
+          const int sl[4] = {(int)FE_CHK(le.z & 0xffffu, S::kSlots, kSiteTileSlot), (int)FE_CHK(le.z >> 16, S::kSlots, kSiteTileSlot),
+                             (int)FE_CHK(le.w & 0xffffu, S::kSlots, kSiteTileSlot), (int)FE_CHK(le.w >> 16, S::kSlots, kSiteTileSlot)};
           float r0[D];
 #pragma unroll
           for (int l = 1; l < K; ++l) {
@@ -519,7 +522,7 @@ fe_status launch_tile_f32(fe_ctx* c, const ModelParams& mp, double* J, double* d
   static std::atomic<uint64_t> smem_set{0};
   fe_status st = ensure_smem((const void*)kern, c->device, S::kBytes, smem_set);
   if (st) return st;
-  TileArgs ta{c->tile_ebeg, c->tile_nbeg, c->tile_node, c->blk32, c->n_tiles, c->wait_limit};
+  TileArgs ta{c->tile_ebeg, c->tile_nbeg, c->tile_node, c->blk32, c->n_tiles, c->n_tpart, c->wait_limit};
   const bool disp = input_is_disp(c);
   const double* b = c->f_host.empty() ? nullptr : c->b;
   const int64_t grid = std::min<int64_t>(c->n_tiles, sm_count(c->device));

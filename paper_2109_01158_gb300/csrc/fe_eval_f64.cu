@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_node_prep(int64_t nn, const double
   double dot = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
-    const int64_t src = perm ? (int64_t)perm[i] : i;
+    const int64_t src = perm ? (int64_t)FE_CHK(perm[i], nn, kSiteNodePerm) : i;
     double w[DP];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kThreads) k_elem_f64(
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
     double ul[K][D];
 #pragma unroll
-    for (int l = 0; l < K; ++l) load_u<D>(u, __ldg(elems + (int64_t)l * ne + e), ul[l]);
+    for (int l = 0; l < K; ++l) load_u<D>(u, FE_CHK(__ldg(elems + (int64_t)l * ne + e), mp.nn, kSiteElemNode), ul[l]);
     double g[DIM][DIM];  // grad(phi_l), l = 1..DIM
 #pragma unroll
     for (int l = 0; l < DIM; ++l)
@@ -293,13 +293,13 @@ __global__ void __launch_bounds__(kThreads) k_elem_f64(
       }
     }
     if (ENERGY) acc = fma(vT, W, acc);
-    if (DENS) dens[eperm ? (int64_t)eperm[e] : e] = W;
+    if (DENS) dens[eperm ? (int64_t)FE_CHK(eperm[e], ne, kSiteElemPerm) : e] = W;
     if (GRAD) {
       // r_l = |T| P grad(phi_l) for l >= 1, r_0 = -sum_{l>=1} r_l (grad(phi_0) = -sum grad(phi_l))
       double r0[D];
 #pragma unroll
       for (int l = 1; l <= DIM; ++l) {
-        const int64_t q = __ldg(slot + (int64_t)l * ne + e);
+        const int64_t q = FE_CHK(__ldg(slot + (int64_t)l * ne + e), ne * K, kSiteElemSlot);
 #pragma unroll
         for (int j = 0; j < D; ++j) {
           double s = P[j][0] * g[l - 1][0];
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kThreads) k_elem_f64(
           r0[j] = (l == 1) ? -s : r0[j] - s;   // (the first term needs no addition)
         }
       }
-      const int64_t q0 = __ldg(slot + e);
+      const int64_t q0 = FE_CHK(__ldg(slot + e), ne * K, kSiteElemSlot);
 #pragma unroll
       for (int j = 0; j < D; ++j) r[q0 * D + j] = r0[j];
     }
@@ -722,6 +722,7 @@ ModelParams model_params(const fe_ctx* c) {
   mp.twoC1 = 2.0 * c->C1;
   mp.twoD1 = 2.0 * c->D1;
   mp.pcase = (c->p == 2.0) ? 2 : (c->p == 3.0) ? 3 : 0;
+  mp.nn = c->nn;
   return mp;
 }
 

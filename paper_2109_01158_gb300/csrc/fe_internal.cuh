@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "bounds.cuh"
 #include "df64.cuh"
 #include "femenergy.h"
 
@@ -32,6 +33,7 @@ struct ModelParams {
   double p, C1, D1;
   double twoC1, twoD1;   // 2 C1 and 2 D1
   int pcase;  // p-Laplacian: 2 -> p == 2, 3 -> p == 3, 0 -> general pow
+  int64_t nn;  // nodes of the mesh (the bound of the node-id checks of the bounds-checking build)
 };
 
 inline int grid_for(int64_t n, int max_blocks) {

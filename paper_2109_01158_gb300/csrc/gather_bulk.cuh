@@ -86,7 +86,15 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
     }
     const int64_t i = n0 + lane;
     if (i < nn) {
+#ifdef FE_DEBUG_BOUNDS
+      int32_t q0 = __ldg(row_ptr + i), q1 = __ldg(row_ptr + i + 1);
+      if (!(s0 <= q0 && q0 <= q1 && q1 <= s1)) {   // the row must lie in the warp's range
+        (void)FE_CHK(q1, 0, kSiteGatherRow);
+        q0 = q1 = (int32_t)s0;
+      }
+#else
       const int32_t q0 = __ldg(row_ptr + i), q1 = __ldg(row_ptr + i + 1);
+#endif
       Acc acc[D];
       if (staged) {
         // element k of r is at sbuf[k - k0] (a0 is a multiple of 16, so of sizeof(T)).
@@ -114,7 +122,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
             else acc[j].add(__ldg(r + (int64_t)q * D + j));
           }
       }
-      const int64_t dst = perm ? (int64_t)__ldg(perm + i) : i;
+      const int64_t dst = perm ? (int64_t)FE_CHK(__ldg(perm + i), nn, kSiteGatherPerm) : i;
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         const double val = b ? acc[j].value() - b[i * D + j] : acc[j].value();

@@ -83,6 +83,7 @@ struct TileArgs {
   const int4* node;            // node records
   const unsigned char* blk;    // ntiles blocks of S::kEBytes: the layout of an element stage
   int64_t ntiles;
+  int64_t npart;               // partial slots of the shared nodes
   long long wait_limit;
 };
 

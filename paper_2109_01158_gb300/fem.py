@@ -15,7 +15,8 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfemenergy.so")
+# the library to load: FEMENERGY_LIBRARY names another build (e.g. libfemenergy_bounds.so)
+LIB_PATH = os.environ.get("FEMENERGY_LIBRARY") or os.path.join(_HERE, "libfemenergy.so")
 
 FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_EDOMAIN, FE_ETIMEOUT, FE_EBUSY = range(7)
 FE_PLAPLACE, FE_NEOHOOKE, FE_PLAPLACE_LP = 0, 1, 2
@@ -92,6 +93,9 @@ _SIGNATURES = {
     "fe_batch_launch_count": [_vp, _vp],
     "fe_batch_set_wait_limit": [_vp, _i64],
     "fe_fp64_rate": [_int, _int, _vp, _vp],
+    "fe_debug_bounds_enabled": [],
+    "fe_debug_bounds": [_int, _vp, _vp],
+    "fe_debug_bounds_selftest": [_int, _i64, _i64],
     "fe_batch_plan": [_int, _vp, _vp, _i64, _vp, _vp, _vp, _vp],
     "fe_lbfgs_save": [_vp, _vp, _vp, _vp, _vp, _vp],
     "fe_lbfgs_restore": [_vp, _vp, _vp, _vp, _vp, _int],
@@ -105,7 +109,7 @@ _SIGNATURES = {
     "fe_energy_noalloc": [_int, _vp, _int, _int, _int, _dbl, _dbl, _dbl, _i64, _vp, _i64, _vp, _vp,
                           _vp, _vp, _vp, _vp],
 }
-_RESTYPE = {"fe_version": ctypes.c_int, "fe_last_error": ctypes.c_char_p}
+_RESTYPE = {"fe_version": ctypes.c_int, "fe_last_error": ctypes.c_char_p, "fe_debug_bounds_enabled": ctypes.c_int}
 
 _lib = None
 
@@ -281,6 +285,8 @@ fe_batch_energy_gradient = _checked("fe_batch_energy_gradient")
 fe_batch_launch_count = _checked("fe_batch_launch_count")
 fe_batch_set_wait_limit = _checked("fe_batch_set_wait_limit")
 fe_fp64_rate = _checked("fe_fp64_rate")
+fe_debug_bounds = _checked("fe_debug_bounds")
+fe_debug_bounds_selftest = _checked("fe_debug_bounds_selftest")
 fe_batch_plan = _checked("fe_batch_plan")
 fe_lbfgs_save = _checked("fe_lbfgs_save")
 fe_lbfgs_restore = _checked("fe_lbfgs_restore")
@@ -298,6 +304,29 @@ def batch_plan(prep_tiles, elem_tiles, resident_blocks):
     fe_batch_plan(n, pt, et, int(resident_blocks), st, rq, sp, ctypes.byref(tot))
     return [(st[q], rq[q], sp[q]) for q in range(3 * n)], tot.value
 FE_RATE_DFMA, FE_RATE_DADD, FE_RATE_DMUL = range(3)
+
+
+def fe_debug_bounds_enabled() -> int:
+    return load_library().fe_debug_bounds_enabled()
+
+
+def debug_bounds_enabled():
+    """True when the loaded library is the bounds-checking build."""
+    return bool(fe_debug_bounds_enabled())
+
+
+def debug_bounds(device=0):
+    """(site, index) of the first out-of-range index the kernels met since the last call, and
+    clear it; (0, 0) when there was none (always in the ordinary build)."""
+    site, index = ctypes.c_int(), ctypes.c_int64()
+    fe_debug_bounds(int(device), ctypes.byref(site), ctypes.byref(index))
+    return site.value, index.value
+
+
+def debug_bounds_selftest(index, n, device=0):
+    """One checked read of entry `index` of a device buffer of n doubles (bounds-checking
+    build only)."""
+    fe_debug_bounds_selftest(int(device), int(index), int(n))
 
 
 def fp64_rate(device=0, op=FE_RATE_DFMA):

@@ -118,3 +118,41 @@ def test_device_free_argument_checks(libpath):
     import sys
     res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert res.returncode == 0, (res.stdout, res.stderr)
+
+
+def test_bounds_calls_in_the_ordinary_build(libpath):
+    """The ordinary build reports that its kernels are not bounds-checked: no record, and the
+    self-test refused (its read would not be checked).  No device call is made."""
+    code = "\n".join([
+        "import ctypes, sys",
+        f"lib = ctypes.CDLL({libpath!r})",
+        "lib.fe_debug_bounds.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]",
+        "lib.fe_debug_bounds_selftest.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64]",
+        "site, index = ctypes.c_int(7), ctypes.c_int64(7)",
+        "got = [lib.fe_debug_bounds_enabled(), lib.fe_debug_bounds(0, ctypes.byref(site), ctypes.byref(index)),",
+        "       site.value, index.value, lib.fe_debug_bounds_selftest(0, 5, 4), lib.fe_debug_bounds(0, None, None)]",
+        "print(got)",
+        "sys.exit(0 if got == [0, 0, 0, 0, 1, 1] else 1)",
+    ])
+    import sys
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0, (res.stdout, res.stderr)
+
+
+def test_bounds_checking_build_links_and_exports_the_boundary():
+    """The bounds-checking variant (-DFE_DEBUG_BOUNDS) builds, says so, and exports every
+    symbol the header declares (loading it registers the kernels' error words; no device call)."""
+    from paper_2109_01158_gb300 import build
+    lib_path = build.build(bounds=True)
+    assert lib_path != build.LIB
+    code = "\n".join([
+        "import ctypes, sys",
+        f"lib = ctypes.CDLL({lib_path!r})",
+        f"names = {declared_names()!r}",
+        "missing = [n for n in names if not hasattr(lib, n)]",
+        "print(missing, lib.fe_debug_bounds_enabled())",
+        "sys.exit(0 if not missing and lib.fe_debug_bounds_enabled() == 1 else 1)",
+    ])
+    import sys
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0, (res.stdout, res.stderr)
