@@ -371,13 +371,22 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_f32(
           const int k = w / D, j = w - k * D;
           const int4 rec = Rr[k];
           const int beg = rec.z & 0xffff, cnt = (int)((unsigned)rec.z >> 16);
-          // the node's slots in order (each node's slots are consecutive in its column)
+          // the node's slots (consecutive in its column), two at a time: a first slot at an odd
+          // position alone, then 8-byte pairs into two running sums (one paired addition per
+          // pair), then a last odd slot; added in that fixed order
           const float* col = rc0 + j * (S::kColBytes / 4) + beg;
           float sum = 0.f;
           if (cnt > 0) {
-            sum = col[0];
+            const int q0 = beg & 1;   // the column starts 16-byte aligned
+            const float head = q0 ? col[0] : 0.f;
+            const int np = (cnt - q0) >> 1;
+            const float2* p2 = reinterpret_cast<const float2*>(col + q0);
+            float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
-            for (int q = 1; q < cnt; ++q) sum = __fadd_rn(sum, col[q]);
+            for (int t = 0; t < np; ++t) acc = __fadd2_rn(acc, p2[t]);
+            const int qt = q0 + 2 * np;
+            const float tail = qt < cnt ? col[qt] : 0.f;
+            sum = __fadd_rn(__fadd_rn(__fadd_rn(head, acc.x), acc.y), tail);
           }
           const int dst = (rec.w >> 1) - 1;
           const int64_t n = FE_CHK(rec.x, mp.nn, kSiteTileNode);
