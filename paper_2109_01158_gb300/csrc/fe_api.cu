@@ -630,6 +630,9 @@ fe_status fe_precompute(fe_ctx* c, unsigned precisions) {
     free_precompute(c);
     return set_error(FE_EINVAL, "degenerate element (zero volume)");
   }
+  // the per-element local ids / slots are in the FP32 tile blocks now (copied there by the
+  // precompute, which the synchronisation above finished): their own array is not read again
+  dev_free(c, &c->tile_elem, (size_t)c->ne);
   c->have_pre = true;
   c->precision = (precisions & 1u) ? FE_F64 : (precisions & 4u) ? FE_DF64 : FE_F32_COMP;
   return FE_OK;
