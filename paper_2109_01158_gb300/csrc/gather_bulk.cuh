@@ -9,6 +9,8 @@
 // read directly from global memory in slot order.
 #pragma once
 
+#include <type_traits>
+
 #include "async_copy.cuh"
 #include "fe_internal.cuh"
 
@@ -35,6 +37,60 @@ struct AccDF {
   __device__ __forceinline__ void add(float2 x) { s = df_add(s, df{x.x, x.y}); }
   __device__ __forceinline__ double value() const { return df_to_double(s); }
 };
+
+// A node's FP64 segment, staged in shared memory, summed in 64-bit fixed point: every term is
+// made an integer relative to the segment's largest exponent (keeping ceil(log2 len) + 1 bits
+// of headroom, so the integer sum cannot overflow), the integers are added exactly on the
+// integer pipes, and the sum goes back to FP64 with one rounding.  A term loses less than
+// 2^-(62 - headroom) of the largest term, so the result is as accurate as a sequential FP64
+// sum, and it does not depend on the order of the terms.  It replaces len FP64 additions per
+// component, which run at 1/64 of the FP32 rate on this GPU, by integer work and one
+// conversion.  Subnormal terms count as zero.  Returns false, and the caller adds in FP64,
+// for a segment longer than 512 terms or with an Inf or NaN term or no normal term.
+// Both passes walk the segment in the same rotated order as the FP64 sum (distinct banks).
+template <int D>
+__device__ __forceinline__ bool fixed_point_sum(const double* sbuf, int64_t q0, int32_t len, int lane,
+                                                double (&out)[D]) {
+  if (len < 1 || len > 512) return false;
+  unsigned emax[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) emax[j] = 0u;
+  int32_t pos = lane % len;
+  for (int32_t t = 0; t < len; ++t) {
+    const int64_t q = q0 + pos;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const unsigned e = (unsigned)((unsigned long long)__double_as_longlong(sbuf[q * D + j]) >> 52) & 0x7ffu;
+      emax[j] = e > emax[j] ? e : emax[j];
+    }
+    pos = (pos + 1 == len) ? 0 : pos + 1;
+  }
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < D; ++j) ok = ok && emax[j] != 0u && emax[j] != 0x7ffu;
+  if (!ok) return false;
+  const int up = 9 - (len > 1 ? 32 - __clz(len - 1) : 0);   // 62 - (ceil(log2 len) + 1) - 52
+  long long acc[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) acc[j] = 0;
+  pos = lane % len;
+  for (int32_t t = 0; t < len; ++t) {
+    const int64_t q = q0 + pos;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(sbuf[q * D + j]);
+      const unsigned e = (unsigned)(bits >> 52) & 0x7ffu;
+      const unsigned long long m = (bits & 0xfffffffffffffULL) | (1ULL << 52);
+      const unsigned d = emax[j] - e;
+      const long long x = (e == 0u || d > 63u) ? 0LL : (long long)((m << up) >> d);
+      acc[j] += (bits >> 63) ? -x : x;
+    }
+    pos = (pos + 1 == len) ? 0 : pos + 1;
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) out[j] = ldexp((double)acc[j], (int)emax[j] - 1075 - up);
+  return true;
+}
 
 // The kernel and its launcher have internal linkage: every translation unit that uses them
 // compiles its own copy of the kernel, and the launcher's once-per-device attribute mask must
@@ -104,8 +160,17 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather_bulk(
         // still fixed by the mesh alone.
         const T* sbuf = reinterpret_cast<const T*>(buf) - a0 / (int64_t)sizeof(T);
         const int32_t len = q1 - q0;
+        bool done = false;
+        if constexpr (std::is_same<T, double>::value) {   // FP64 slots: fixed-point sums
+          double fx[D];
+          done = fixed_point_sum<D>(reinterpret_cast<const double*>(sbuf), (int64_t)q0, len, lane, fx);
+          if (done) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) acc[j].set(fx[j]);
+          }
+        }
         int32_t pos = len > 0 ? lane % len : 0;
-        for (int32_t t = 0; t < len; ++t) {
+        for (int32_t t = 0; t < len && !done; ++t) {
           const int64_t q = (int64_t)q0 + pos;
 #pragma unroll
           for (int j = 0; j < D; ++j) {
